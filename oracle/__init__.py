@@ -1,0 +1,261 @@
+"""CPU oracle for the ACO hot path (test infrastructure only).
+
+The oracle is the correctness reference the CUDA library is checked against: a plain,
+single-threaded FP64 C implementation (``aco_oracle.c``) of Chitty's ACO method -- Section 2
+(Eq. 1-5, dense pheromone), Section 3 (per-ant l_best pheromone source, weights
+C_gbest / C_lbest) and Algorithm 1 (PartialACO) -- plus exact k-nearest-neighbour candidate
+lists and exact tour lengths.  Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's
+CPU-baseline leg may import this package; the library never does.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "aco_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "lib")
+_LIB = os.path.join(_LIB_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MODE_DENSE = 0
+MODE_LBEST = 1
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("mode", ctypes.c_int32), ("n", ctypes.c_int32), ("m", ctypes.c_int32), ("k", ctypes.c_int32),
+        ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("rho", ctypes.c_double),
+        ("tau0", ctypes.c_double), ("max_mod_frac", ctypes.c_double), ("p_partial", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("fallback", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc, FP64, no FMA contraction) into oracle/lib/liboracle.so."""
+    with _lock:
+        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+            return _LIB
+        os.makedirs(_LIB_DIR, exist_ok=True)
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+        f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+        u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+        u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+        u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+        i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+        sig = {
+            "or_philox4x32_10": (None, [u32p, u32p, u32p]),
+            "or_u53": (ctypes.c_double, [ctypes.c_uint32, ctypes.c_uint32]),
+            "or_bounded": (ctypes.c_uint32, [ctypes.c_uint32, ctypes.c_uint32]),
+            "or_powr": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
+            "or_edge_len": (ctypes.c_double, [f64p, ctypes.c_int, ctypes.c_int]),
+            "or_tour_length": (ctypes.c_double, [ctypes.c_int, f64p, i32p]),
+            "or_tour_lengths": (None, [ctypes.c_int, f64p, i32p, ctypes.c_int, f64p]),
+            "or_knn": (ctypes.c_int, [ctypes.c_int, f64p, ctypes.c_int, i32p]),
+            "or_create": (P, [ctypes.POINTER(Params), f64p]),
+            "or_destroy": (None, [P]),
+            "or_construct": (None, [P, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
+            "or_update": (None, [P]),
+            "or_get_lbest": (None, [P, i32p]),
+            "or_get_clen": (None, [P, f64p]),
+            "or_get_newtours": (None, [P, i32p]),
+            "or_get_newlen": (None, [P, f64p]),
+            "or_get_seg": (None, [P, i32p, i32p]),
+            "or_get_tau": (None, [P, f64p]),
+            "or_set_tau": (None, [P, f64p]),
+            "or_get_cand": (None, [P, i32p]),
+            "or_get_etab": (None, [P, f64p]),
+            "or_get_counters": (None, [P, i64p]),
+            "or_reset_counters": (None, [P]),
+            "or_initialized": (ctypes.c_int, [P]),
+            "or_cand_weights": (None, [P, f64p, u64p, u64p]),
+            "or_set_lbest": (None, [P, i32p, f64p]),
+            "or_step_probs": (ctypes.c_int, [P, ctypes.c_int, u8p, f64p]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------------ free functions
+def philox4x32_10(ctr, key) -> np.ndarray:
+    out = np.zeros(4, np.uint32)
+    lib().or_philox4x32_10(np.asarray(ctr, np.uint32), np.asarray(key, np.uint32), out)
+    return out
+
+
+def u53(x0: int, x1: int) -> float:
+    return lib().or_u53(x0, x1)
+
+
+def bounded(x: int, r: int) -> int:
+    return lib().or_bounded(x, r)
+
+
+def powr(x: float, e: float) -> float:
+    return lib().or_powr(x, e)
+
+
+def edge_len(xy: np.ndarray, i: int, j: int) -> float:
+    return lib().or_edge_len(np.ascontiguousarray(xy, np.float64), i, j)
+
+
+def tour_length(xy: np.ndarray, tour: np.ndarray) -> float:
+    xy = np.ascontiguousarray(xy, np.float64)
+    return lib().or_tour_length(xy.shape[0], xy, np.ascontiguousarray(tour, np.int32))
+
+
+def tour_lengths(xy: np.ndarray, tours: np.ndarray) -> np.ndarray:
+    xy = np.ascontiguousarray(xy, np.float64)
+    tours = np.ascontiguousarray(tours, np.int32)
+    out = np.zeros(tours.shape[0], np.float64)
+    lib().or_tour_lengths(tours.shape[1], xy, tours, tours.shape[0], out)
+    return out
+
+
+def knn(xy: np.ndarray, k: int) -> np.ndarray:
+    """Exact candidate lists (n, k); raises on coincident cities."""
+    xy = np.ascontiguousarray(xy, np.float64)
+    cand = np.zeros((xy.shape[0], k), np.int32)
+    if lib().or_knn(xy.shape[0], xy, k, cand) != 0:
+        raise ValueError("coincident cities")
+    return cand
+
+
+# ------------------------------------------------------------------ solver
+class Oracle:
+    """One colony: dense Section 2 ACO (mode 0) or the Section 3 l_best/PartialACO form (mode 1)."""
+
+    def __init__(self, xy: np.ndarray, *, mode: int, n: int, m: int, k: int = 0, alpha: float = 1.0,
+                 beta: float = 2.0, rho: float = 0.5, tau0: float = 1.0, max_mod_frac: float = 1.0,
+                 p_partial: float = 1.0, seed: int = 1, fallback: int = 0):
+        self.xy = np.ascontiguousarray(xy, np.float64)
+        assert self.xy.shape == (n, 2)
+        self.p = Params(mode, n, m, k, alpha, beta, rho, tau0, max_mod_frac, p_partial, seed, fallback, 0)
+        self.n, self.m, self.k, self.mode = n, m, k, mode
+        self._h = lib().or_create(ctypes.byref(self.p), self.xy)
+        if not self._h:
+            raise ValueError("oracle rejected the instance (n < 3, bad k or coincident cities)")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().or_destroy(h)
+            self._h = None
+
+    def construct(self, iteration: int, ants=None):
+        if ants is None:
+            lib().or_construct(self._h, iteration, None, 0)
+        else:
+            a = np.ascontiguousarray(ants, np.int32)
+            lib().or_construct(self._h, iteration, a.ctypes.data_as(ctypes.c_void_p), a.size)
+
+    def update(self):
+        lib().or_update(self._h)
+
+    def iterate(self, iteration: int):
+        self.construct(iteration)
+        self.update()
+
+    @property
+    def lbest(self) -> np.ndarray:
+        out = np.zeros((self.m, self.n), np.int32)
+        lib().or_get_lbest(self._h, out)
+        return out
+
+    @property
+    def clen(self) -> np.ndarray:
+        out = np.zeros(self.m, np.float64)
+        lib().or_get_clen(self._h, out)
+        return out
+
+    @property
+    def newtours(self) -> np.ndarray:
+        out = np.zeros((self.m, self.n), np.int32)
+        lib().or_get_newtours(self._h, out)
+        return out
+
+    @property
+    def newlen(self) -> np.ndarray:
+        out = np.zeros(self.m, np.float64)
+        lib().or_get_newlen(self._h, out)
+        return out
+
+    def segments(self):
+        s = np.zeros(self.m, np.int32)
+        M = np.zeros(self.m, np.int32)
+        lib().or_get_seg(self._h, s, M)
+        return s, M
+
+    @property
+    def tau(self) -> np.ndarray:
+        out = np.zeros((self.n, self.n), np.float64)
+        lib().or_get_tau(self._h, out)
+        return out
+
+    def set_tau(self, tau: np.ndarray):
+        lib().or_set_tau(self._h, np.ascontiguousarray(tau, np.float64))
+
+    @property
+    def cand(self) -> np.ndarray:
+        out = np.zeros((self.n, self.k), np.int32)
+        lib().or_get_cand(self._h, out)
+        return out
+
+    @property
+    def etab(self) -> np.ndarray:
+        out = np.zeros((self.n, self.n) if self.mode == 0 else (self.n, self.k), np.float64)
+        lib().or_get_etab(self._h, out)
+        return out
+
+    def counters(self) -> dict:
+        out = np.zeros(3, np.int64)
+        lib().or_get_counters(self._h, out)
+        return dict(decisions=int(out[0]), fallbacks=int(out[1]), scans=int(out[2]))
+
+    def reset_counters(self):
+        lib().or_reset_counters(self._h)
+
+    @property
+    def initialized(self) -> bool:
+        return bool(lib().or_initialized(self._h))
+
+    def cand_weights(self):
+        """(W, Q, q): candidate-edge weights tau^alpha eta^beta, integer pheromone sums, per-ant q."""
+        W = np.zeros((self.n, self.k), np.float64)
+        Q = np.zeros((self.n, self.k), np.uint64)
+        q = np.zeros(self.m, np.uint64)
+        lib().or_cand_weights(self._h, W, Q, q)
+        return W, Q, q
+
+    def set_lbest(self, lbest: np.ndarray, clen: np.ndarray):
+        lib().or_set_lbest(self._h, np.ascontiguousarray(lbest, np.int32), np.ascontiguousarray(clen, np.float64))
+
+    def step_probs(self, i: int, visited: np.ndarray):
+        """Eq. 1 probabilities at city i; returns (probs, exhausted)."""
+        v = np.ascontiguousarray(visited, np.uint8)
+        out = np.zeros(self.n if self.mode == 0 else self.k, np.float64)
+        ex = lib().or_step_probs(self._h, i, v, out)
+        return out, bool(ex)
