@@ -1,0 +1,152 @@
+/*
+ * aco.h -- C ABI of the GB300 (sm_103a) ACO library for the symmetric Euclidean TSP.
+ *
+ * The library implements the data-parallel hot path of D. M. Chitty, "Applying ACO To Large
+ * Scale TSP Instances" (UKCI 2017): tour construction by the random proportional rule
+ * (Section 2, Eq. 1), the pheromone update -- evaporation and deposit (Section 2, Eq. 2-5) in
+ * the dense form, and the per-ant l_best pheromone source of Section 3 with the PartialACO
+ * efficiency measure (Section 3.1, Algorithm 1) in the scalable form -- and the tour-length
+ * reduction.  Candidate lists of the k nearest cities (the Ant Colony System device cited in
+ * Section 6) restrict each decision in the scalable form.
+ *
+ * Conventions (every entry point):
+ *  - Pointers named *_dev are CUDA device pointers on the instance's device; *_host are host
+ *    pointers.  The caller owns every buffer it passes; the library copies what it keeps.
+ *  - All work is enqueued on the instance's stream.  Only the calls documented as
+ *    synchronising wait for the device.
+ *  - All device memory is allocated by aco_create_instance; no later call allocates.
+ *  - No call aborts or throws.  Errors are returned as aco_status; aco_last_error() gives a
+ *    message.  A device-side error (e.g. coincident cities) is reported by the next
+ *    synchronising call.
+ *  - An instance is not thread-safe: one host thread at a time.
+ */
+#ifndef ACO_H
+#define ACO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum aco_status {
+    ACO_OK = 0,
+    ACO_ERR_INVALID_ARG = 1, /* bad size, parameter or pointer; coincident cities          */
+    ACO_ERR_OOM = 2,         /* device allocation failed in aco_create_instance             */
+    ACO_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed                 */
+    ACO_ERR_STATE = 4,       /* call out of order (e.g. construct before build_candidates) */
+    ACO_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up                          */
+} aco_status;
+
+typedef enum aco_mode {
+    ACO_MODE_DENSE = 0,         /* Section 2: n x n FP64 pheromone, Eq. 1 over all unvisited */
+    ACO_MODE_LBEST_PARTIAL = 1  /* Section 3 + Algorithm 1: l_best pheromone, PartialACO    */
+} aco_mode;
+
+/* Parameters of one colony (Section 2-3 notation). */
+typedef struct aco_params {
+    int32_t mode;         /* aco_mode                                                        */
+    int32_t n;            /* cities, >= 3                                                    */
+    int32_t m;            /* ants, >= 1                                                      */
+    int32_t k;            /* candidate-list length, 1..min(32, n-1) (ignored in DENSE)       */
+    double alpha;         /* pheromone exponent of Eq. 1                                     */
+    double beta;          /* heuristic exponent of Eq. 1 (eta = 1/d)                         */
+    double rho;           /* evaporation rate of Eq. 2 (DENSE only; the Section 3 form has
+                             no evaporation matrix)                                          */
+    double tau0;          /* initial / base pheromone, > 0                                   */
+    double max_mod_frac;  /* f: at most floor(f n) cities are rebuilt (Section 3.1), (0, 1]  */
+    double p_partial;     /* probability of a partial (vs full) rebuild per ant, [0, 1]      */
+    uint64_t seed;        /* Philox4x32-10 key                                               */
+    int32_t fallback;     /* exhausted list: 0 = argmax tau^a eta^b over unvisited (ties to the
+                             lowest index), 1 = Eq. 1 over all unvisited                    */
+    int32_t reserved;     /* must be 0                                                       */
+} aco_params;
+
+/* Counters accumulated since creation (aco_get_stats). */
+typedef struct aco_stats {
+    uint64_t decisions;      /* cities chosen by Eq. 1 or the exhausted-list rule            */
+    uint64_t fallbacks;      /* decisions taken by the exhausted-list rule                   */
+    uint64_t exact_resolves; /* decisions re-evaluated in FP64 (FP32 screen inconclusive)    */
+    uint64_t improved;       /* l_best replacements (Algorithm 1) / tours deposited (DENSE)  */
+    uint64_t partial_ants;   /* partial rebuilds                                             */
+    uint64_t full_ants;      /* full constructions                                           */
+    double gbest;            /* length of the best tour so far (C_gbest), +inf if none       */
+    int32_t gbest_ant;       /* ant holding it (lowest index among equals), -1 if none       */
+    int32_t iterations;      /* completed construct + update pairs                           */
+} aco_stats;
+
+typedef struct aco_instance aco_instance; /* opaque: owns all device state of one colony */
+
+/* Create a colony on the current CUDA device.  xy_dev: n*2 FP64 coordinates (x0,y0,x1,...),
+ * copied.  stream: cudaStream_t to enqueue on (NULL = the legacy default stream).  Checks the
+ * parameters and that the coordinates are finite with bounding box * n < 2^30 (exact length
+ * accumulation range).  Allocates every device buffer the instance will use.  Synchronises.
+ * Problem statement: Section 2 (G = (V, E, d), d_ij = d_ji); parameters: Section 2-3. */
+aco_status aco_create_instance(const double* xy_dev, const aco_params* p, void* stream,
+                               aco_instance** out);
+
+/* Build the candidate lists: for every city the k nearest other cities, key (d^2, index)
+ * ascending with d^2 = dx*dx + dy*dy in FP64 (exact ACS-style candidate lists, Section 6), and
+ * the heuristic table eta^beta of every candidate edge (Section 2).  Also initialises the
+ * Eq. 1 weights to tau0^alpha eta^beta.  cand_out_dev: optional n*k int32 copy of the lists.
+ * In DENSE mode builds the n x n eta^beta table and sets tau = tau0.  Synchronises; returns
+ * ACO_ERR_INVALID_ARG if two cities coincide (eta = 1/d undefined). */
+aco_status aco_build_candidates(aco_instance* inst, int32_t* cand_out_dev);
+
+/* Tour construction for every ant (Section 2, Eq. 1; Algorithm 1).
+ * DENSE: each ant starts at a random city and applies Eq. 1 over all unvisited cities.
+ * LBEST: the first call builds full initial tours (Algorithm 1, lines 1-3; tau = tau0).  Later
+ * calls rebuild, per ant, a random contiguous part of at most floor(f n) cities of l_best
+ * (with probability p_partial; otherwise a full tour), using Eq. 1 over the unvisited
+ * candidates and the exhausted-list rule.  `iteration` keys the Philox draws (callers pass
+ * 0, 1, 2, ...).  tours_out_dev: optional m*n int32 copy of the new tours (l_best layout);
+ * len_out_dev: optional m FP64 lengths.  Needs aco_build_candidates first (ACO_ERR_STATE). */
+aco_status aco_construct_tours(aco_instance* inst, int32_t iteration, int32_t* tours_out_dev,
+                               double* len_out_dev);
+
+/* Pheromone update after aco_construct_tours.
+ * DENSE: Eq. 2 (tau <- (1 - rho) tau on every edge) then Eq. 3-5 (tau_ij += sum_k 1/C^k over
+ * the tours containing edge (i,j), both directions).
+ * LBEST: Algorithm 1 line 10 (an ant's l_best is replaced by its new tour when strictly
+ * shorter), C_gbest = min C_lbest, then the Section 3 pheromone of every candidate edge,
+ * tau_ij = tau0 + sum_a (C_gbest / C_a) [ (i,j) in l_best_a ] -- edges of replaced tours drop
+ * out (evaporation) and edges of new l_best tours enter (deposit). */
+aco_status aco_update_pheromone(aco_instance* inst);
+
+/* Tour-length reduction: out_dev[c] = sum of the n edge lengths of tours_dev[c*n ..] including
+ * the closing edge (Section 2), for c < count.  Exact: every edge on a 2^-96 grid, integer
+ * sum, one rounding to FP64 (order-free).  Tours must be permutations of 0..n-1 (not checked
+ * beyond index range; out-of-range indices give ACO_ERR_INVALID_ARG at the next
+ * synchronising call). */
+aco_status aco_tour_lengths(aco_instance* inst, const int32_t* tours_dev, int32_t count,
+                            double* out_dev);
+
+/* Checkpoint (Section 3 state): lbest_out_dev m*n int32 l_best tours, clen_out_dev m FP64
+ * lengths; tau_out_dev n*n FP64 (DENSE only, else may be NULL).  Any pointer may be NULL.
+ * Synchronises. */
+aco_status aco_get_state(aco_instance* inst, int32_t* lbest_out_dev, double* clen_out_dev,
+                         double* tau_out_dev);
+
+/* Restore a checkpoint (LBEST: l_best tours, lengths recomputed exactly; DENSE: tau).
+ * Philox draws are counter-based, so resuming at iteration t reproduces an uninterrupted run.
+ * Synchronises. */
+aco_status aco_set_state(aco_instance* inst, const int32_t* lbest_dev, const double* tau_dev);
+
+/* Counters since creation; synchronises and reports pending device-side errors. */
+aco_status aco_get_stats(aco_instance* inst, aco_stats* out_host);
+
+/* Eq. 1 probabilities as the construction kernel sees them (FP32 weights, FP32 normaliser)
+ * at city `city` for the visited bitset visited_bits_dev (ceil(n/32) uint32 words, bit j of
+ * word j/32 set = visited).  probs_out_dev: k floats (LBEST, candidate ranks) or n floats
+ * (DENSE).  *exhausted_out_dev = 1 when no candidate is unvisited (LBEST).  Diagnostic. */
+aco_status aco_step_probs(aco_instance* inst, int32_t city, const uint32_t* visited_bits_dev,
+                          float* probs_out_dev, int32_t* exhausted_out_dev);
+
+void aco_destroy_instance(aco_instance* inst);
+const char* aco_status_string(aco_status s);
+const char* aco_last_error(const aco_instance* inst);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ACO_H */

@@ -1,0 +1,29 @@
+"""GB300 (sm_103a) ACO library for large symmetric TSP instances -- Python binding.
+
+Thin ctypes marshalling over the C ABI in ``include/aco.h`` (same entry-point names).  Every step
+of the method runs in the library's CUDA kernels; PyTorch only provides device memory (tensor
+``data_ptr()``) and streams.  Importing this package does not touch the GPU; the first call
+loads ``lib/libaco_gb300.so`` and raises if it has not been built (``build.build()``).
+
+The method is D. M. Chitty, "Applying ACO To Large Scale TSP Instances" (UKCI 2017):
+Section 2 (Eq. 1-5), Section 3 (l_best pheromone, weights C_gbest / C_lbest) and Section 3.1
+(PartialACO, Algorithm 1).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from ._ffi import (ACO_MODE_DENSE, ACO_MODE_LBEST_PARTIAL, AcoError, Params, Stats, lib, library_path)
+from .colony import Colony
+
+__all__ = [
+    "ACO_MODE_DENSE", "ACO_MODE_LBEST_PARTIAL", "AcoError", "Params", "Stats", "Colony", "lib", "library_path",
+    "aco_create_instance", "aco_build_candidates", "aco_construct_tours", "aco_update_pheromone",
+    "aco_tour_lengths", "aco_get_state", "aco_set_state", "aco_get_stats", "aco_step_probs",
+    "aco_destroy_instance",
+]
+
+from ._ffi import (aco_build_candidates, aco_construct_tours, aco_create_instance, aco_destroy_instance,  # noqa: E402
+                   aco_get_state, aco_get_stats, aco_set_state, aco_step_probs, aco_tour_lengths,
+                   aco_update_pheromone)

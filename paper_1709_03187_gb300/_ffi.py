@@ -1,0 +1,148 @@
+"""ctypes declarations of include/aco.h and one Python function per entry point.
+
+Arguments are marshalled only: tensors become device pointers, streams become cudaStream_t
+handles, and a non-OK aco_status becomes ``AcoError``.  There is no fallback path: if the
+shared library is missing the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(HERE, "lib", "libaco_gb300.so")
+
+ACO_MODE_DENSE = 0
+ACO_MODE_LBEST_PARTIAL = 1
+_STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error", 4: "call out of order",
+           5: "device wait timed out"}
+
+
+class AcoError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("mode", ctypes.c_int32), ("n", ctypes.c_int32), ("m", ctypes.c_int32), ("k", ctypes.c_int32),
+        ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("rho", ctypes.c_double), ("tau0", ctypes.c_double),
+        ("max_mod_frac", ctypes.c_double), ("p_partial", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("fallback", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("decisions", ctypes.c_uint64), ("fallbacks", ctypes.c_uint64), ("exact_resolves", ctypes.c_uint64),
+        ("improved", ctypes.c_uint64), ("partial_ants", ctypes.c_uint64), ("full_ants", ctypes.c_uint64),
+        ("gbest", ctypes.c_double), ("gbest_ant", ctypes.c_int32), ("iterations", ctypes.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(library_path):
+            raise ImportError(f"CUDA library not built: {library_path} (run paper_1709_03187_gb300.build.build())")
+        L = ctypes.CDLL(library_path)
+        V, I32, I32P = ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p
+        S = ctypes.c_int
+        sig = {
+            "aco_create_instance": (S, [V, ctypes.POINTER(Params), V, ctypes.POINTER(V)]),
+            "aco_build_candidates": (S, [V, V]),
+            "aco_construct_tours": (S, [V, I32, V, V]),
+            "aco_update_pheromone": (S, [V]),
+            "aco_tour_lengths": (S, [V, V, I32, V]),
+            "aco_get_state": (S, [V, V, V, V]),
+            "aco_set_state": (S, [V, V, V]),
+            "aco_get_stats": (S, [V, ctypes.POINTER(Stats)]),
+            "aco_step_probs": (S, [V, I32, V, V, V]),
+            "aco_destroy_instance": (None, [V]),
+            "aco_status_string": (ctypes.c_char_p, [S]),
+            "aco_last_error": (ctypes.c_char_p, [V]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        del I32P
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _check(status: int, where: str, handle=None):
+    if status != 0:
+        msg = lib().aco_last_error(handle)
+        raise AcoError(status, where, msg.decode() if msg else "")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def aco_create_instance(xy_dev, params: Params, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().aco_create_instance(_ptr(xy_dev), ctypes.byref(params), _stream_handle(stream), ctypes.byref(h)),
+           "aco_create_instance")
+    return h.value
+
+
+def aco_build_candidates(h, cand_out_dev=None):
+    _check(lib().aco_build_candidates(h, _ptr(cand_out_dev)), "aco_build_candidates", h)
+
+
+def aco_construct_tours(h, iteration: int, tours_out_dev=None, len_out_dev=None):
+    _check(lib().aco_construct_tours(h, iteration, _ptr(tours_out_dev), _ptr(len_out_dev)), "aco_construct_tours", h)
+
+
+def aco_update_pheromone(h):
+    _check(lib().aco_update_pheromone(h), "aco_update_pheromone", h)
+
+
+def aco_tour_lengths(h, tours_dev, count: int, out_dev):
+    _check(lib().aco_tour_lengths(h, _ptr(tours_dev), count, _ptr(out_dev)), "aco_tour_lengths", h)
+
+
+def aco_get_state(h, lbest_out_dev=None, clen_out_dev=None, tau_out_dev=None):
+    _check(lib().aco_get_state(h, _ptr(lbest_out_dev), _ptr(clen_out_dev), _ptr(tau_out_dev)), "aco_get_state", h)
+
+
+def aco_set_state(h, lbest_dev=None, tau_dev=None):
+    _check(lib().aco_set_state(h, _ptr(lbest_dev), _ptr(tau_dev)), "aco_set_state", h)
+
+
+def aco_get_stats(h) -> Stats:
+    s = Stats()
+    _check(lib().aco_get_stats(h, ctypes.byref(s)), "aco_get_stats", h)
+    return s
+
+
+def aco_step_probs(h, city: int, visited_bits_dev, probs_out_dev, exhausted_out_dev):
+    _check(lib().aco_step_probs(h, city, _ptr(visited_bits_dev), _ptr(probs_out_dev), _ptr(exhausted_out_dev)),
+           "aco_step_probs", h)
+
+
+def aco_destroy_instance(h):
+    if h:
+        lib().aco_destroy_instance(h)

@@ -1,0 +1,362 @@
+// api.cu -- the C ABI entry points of include/aco.h: argument checks, allocation (all in
+// aco_create_instance), call ordering and error reporting.  Kernels live in grid_knn.cu,
+// construct.cu and update.cu.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "common.cuh"
+
+aco_status set_err(aco_instance* inst, aco_status s, const char* fmt, ...) {
+    if (inst) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(inst->err, sizeof(inst->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+aco_status check_launch(aco_instance* inst, const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_err(inst, ACO_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return ACO_OK;
+}
+
+static thread_local char g_create_err[512];
+
+extern "C" const char* aco_status_string(aco_status s) {
+    switch (s) {
+        case ACO_OK: return "ok";
+        case ACO_ERR_INVALID_ARG: return "invalid argument";
+        case ACO_ERR_OOM: return "out of device memory";
+        case ACO_ERR_CUDA: return "CUDA error";
+        case ACO_ERR_STATE: return "call out of order";
+        case ACO_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* aco_last_error(const aco_instance* inst) { return inst ? inst->err : g_create_err; }
+
+static void free_all(aco_instance* inst) {
+    void* ptrs[] = {inst->xy, inst->grid_dev, inst->city_cell, inst->cell_start, inst->cell_city, inst->cell_xy,
+                    inst->cell_fill, inst->candw, inst->cand, inst->etab, inst->W64, inst->rowflag, inst->lbest,
+                    inst->nb, inst->nbrank, inst->clen, inst->cfix, inst->q, inst->gbest, inst->gbest_ant,
+                    inst->seg, inst->antit, inst->accq, inst->tau, inst->etab_d, inst->W64d, inst->W32d,
+                    inst->tours, inst->succ_d, inst->pred_d, inst->counters, inst->errflag};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+template <typename T>
+static bool dalloc(T** p, size_t count, size_t* total) {
+    if (count == 0) count = 1;
+    *total += count * sizeof(T);
+    return cudaMalloc((void**)p, count * sizeof(T)) == cudaSuccess;
+}
+
+static bool params_ok(const aco_params* p, char* why, size_t wn) {
+    if (p->mode != ACO_MODE_DENSE && p->mode != ACO_MODE_LBEST_PARTIAL) return snprintf(why, wn, "mode"), false;
+    if (p->n < 3) return snprintf(why, wn, "n < 3"), false;
+    if (p->m < 1 || p->m > 16384) return snprintf(why, wn, "m must be in [1, 16384]"), false;
+    if (p->mode == ACO_MODE_LBEST_PARTIAL && (p->k < 1 || p->k > ACO_MAX_K || p->k > p->n - 1))
+        return snprintf(why, wn, "k must be in [1, min(32, n-1)]"), false;
+    if (!(isfinite(p->alpha) && p->alpha >= 0) || !(isfinite(p->beta) && p->beta >= 0))
+        return snprintf(why, wn, "alpha, beta must be finite and >= 0"), false;
+    if (!(isfinite(p->tau0) && p->tau0 > 0)) return snprintf(why, wn, "tau0 must be > 0"), false;
+    if (p->mode == ACO_MODE_DENSE && !(p->rho >= 0 && p->rho <= 1)) return snprintf(why, wn, "rho in [0,1]"), false;
+    if (p->mode == ACO_MODE_LBEST_PARTIAL && !(p->max_mod_frac > 0 && p->max_mod_frac <= 1))
+        return snprintf(why, wn, "max_mod_frac in (0,1]"), false;
+    if (!(p->p_partial >= 0 && p->p_partial <= 1)) return snprintf(why, wn, "p_partial in [0,1]"), false;
+    if (p->fallback != 0 && p->fallback != 1) return snprintf(why, wn, "fallback must be 0 or 1"), false;
+    if (p->reserved != 0) return snprintf(why, wn, "reserved must be 0"), false;
+    if (p->mode == ACO_MODE_DENSE && p->n > 8192) return snprintf(why, wn, "DENSE mode supports n <= 8192"), false;
+    // the visited bitset of one ant lives in shared memory (<= 200 KB)
+    if ((long long)(p->n + 31) / 32 * 4 > 200 * 1024) return snprintf(why, wn, "n too large for the visited bitset"), false;
+    if ((long long)p->n * p->m > (1ll << 31) - 1) return snprintf(why, wn, "n*m must be < 2^31"), false;
+    return true;
+}
+
+extern "C" aco_status aco_create_instance(const double* xy_dev, const aco_params* p, void* stream,
+                                          aco_instance** out) {
+    g_create_err[0] = 0;
+    if (!out || !p || !xy_dev) {
+        snprintf(g_create_err, sizeof(g_create_err), "null argument");
+        return ACO_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (!params_ok(p, g_create_err, sizeof(g_create_err))) return ACO_ERR_INVALID_ARG;
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, xy_dev) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        snprintf(g_create_err, sizeof(g_create_err), "xy_dev is not a device pointer");
+        return ACO_ERR_INVALID_ARG;
+    }
+    aco_instance* inst = new (std::nothrow) aco_instance();
+    if (!inst) return ACO_ERR_OOM;
+    memset(inst, 0, sizeof(*inst));
+    inst->p = *p;
+    inst->stream = (cudaStream_t)stream;
+    inst->gbest_ant = nullptr;
+    cudaGetDevice(&inst->device);
+    cudaDeviceGetAttribute(&inst->num_sms, cudaDevAttrMultiProcessorCount, inst->device);
+
+    const long long n = p->n, m = p->m, k = p->k;
+    size_t total = 0;
+    bool ok = true;
+    ok &= dalloc(&inst->xy, 2 * n, &total);
+    ok &= dalloc(&inst->grid_dev, 1, &total);
+    ok &= dalloc(&inst->city_cell, n, &total);
+    inst->ncells_cap = (int32_t)(n / 2 + 16);
+    ok &= dalloc(&inst->cell_start, inst->ncells_cap + 1, &total);
+    ok &= dalloc(&inst->cell_fill, inst->ncells_cap, &total);
+    ok &= dalloc(&inst->cell_city, n, &total);
+    ok &= dalloc(&inst->cell_xy, 2 * n, &total);
+    ok &= dalloc(&inst->counters, CNT_N, &total);
+    ok &= dalloc(&inst->errflag, 1, &total);
+    ok &= dalloc(&inst->clen, m, &total);
+    ok &= dalloc(&inst->cfix, 2 * m, &total);
+    ok &= dalloc(&inst->gbest, 1, &total);
+    ok &= dalloc(&inst->gbest_ant, 1, &total);
+    if (p->mode == ACO_MODE_LBEST_PARTIAL) {
+        ok &= dalloc(&inst->candw, n * k, &total);
+        ok &= dalloc(&inst->cand, n * k, &total);
+        ok &= dalloc(&inst->etab, n * k, &total);
+        ok &= dalloc(&inst->W64, n * k, &total);
+        ok &= dalloc(&inst->rowflag, n, &total);
+        ok &= dalloc(&inst->lbest, m * n, &total);
+        ok &= dalloc(&inst->nb, 2 * n * m, &total);
+        ok &= dalloc(&inst->nbrank, 2 * n * m, &total);
+        ok &= dalloc(&inst->q, m, &total);
+        ok &= dalloc(&inst->seg, m * n, &total);
+        ok &= dalloc(&inst->antit, m, &total);
+        ok &= dalloc(&inst->accq, m * n, &total);
+    } else {
+        ok &= dalloc(&inst->tau, n * n, &total);
+        ok &= dalloc(&inst->etab_d, n * n, &total);
+        ok &= dalloc(&inst->W64d, n * n, &total);
+        ok &= dalloc(&inst->W32d, n * n, &total);
+        ok &= dalloc(&inst->rowflag, n, &total);
+        ok &= dalloc(&inst->tours, m * n, &total);
+        ok &= dalloc(&inst->succ_d, m * n, &total);
+        ok &= dalloc(&inst->pred_d, m * n, &total);
+    }
+    if (!ok) {
+        cudaGetLastError();
+        snprintf(g_create_err, sizeof(g_create_err), "device allocation of %.3f GB failed", total / 1e9);
+        free_all(inst);
+        delete inst;
+        return ACO_ERR_OOM;
+    }
+    cudaStream_t s = inst->stream;
+    cudaMemcpyAsync(inst->xy, xy_dev, sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice, s);
+    cudaMemsetAsync(inst->counters, 0, sizeof(unsigned long long) * CNT_N, s);
+    cudaMemsetAsync(inst->errflag, 0, sizeof(int), s);
+    if (p->mode == ACO_MODE_LBEST_PARTIAL) {
+        cudaMemsetAsync(inst->accq, 0, sizeof(unsigned long long) * m * n, s);
+        cudaMemsetAsync(inst->nb, 0xFF, sizeof(int32_t) * 2 * n * m, s);
+        cudaMemsetAsync(inst->nbrank, 0xFF, 2 * n * m, s);
+    }
+    // coordinates: finite, and bounding box * n small enough for the exact length grid
+    double* hxy = (double*)malloc(sizeof(double) * 2 * n);
+    cudaMemcpyAsync(hxy, xy_dev, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        free(hxy);
+        snprintf(g_create_err, sizeof(g_create_err), "create: %s", cudaGetErrorString(e));
+        free_all(inst);
+        delete inst;
+        return ACO_ERR_CUDA;
+    }
+    double xmin = hxy[0], xmax = hxy[0], ymin = hxy[1], ymax = hxy[1];
+    bool finite = true;
+    for (long long i = 0; i < n; ++i) {
+        const double x = hxy[2 * i], y = hxy[2 * i + 1];
+        finite &= (bool)(isfinite(x) && isfinite(y));
+        xmin = fmin(xmin, x); xmax = fmax(xmax, x); ymin = fmin(ymin, y); ymax = fmax(ymax, y);
+    }
+    free(hxy);
+    const double diag = hypot(xmax - xmin, ymax - ymin);
+    if (!finite || !(diag * (double)n < 1073741824.0)) {
+        snprintf(g_create_err, sizeof(g_create_err), "coordinates must be finite with bbox diagonal * n < 2^30");
+        free_all(inst);
+        delete inst;
+        return ACO_ERR_INVALID_ARG;
+    }
+    // grid over the bounding box, about two cities per cell
+    GridDesc g;
+    g.xmin = xmin; g.xmax = xmax; g.ymin = ymin; g.ymax = ymax;
+    const double wx = fmax(xmax - xmin, 1e-300), wy = fmax(ymax - ymin, 1e-300);
+    const double target_cells = fmax(1.0, (double)(n / 2));
+    double h = sqrt(wx * wy / target_cells);
+    if (!(h > 0)) h = fmax(wx, wy);
+    h = fmax(h, fmax(wx, wy) / 4096.0);
+    int gx = (int)fmin(4096.0, floor(wx / h) + 1), gy = (int)fmin(4096.0, floor(wy / h) + 1);
+    while ((long long)gx * gy > inst->ncells_cap) {
+        h *= 1.05;
+        gx = (int)floor(wx / h) + 1;
+        gy = (int)floor(wy / h) + 1;
+    }
+    g.h = h; g.gx = gx; g.gy = gy;
+    const double mag = fabs(xmin) + fabs(xmax) + fabs(ymin) + fabs(ymax);
+    g.margin = 1e-6 * h + 1e-14 * mag;
+    inst->grid = g;
+    cudaMemcpy(inst->grid_dev, &g, sizeof(g), cudaMemcpyHostToDevice);
+    inst->last_iteration = -1;
+    *out = inst;
+    return ACO_OK;
+}
+
+extern "C" void aco_destroy_instance(aco_instance* inst) {
+    if (!inst) return;
+    cudaStreamSynchronize(inst->stream);
+    free_all(inst);
+    delete inst;
+}
+
+static aco_status sync_and_check(aco_instance* inst, const char* what) {
+    cudaError_t e = cudaStreamSynchronize(inst->stream);
+    if (e != cudaSuccess) return set_err(inst, ACO_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    int flag = 0;
+    e = cudaMemcpy(&flag, inst->errflag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return set_err(inst, ACO_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    if (flag) {
+        cudaMemset(inst->errflag, 0, sizeof(int));
+        if (flag & DEVERR_DUPLICATE) return set_err(inst, ACO_ERR_INVALID_ARG, "%s: coincident cities", what);
+        if (flag & DEVERR_BAD_TOUR) return set_err(inst, ACO_ERR_INVALID_ARG, "%s: tour index out of range", what);
+        if (flag & DEVERR_NONFINITE) return set_err(inst, ACO_ERR_INVALID_ARG, "%s: non-finite weight", what);
+        return set_err(inst, ACO_ERR_CUDA, "%s: device error flag %d", what, flag);
+    }
+    return ACO_OK;
+}
+
+extern "C" aco_status aco_build_candidates(aco_instance* inst, int32_t* cand_out_dev) {
+    if (!inst) return ACO_ERR_INVALID_ARG;
+    aco_status st = launch_build_grid_and_knn(inst);
+    if (st != ACO_OK) return st;
+    if (inst->p.mode == ACO_MODE_LBEST_PARTIAL) {
+        st = launch_lbest_init_weights(inst);
+        if (st != ACO_OK) return st;
+        if (cand_out_dev)
+            cudaMemcpyAsync(cand_out_dev, inst->cand, sizeof(int32_t) * (size_t)inst->p.n * inst->p.k,
+                            cudaMemcpyDeviceToDevice, inst->stream);
+    } else {
+        st = launch_dense_init(inst);
+        if (st != ACO_OK) return st;
+    }
+    st = sync_and_check(inst, "build_candidates");
+    if (st != ACO_OK) return st;
+    inst->cand_built = true;
+    inst->constructed = false;
+    inst->initialized = false;
+    return ACO_OK;
+}
+
+extern "C" aco_status aco_construct_tours(aco_instance* inst, int32_t iteration, int32_t* tours_out_dev,
+                                          double* len_out_dev) {
+    if (!inst) return ACO_ERR_INVALID_ARG;
+    if (!inst->cand_built) return set_err(inst, ACO_ERR_STATE, "construct_tours before build_candidates");
+    if (iteration < 0) return set_err(inst, ACO_ERR_INVALID_ARG, "iteration must be >= 0");
+    aco_status st = inst->p.mode == ACO_MODE_LBEST_PARTIAL ? launch_construct_lbest(inst, iteration)
+                                                           : launch_construct_dense(inst, iteration);
+    if (st != ACO_OK) return st;
+    if (tours_out_dev || len_out_dev) {
+        st = launch_write_new_tours(inst, tours_out_dev, len_out_dev);
+        if (st != ACO_OK) return st;
+    }
+    inst->constructed = true;
+    inst->last_iteration = iteration;
+    return ACO_OK;
+}
+
+extern "C" aco_status aco_update_pheromone(aco_instance* inst) {
+    if (!inst) return ACO_ERR_INVALID_ARG;
+    if (!inst->constructed) return set_err(inst, ACO_ERR_STATE, "update_pheromone without a construction");
+    aco_status st = inst->p.mode == ACO_MODE_LBEST_PARTIAL ? launch_update_lbest(inst) : launch_update_dense(inst);
+    if (st != ACO_OK) return st;
+    inst->constructed = false;
+    inst->initialized = true;
+    inst->iterations++;
+    return ACO_OK;
+}
+
+extern "C" aco_status aco_tour_lengths(aco_instance* inst, const int32_t* tours_dev, int32_t count, double* out_dev) {
+    if (!inst || count < 0 || (count > 0 && (!tours_dev || !out_dev))) return ACO_ERR_INVALID_ARG;
+    if (count == 0) return ACO_OK;
+    return launch_tour_lengths(inst, tours_dev, count, out_dev);
+}
+
+extern "C" aco_status aco_get_state(aco_instance* inst, int32_t* lbest_out_dev, double* clen_out_dev,
+                                    double* tau_out_dev) {
+    if (!inst) return ACO_ERR_INVALID_ARG;
+    const size_t n = inst->p.n, m = inst->p.m;
+    cudaStream_t s = inst->stream;
+    if (inst->p.mode == ACO_MODE_LBEST_PARTIAL) {
+        if (lbest_out_dev) cudaMemcpyAsync(lbest_out_dev, inst->lbest, sizeof(int32_t) * m * n, cudaMemcpyDeviceToDevice, s);
+        if (clen_out_dev) cudaMemcpyAsync(clen_out_dev, inst->clen, sizeof(double) * m, cudaMemcpyDeviceToDevice, s);
+    } else {
+        if (lbest_out_dev) cudaMemcpyAsync(lbest_out_dev, inst->tours, sizeof(int32_t) * m * n, cudaMemcpyDeviceToDevice, s);
+        if (clen_out_dev) cudaMemcpyAsync(clen_out_dev, inst->clen, sizeof(double) * m, cudaMemcpyDeviceToDevice, s);
+        if (tau_out_dev) cudaMemcpyAsync(tau_out_dev, inst->tau, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s);
+    }
+    return sync_and_check(inst, "get_state");
+}
+
+extern "C" aco_status aco_set_state(aco_instance* inst, const int32_t* lbest_dev, const double* tau_dev) {
+    if (!inst) return ACO_ERR_INVALID_ARG;
+    if (!inst->cand_built) return set_err(inst, ACO_ERR_STATE, "set_state before build_candidates");
+    if (inst->p.mode == ACO_MODE_LBEST_PARTIAL) {
+        if (!lbest_dev) return set_err(inst, ACO_ERR_INVALID_ARG, "lbest_dev is required");
+        aco_status st = launch_set_lbest(inst, lbest_dev);
+        if (st != ACO_OK) return st;
+    } else {
+        if (!tau_dev) return set_err(inst, ACO_ERR_INVALID_ARG, "tau_dev is required");
+        const size_t n = inst->p.n;
+        cudaMemcpyAsync(inst->tau, tau_dev, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, inst->stream);
+        aco_status st = launch_dense_init(inst);  // rebuilds the weights from tau (keeps tau)
+        if (st != ACO_OK) return st;
+    }
+    aco_status st = sync_and_check(inst, "set_state");
+    if (st != ACO_OK) return st;
+    inst->initialized = true;
+    inst->constructed = false;
+    return ACO_OK;
+}
+
+extern "C" aco_status aco_get_stats(aco_instance* inst, aco_stats* out_host) {
+    if (!inst || !out_host) return ACO_ERR_INVALID_ARG;
+    aco_status st = sync_and_check(inst, "get_stats");
+    if (st != ACO_OK) return st;
+    unsigned long long c[CNT_N];
+    cudaMemcpy(c, inst->counters, sizeof(c), cudaMemcpyDeviceToHost);
+    memset(out_host, 0, sizeof(*out_host));
+    out_host->decisions = c[CNT_DECISIONS];
+    out_host->fallbacks = c[CNT_FALLBACKS];
+    out_host->exact_resolves = c[CNT_RESOLVES];
+    out_host->improved = c[CNT_IMPROVED];
+    out_host->partial_ants = c[CNT_PARTIAL];
+    out_host->full_ants = c[CNT_FULL];
+    out_host->gbest = INFINITY;
+    out_host->gbest_ant = -1;
+    if (inst->initialized) {
+        cudaMemcpy(&out_host->gbest, inst->gbest, sizeof(double), cudaMemcpyDeviceToHost);
+        cudaMemcpy(&out_host->gbest_ant, inst->gbest_ant, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    }
+    out_host->iterations = inst->iterations;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_err(inst, ACO_ERR_CUDA, "get_stats: %s", cudaGetErrorString(e));
+    return ACO_OK;
+}
+
+extern "C" aco_status aco_step_probs(aco_instance* inst, int32_t city, const uint32_t* visited_bits_dev,
+                                     float* probs_out_dev, int32_t* exhausted_out_dev) {
+    if (!inst || !visited_bits_dev || !probs_out_dev || !exhausted_out_dev) return ACO_ERR_INVALID_ARG;
+    if (city < 0 || city >= inst->p.n) return set_err(inst, ACO_ERR_INVALID_ARG, "city out of range");
+    if (!inst->cand_built) return set_err(inst, ACO_ERR_STATE, "step_probs before build_candidates");
+    return launch_step_probs(inst, city, visited_bits_dev, probs_out_dev, exhausted_out_dev);
+}

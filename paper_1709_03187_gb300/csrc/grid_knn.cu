@@ -1,0 +1,201 @@
+// grid_knn.cu -- uniform grid over the cities and the exact k-nearest-neighbour candidate
+// lists (the ACS candidate lists cited in Section 6), fused with the heuristic table
+// eta^beta = (1/d)^beta of every candidate edge (Section 2).
+//
+// Grid: about two cities per cell over the bounding box; cities are counting-sorted by cell
+// (city ids and coordinates in cell order).  A query scans Chebyshev rings of cells around its
+// own cell and stops once the k-th best key (d^2, j) lies strictly inside a conservative lower
+// bound of the distance to every unscanned cell.  The result is the unique list of the k
+// smallest keys, identical to a brute-force sort.
+#include <float.h>
+#include <math.h>
+
+#include "common.cuh"
+
+#define FULL 0xffffffffu
+
+
+__global__ void grid_count_kernel(const double* __restrict__ xy, int n, const GridDesc* __restrict__ gd,
+                                  int* __restrict__ city_cell, int* __restrict__ cell_fill) {
+    const GridDesc g = *gd;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int cx = cell_coord(xy[2 * i], g.xmin, g.h, g.gx);
+        const int cy = cell_coord(xy[2 * i + 1], g.ymin, g.h, g.gy);
+        const int c = cy * g.gx + cx;
+        city_cell[i] = c;
+        atomicAdd(&cell_fill[c], 1);
+    }
+}
+
+// Exclusive scan of cnt[0..len) into out[0..len] with one block (len up to a few million).
+__global__ void scan_single_block_kernel(const int* __restrict__ cnt, int len, int* __restrict__ out) {
+    __shared__ int part[1024];
+    const int t = threadIdx.x, T = blockDim.x;
+    const int chunk = (len + T - 1) / T;
+    const int b = min(len, t * chunk), e = min(len, b + chunk);
+    int s = 0;
+    for (int i = b; i < e; ++i) s += cnt[i];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < T; o <<= 1) {
+        const int v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int run = part[t] - s;  // exclusive prefix of this chunk
+    for (int i = b; i < e; ++i) {
+        out[i] = run;
+        run += cnt[i];
+    }
+    if (t == T - 1) out[len] = part[T - 1];
+}
+
+__global__ void grid_scatter_kernel(const double* __restrict__ xy, int n, const int* __restrict__ city_cell,
+                                    const int* __restrict__ cell_start, int* __restrict__ cell_fill,
+                                    int* __restrict__ cell_city, double* __restrict__ cell_xy) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = city_cell[i];
+        const int pos = cell_start[c] + atomicAdd(&cell_fill[c], 1);
+        cell_city[pos] = i;
+        cell_xy[2 * pos] = xy[2 * i];
+        cell_xy[2 * pos + 1] = xy[2 * i + 1];
+    }
+}
+
+// Cell of the `idx`-th cell on Chebyshev ring r around (cx, cy); returns -1 outside the grid.
+__device__ __forceinline__ int ring_cell(const GridDesc& g, int cx, int cy, int r, int idx) {
+    int x, y;
+    if (r == 0) {
+        x = cx; y = cy;
+    } else if (idx < 2 * r + 1) {
+        x = cx - r + idx; y = cy - r;
+    } else if (idx < 4 * r + 2) {
+        x = cx - r + (idx - 2 * r - 1); y = cy + r;
+    } else if (idx < 6 * r + 1) {
+        x = cx - r; y = cy - r + 1 + (idx - 4 * r - 2);
+    } else {
+        x = cx + r; y = cy - r + 1 + (idx - 6 * r - 1);
+    }
+    if (x < 0 || y < 0 || x >= g.gx || y >= g.gy) return -1;
+    return y * g.gx + x;
+}
+
+__device__ __forceinline__ bool key_less(double da, int ja, double db, int jb) {
+    return da < db || (da == db && ja < jb);
+}
+
+// One warp per query city.
+__global__ void __launch_bounds__(256) knn_kernel(const double* __restrict__ xy, const GridDesc* __restrict__ gd,
+                                                  const int* __restrict__ city_cell, const int* __restrict__ cell_start,
+                                                  const int* __restrict__ cell_city, const double* __restrict__ cell_xy,
+                                                  int n, int k, double beta, int* __restrict__ cand,
+                                                  CandW* __restrict__ candw, double* __restrict__ etab,
+                                                  int* __restrict__ errflag) {
+    const GridDesc g = *gd;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nwarps) {
+        const double qx = xy[2 * i], qy = xy[2 * i + 1];
+        const int cell = city_cell[i];
+        const int cx = cell % g.gx, cy = cell / g.gx;
+        double ld = DBL_MAX;  // this lane's list entry (lanes < k), sorted ascending
+        int lj = 0x7fffffff;
+        double kd = DBL_MAX;
+        int kj = 0x7fffffff;
+        for (int r = 0;; ++r) {
+            const int ncell = r == 0 ? 1 : 8 * r;
+            for (int c0 = 0; c0 < ncell; c0 += 32) {
+                int pb = 0, pe = 0;
+                if (c0 + lane < ncell) {
+                    const int c = ring_cell(g, cx, cy, r, c0 + lane);
+                    if (c >= 0) { pb = cell_start[c]; pe = cell_start[c + 1]; }
+                }
+                while (__any_sync(FULL, pb < pe)) {
+                    double d2 = DBL_MAX;
+                    int j = 0x7fffffff;
+                    bool cand_ok = false;
+                    if (pb < pe) {
+                        j = cell_city[pb];
+                        d2 = dist2(qx, qy, cell_xy[2 * pb], cell_xy[2 * pb + 1]);
+                        cand_ok = (j != i) && key_less(d2, j, kd, kj);
+                        ++pb;
+                    }
+                    unsigned pend = __ballot_sync(FULL, cand_ok);
+                    while (pend) {
+                        const int src = __ffs(pend) - 1;
+                        pend &= pend - 1;
+                        const double cd = __shfl_sync(FULL, d2, src);
+                        const int cj = __shfl_sync(FULL, j, src);
+                        if (key_less(cd, cj, kd, kj)) {
+                            const bool before = lane < k && key_less(ld, lj, cd, cj);
+                            const int pos = __popc(__ballot_sync(FULL, before));
+                            const double ud = __shfl_up_sync(FULL, ld, 1);
+                            const int uj = __shfl_up_sync(FULL, lj, 1);
+                            if (lane == pos) { ld = cd; lj = cj; }
+                            else if (lane > pos) { ld = ud; lj = uj; }
+                            kd = __shfl_sync(FULL, ld, k - 1);
+                            kj = __shfl_sync(FULL, lj, k - 1);
+                        }
+                    }
+                }
+            }
+            const double lb = ring_lower_bound(g, qx, qy, cx, cy, r);
+            if (lb < 0.0) break;                       // every cell scanned
+            if (kd < __dmul_rn(lb, lb)) break;        // nothing unscanned can enter the list
+        }
+        if (lane < k) {
+            cand[(size_t)i * k + lane] = lj;
+            candw[(size_t)i * k + lane].city = lj;
+            if (ld == 0.0) atomicOr(errflag, DEVERR_DUPLICATE);
+            const double e = eta_pow_from_d2(ld, beta);
+            if (!isfinite(e)) atomicOr(errflag, DEVERR_NONFINITE);
+            etab[(size_t)i * k + lane] = e;
+        }
+    }
+}
+
+// Dense mode: eta^beta for every ordered pair and tau = tau0.
+__global__ void dense_eta_kernel(const double* __restrict__ xy, int n, double beta, double tau0,
+                                 double* __restrict__ etab_d, double* __restrict__ tau, int* __restrict__ errflag) {
+    const long long total = (long long)n * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        tau[e] = tau0;
+        if (i == j) { etab_d[e] = 0.0; continue; }
+        const double d2 = dist2(xy[2 * i], xy[2 * i + 1], xy[2 * j], xy[2 * j + 1]);
+        if (d2 == 0.0) atomicOr(errflag, DEVERR_DUPLICATE);
+        const double v = eta_pow_from_d2(d2, beta);
+        if (!isfinite(v)) atomicOr(errflag, DEVERR_NONFINITE);
+        etab_d[e] = v;
+    }
+}
+
+aco_status launch_build_grid_and_knn(aco_instance* inst) {
+    const int n = inst->p.n;
+    cudaStream_t s = inst->stream;
+    if (inst->p.mode == ACO_MODE_DENSE) {
+        const long long total = (long long)n * n;
+        const int blocks = (int)fmin(4.0 * inst->num_sms * 8, (double)ceil_div(total, 256));
+        dense_eta_kernel<<<blocks, 256, 0, s>>>(inst->xy, n, inst->p.beta, inst->p.tau0, inst->etab_d, inst->tau,
+                                                inst->errflag);
+        return check_launch(inst, "dense_eta_kernel");
+    }
+    const GridDesc& g = inst->grid;
+    const int ncells = g.gx * g.gy;
+    cudaMemsetAsync(inst->cell_fill, 0, sizeof(int) * ncells, s);
+    const int blocks = (int)fmin((double)inst->num_sms * 8, (double)ceil_div(n, 256));
+    grid_count_kernel<<<blocks, 256, 0, s>>>(inst->xy, n, inst->grid_dev, inst->city_cell, inst->cell_fill);
+    scan_single_block_kernel<<<1, 1024, 0, s>>>(inst->cell_fill, ncells, inst->cell_start);
+    cudaMemsetAsync(inst->cell_fill, 0, sizeof(int) * ncells, s);
+    grid_scatter_kernel<<<blocks, 256, 0, s>>>(inst->xy, n, inst->city_cell, inst->cell_start, inst->cell_fill,
+                                               inst->cell_city, inst->cell_xy);
+    aco_status st = check_launch(inst, "grid build");
+    if (st != ACO_OK) return st;
+    const int warps_per_block = 8;
+    const int kblocks = (int)fmin((double)inst->num_sms * 16, (double)ceil_div(n, warps_per_block));
+    knn_kernel<<<kblocks, 32 * warps_per_block, 0, s>>>(inst->xy, inst->grid_dev, inst->city_cell, inst->cell_start,
+                                                       inst->cell_city, inst->cell_xy, n, inst->p.k, inst->p.beta,
+                                                       inst->cand, inst->candw, inst->etab, inst->errflag);
+    return check_launch(inst, "knn_kernel");
+}

@@ -1,0 +1,438 @@
+// update.cu -- pheromone update and tour lengths.
+//
+// Scalable form (Section 3, Algorithm 1):
+//   commit_kernel      l_best_a <- new tour when strictly shorter (Algorithm 1, last step of the
+//                      ant loop); rewrites only the rebuilt positions and the neighbour entries
+//                      (succ, pred and their candidate ranks) of the M + 2 cities they touch.
+//   gbest_q_kernel     C_gbest = min_a C_a (lowest ant on ties); per-ant deposit weight
+//                      q_a = round(C_gbest / C_a * 2^32)  (Section 3: quality of g_best over
+//                      quality of l_best, in (0, 1]).
+//   rebuild_kernel     the pheromone of every candidate edge,
+//                      Q_ir = sum_a q_a [cand_ir is succ_a(i) or pred_a(i)],
+//                      tau_ir = tau0 + Q_ir 2^-32, and the Eq. 1 weight tau^alpha eta^beta in
+//                      FP64 plus its FP32 screen copy.  Edges of replaced l_best tours have
+//                      dropped out of the neighbour table (the P-ACO form of evaporation) and
+//                      the new ones entered (deposit).  This is a streaming pass over the
+//                      n x m table of neighbour ranks (2 bytes per city and ant).
+// Dense form (Section 2): Eq. 2 then Eq. 3-5 on the n x n matrix.
+// Tour lengths: exact 2^-96 fixed-point sums (order-free), one rounding.
+#include <float.h>
+#include <math.h>
+
+#include "common.cuh"
+
+#define FULL 0xffffffffu
+
+__device__ __forceinline__ uint8_t rank_of(const int* __restrict__ cand, int k, int city, int other) {
+    const int* row = cand + (size_t)city * k;
+    for (int r = 0; r < k; ++r)
+        if (row[r] == other) return (uint8_t)r;
+    return 0xFF;
+}
+
+__device__ __forceinline__ void set_neighbours(int* __restrict__ nb, uint8_t* __restrict__ nbrank,
+                                               const int* __restrict__ cand, int m, int k, int a, int c, int succ,
+                                               int pred) {
+    const size_t e = ((size_t)c * m + a) * 2;
+    nb[e] = succ;
+    nb[e + 1] = pred;
+    nbrank[e] = rank_of(cand, k, c, succ);
+    nbrank[e + 1] = rank_of(cand, k, c, pred);
+}
+
+// One warp per ant.
+__global__ void __launch_bounds__(32) commit_kernel(int n, int m, int k, const int* __restrict__ cand,
+                                                    int* __restrict__ lbest, int* __restrict__ nb,
+                                                    uint8_t* __restrict__ nbrank, const int* __restrict__ seg,
+                                                    const AntIter* __restrict__ antit, double* __restrict__ clen,
+                                                    unsigned long long* __restrict__ cfix,
+                                                    unsigned long long* __restrict__ counters) {
+    const int a = blockIdx.x, lane = threadIdx.x;
+    const AntIter it = antit[a];
+    if (!(it.newlen < clen[a])) return;
+    int* L = lbest + (size_t)a * n;
+    const int* S = seg + (size_t)a * n;
+    if (it.s < 0) {
+        for (int t = lane; t < n; t += 32) L[t] = S[t];
+        __syncwarp();
+        for (int t = lane; t < n; t += 32)
+            set_neighbours(nb, nbrank, cand, m, k, a, S[t], S[t + 1 == n ? 0 : t + 1], S[t == 0 ? n - 1 : t - 1]);
+    } else {
+        const int e = L[(it.s + it.P - 1) % n];
+        const int start = L[it.s];
+        const int M = it.M;
+        __syncwarp();
+        for (int t = lane; t < M; t += 32) L[(it.s + it.P + t) % n] = S[t];
+        for (int t = lane; t < M; t += 32) {
+            const int pc = t == 0 ? e : S[t - 1];
+            const int sc = t == M - 1 ? start : S[t + 1];
+            set_neighbours(nb, nbrank, cand, m, k, a, S[t], sc, pc);
+        }
+        if (lane == 0) {
+            const size_t ee = ((size_t)e * m + a) * 2;
+            nb[ee] = S[0];
+            nbrank[ee] = rank_of(cand, k, e, S[0]);
+            const size_t es = ((size_t)start * m + a) * 2 + 1;
+            nb[es] = S[M - 1];
+            nbrank[es] = rank_of(cand, k, start, S[M - 1]);
+        }
+    }
+    if (lane == 0) {
+        clen[a] = it.newlen;
+        cfix[2 * a] = it.fix_lo;
+        cfix[2 * a + 1] = it.fix_hi;
+        atomicAdd(&counters[CNT_IMPROVED], 1ull);
+    }
+}
+
+// Single block: C_gbest, its ant, and the per-ant deposit weights.  keep_prev: fold in the
+// previous g_best (dense mode keeps the best over all iterations).
+__global__ void gbest_q_kernel(int m, const double* __restrict__ clen, double* __restrict__ gbest,
+                               int* __restrict__ gbest_ant, unsigned long long* __restrict__ q, int keep_prev) {
+    __shared__ double sv[32];
+    __shared__ int si[32];
+    __shared__ double cg_s;
+    double v = DBL_MAX * 2;  // +inf
+    int idx = 0x7fffffff;
+    for (int a = threadIdx.x; a < m; a += blockDim.x) {
+        const double c = clen[a];
+        if (c < v || (c == v && a < idx)) { v = c; idx = a; }
+    }
+    for (int o = 16; o; o >>= 1) {
+        const double ov = __shfl_xor_sync(FULL, v, o);
+        const int oi = __shfl_xor_sync(FULL, idx, o);
+        if (ov < v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { sv[threadIdx.x >> 5] = v; si[threadIdx.x >> 5] = idx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (sv[w] < v || (sv[w] == v && si[w] < idx)) { v = sv[w]; idx = si[w]; }
+        if (keep_prev && !(v < *gbest)) {
+            v = *gbest;
+            idx = *gbest_ant;
+        }
+        *gbest = v;
+        *gbest_ant = idx;
+        cg_s = v;
+    }
+    __syncthreads();
+    if (q) {
+        const double cg = cg_s;
+        for (int a = threadIdx.x; a < m; a += blockDim.x)
+            q[a] = __double2ull_rn(__dmul_rn(__ddiv_rn(cg, clen[a]), 4294967296.0));
+    }
+}
+
+// One warp per city; lane-private histograms in shared memory (conflict-free column per lane).
+template <bool VEC>
+__global__ void __launch_bounds__(256) rebuild_kernel(int n, int m, int k, double tau0, double alpha, int use_ants,
+                                                      const uint8_t* __restrict__ nbrank,
+                                                      const unsigned long long* __restrict__ q,
+                                                      const double* __restrict__ etab, CandW* __restrict__ candw,
+                                                      double* __restrict__ W64, uint8_t* __restrict__ rowflag,
+                                                      int* __restrict__ errflag) {
+    extern __shared__ unsigned long long sm[];
+    const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned long long* qs = sm;                                  // m
+    unsigned long long* hist = sm + m + (size_t)w * k * 32;      // [k][32]
+    if (use_ants)
+        for (int a = threadIdx.x; a < m; a += blockDim.x) qs[a] = q[a];
+    __syncthreads();
+    for (int i = blockIdx.x * warps + w; i < n; i += gridDim.x * warps) {
+        unsigned long long Q = 0;
+        if (use_ants) {
+            for (int r = 0; r < k; ++r) hist[r * 32 + lane] = 0ull;
+            const uint8_t* row = nbrank + (size_t)i * m * 2;
+            if (VEC) {
+                for (int base = 0; base < m; base += 256) {
+                    const int a0 = base + lane * 8;
+                    if (a0 < m) {
+                        const uint4 v = *reinterpret_cast<const uint4*>(row + 2 * (size_t)a0);
+                        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+#pragma unroll
+                            for (int g = 0; g < 2; ++g) {
+                                const int a = a0 + 2 * h + g;
+                                const uint32_t pair = wv[h] >> (16 * g);
+                                const uint32_t rs = pair & 0xFFu, rp = (pair >> 8) & 0xFFu;
+                                const unsigned long long qa = qs[a];
+                                if (rs < (uint32_t)k) hist[rs * 32 + lane] += qa;
+                                if (rp < (uint32_t)k) hist[rp * 32 + lane] += qa;
+                            }
+                        }
+                    }
+                }
+            } else {
+                for (int a = lane; a < m; a += 32) {
+                    const uint32_t rs = row[2 * a], rp = row[2 * a + 1];
+                    const unsigned long long qa = qs[a];
+                    if (rs < (uint32_t)k) hist[rs * 32 + lane] += qa;
+                    if (rp < (uint32_t)k) hist[rp * 32 + lane] += qa;
+                }
+            }
+            __syncwarp();
+            if (lane < k) {
+                const unsigned long long* h = hist + lane * 32;
+#pragma unroll 8
+                for (int l = 0; l < 32; ++l) Q += h[l];
+            }
+            __syncwarp();
+        }
+        bool flag = false;
+        if (lane < k) {
+            const size_t e = (size_t)i * k + lane;
+            const double tau = __dadd_rn(tau0, __dmul_rn(__ull2double_rn(Q), 0x1.0p-32));
+            const double wv = __dmul_rn(powr(tau, alpha), etab[e]);
+            const float w32 = __double2float_rn(wv);
+            if (!isfinite(wv)) atomicOr(errflag, DEVERR_NONFINITE);
+            flag = !(w32 >= FLT_MIN && w32 <= FLT_MAX);
+            W64[e] = wv;
+            candw[e].w = w32;
+        }
+        const unsigned fl = __ballot_sync(FULL, flag);
+        if (lane == 0) rowflag[i] = fl ? 1 : 0;
+    }
+}
+
+static aco_status launch_rebuild(aco_instance* inst, int use_ants) {
+    const aco_params& p = inst->p;
+    const int warps = 8;
+    const size_t smem = sizeof(unsigned long long) * ((size_t)p.m + (size_t)warps * p.k * 32);
+    const int blocks = (int)fmin((double)inst->num_sms * 4, (double)ceil_div(p.n, warps));
+    const bool vec = (p.m % 8) == 0;
+    if (vec) {
+        cudaFuncSetAttribute(rebuild_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        rebuild_kernel<true><<<blocks, 32 * warps, smem, inst->stream>>>(p.n, p.m, p.k, p.tau0, p.alpha, use_ants,
+                                                                        inst->nbrank, inst->q, inst->etab, inst->candw,
+                                                                        inst->W64, inst->rowflag, inst->errflag);
+    } else {
+        cudaFuncSetAttribute(rebuild_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        rebuild_kernel<false><<<blocks, 32 * warps, smem, inst->stream>>>(p.n, p.m, p.k, p.tau0, p.alpha, use_ants,
+                                                                         inst->nbrank, inst->q, inst->etab,
+                                                                         inst->candw, inst->W64, inst->rowflag,
+                                                                         inst->errflag);
+    }
+    return check_launch(inst, "rebuild_kernel");
+}
+
+__global__ void fill_inf_kernel(double* __restrict__ v, int count) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) v[i] = INFINITY;
+}
+
+aco_status launch_lbest_init_weights(aco_instance* inst) {
+    // C_lbest = +inf: the first tour of every ant is accepted (Algorithm 1, initial tours)
+    fill_inf_kernel<<<ceil_div(inst->p.m, 256), 256, 0, inst->stream>>>(inst->clen, inst->p.m);
+    fill_inf_kernel<<<1, 32, 0, inst->stream>>>(inst->gbest, 1);
+    aco_status st = check_launch(inst, "fill_inf_kernel");
+    if (st != ACO_OK) return st;
+    return launch_rebuild(inst, 0);
+}
+
+aco_status launch_update_lbest(aco_instance* inst) {
+    const aco_params& p = inst->p;
+    commit_kernel<<<p.m, 32, 0, inst->stream>>>(p.n, p.m, p.k, inst->cand, inst->lbest, inst->nb, inst->nbrank,
+                                                 inst->seg, inst->antit, inst->clen, inst->cfix, inst->counters);
+    aco_status st = check_launch(inst, "commit_kernel");
+    if (st != ACO_OK) return st;
+    gbest_q_kernel<<<1, 1024, 0, inst->stream>>>(p.m, inst->clen, inst->gbest, inst->gbest_ant, inst->q, 0);
+    st = check_launch(inst, "gbest_q_kernel");
+    if (st != ACO_OK) return st;
+    return launch_rebuild(inst, 1);
+}
+
+// ------------------------------------------------------------------ exact tour lengths
+__global__ void tour_length_kernel(const double* __restrict__ xy, const int* __restrict__ tours, int n, int count,
+                                   double* __restrict__ out_len, unsigned long long* __restrict__ out_fix,
+                                   int* __restrict__ errflag) {
+    __shared__ unsigned long long red[2][32];
+    for (int c = blockIdx.x; c < count; c += gridDim.x) {
+        const int* T = tours + (size_t)c * n;
+        u128 acc = 0;
+        bool bad = false;
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            const int i = T[p], j = T[p + 1 == n ? 0 : p + 1];
+            if ((unsigned)i >= (unsigned)n || (unsigned)j >= (unsigned)n) { bad = true; continue; }
+            acc += len_to_fix(__dsqrt_rn(dist2(xy[2 * i], xy[2 * i + 1], xy[2 * j], xy[2 * j + 1])));
+        }
+        if (bad) atomicOr(errflag, DEVERR_BAD_TOUR);
+        acc = warp_sum_u128(acc);
+        const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+        if (l == 0) { red[0][w] = (unsigned long long)acc; red[1][w] = (unsigned long long)(acc >> 64); }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            u128 t = 0;
+            for (int v = 0; v < (int)(blockDim.x >> 5); ++v) t += (((u128)red[1][v]) << 64) | red[0][v];
+            out_len[c] = fix_to_len(t);
+            if (out_fix) { out_fix[2 * c] = (unsigned long long)t; out_fix[2 * c + 1] = (unsigned long long)(t >> 64); }
+        }
+        __syncthreads();
+    }
+}
+
+aco_status launch_tour_lengths(aco_instance* inst, const int32_t* tours, int32_t count, double* out) {
+    const int blocks = (int)fmin((double)count, (double)inst->num_sms * 8);
+    tour_length_kernel<<<blocks, 256, 0, inst->stream>>>(inst->xy, tours, inst->p.n, count, out, nullptr,
+                                                         inst->errflag);
+    return check_launch(inst, "tour_length_kernel");
+}
+
+// ------------------------------------------------------------------ checkpoint restore
+__global__ void neighbours_all_kernel(int n, int m, int k, const int* __restrict__ cand,
+                                      const int* __restrict__ lbest, int* __restrict__ nb,
+                                      uint8_t* __restrict__ nbrank) {
+    const long long total = (long long)n * m;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(e / n), t = (int)(e % n);
+        const int* L = lbest + (size_t)a * n;
+        set_neighbours(nb, nbrank, cand, m, k, a, L[t], L[t + 1 == n ? 0 : t + 1], L[t == 0 ? n - 1 : t - 1]);
+    }
+}
+
+aco_status launch_set_lbest(aco_instance* inst, const int32_t* lbest) {
+    const aco_params& p = inst->p;
+    cudaStream_t s = inst->stream;
+    cudaMemcpyAsync(inst->lbest, lbest, sizeof(int32_t) * (size_t)p.m * p.n, cudaMemcpyDeviceToDevice, s);
+    tour_length_kernel<<<(int)fmin((double)p.m, (double)inst->num_sms * 8), 256, 0, s>>>(
+        inst->xy, inst->lbest, p.n, p.m, inst->clen, inst->cfix, inst->errflag);
+    const long long total = (long long)p.n * p.m;
+    neighbours_all_kernel<<<(int)fmin((double)inst->num_sms * 16, (double)ceil_div(total, 256)), 256, 0, s>>>(
+        p.n, p.m, p.k, inst->cand, inst->lbest, inst->nb, inst->nbrank);
+    aco_status st = check_launch(inst, "set_lbest");
+    if (st != ACO_OK) return st;
+    gbest_q_kernel<<<1, 1024, 0, s>>>(p.m, inst->clen, inst->gbest, inst->gbest_ant, inst->q, 0);
+    st = check_launch(inst, "gbest_q_kernel");
+    if (st != ACO_OK) return st;
+    return launch_rebuild(inst, 1);
+}
+
+// ------------------------------------------------------------------ dense mode (Section 2)
+// One warp per row: W = tau^alpha eta^beta, FP32 copy, row flag.
+__global__ void dense_weights_kernel(int n, double alpha, const double* __restrict__ tau,
+                                     const double* __restrict__ etab_d, double* __restrict__ W64,
+                                     float* __restrict__ W32, uint8_t* __restrict__ rowflag,
+                                     int* __restrict__ errflag) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        bool flag = false;
+        for (int j = lane; j < n; j += 32) {
+            const size_t e = (size_t)i * n + j;
+            double w = 0.0;
+            if (j != i) {
+                w = __dmul_rn(powr(tau[e], alpha), etab_d[e]);
+                if (!isfinite(w)) atomicOr(errflag, DEVERR_NONFINITE);
+            }
+            const float w32 = __double2float_rn(w);
+            if (j != i) flag |= !(w32 >= FLT_MIN && w32 <= FLT_MAX);
+            W64[e] = w;
+            W32[e] = w32;
+        }
+        const unsigned fl = __ballot_sync(FULL, flag);
+        if (lane == 0) rowflag[i] = fl ? 1 : 0;
+    }
+}
+
+aco_status launch_dense_init(aco_instance* inst) {
+    const int n = inst->p.n;
+    const int blocks = (int)fmin((double)inst->num_sms * 4, (double)ceil_div(n, 8));
+    dense_weights_kernel<<<blocks, 256, 0, inst->stream>>>(n, inst->p.alpha, inst->tau, inst->etab_d, inst->W64d,
+                                                            inst->W32d, inst->rowflag, inst->errflag);
+    if (!inst->initialized) fill_inf_kernel<<<1, 32, 0, inst->stream>>>(inst->gbest, 1);
+    return check_launch(inst, "dense_weights_kernel");
+}
+
+__global__ void succ_pred_kernel(int n, int m, const int* __restrict__ tours, int* __restrict__ succ,
+                                 int* __restrict__ pred) {
+    const long long total = (long long)n * m;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(e / n), t = (int)(e % n);
+        const int* T = tours + (size_t)a * n;
+        const int c = T[t];
+        succ[(size_t)a * n + c] = T[t + 1 == n ? 0 : t + 1];
+        pred[(size_t)a * n + c] = T[t == 0 ? n - 1 : t - 1];
+    }
+}
+
+// Eq. 2 then Eq. 3-5 for every ordered pair (i, j), i != j; the deposit sum runs over ants in
+// index order.
+__global__ void dense_tau_kernel(int n, int m, double keep, const int* __restrict__ succ,
+                                 const int* __restrict__ pred, const double* __restrict__ clen,
+                                 double* __restrict__ tau) {
+    const long long total = (long long)n * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        const double ev = __dmul_rn(keep, tau[e]);
+        if (i == j) {  // Eq. 2 applies to every entry; the diagonal receives no deposit
+            tau[e] = ev;
+            continue;
+        }
+        double s = 0.0;
+        for (int a = 0; a < m; ++a) {
+            const size_t o = (size_t)a * n + i;
+            if (succ[o] == j || pred[o] == j) s = __dadd_rn(s, __ddiv_rn(1.0, clen[a]));
+        }
+        tau[e] = __dadd_rn(ev, s);
+    }
+}
+
+aco_status launch_update_dense(aco_instance* inst) {
+    const aco_params& p = inst->p;
+    cudaStream_t s = inst->stream;
+    const long long nm = (long long)p.n * p.m, nn = (long long)p.n * p.n;
+    succ_pred_kernel<<<(int)fmin((double)inst->num_sms * 8, (double)ceil_div(nm, 256)), 256, 0, s>>>(
+        p.n, p.m, inst->tours, inst->succ_d, inst->pred_d);
+    const double keep = 1.0 - p.rho;
+    dense_tau_kernel<<<(int)fmin((double)inst->num_sms * 8, (double)ceil_div(nn, 256)), 256, 0, s>>>(
+        p.n, p.m, keep, inst->succ_d, inst->pred_d, inst->clen, inst->tau);
+    gbest_q_kernel<<<1, 1024, 0, s>>>(p.m, inst->clen, inst->gbest, inst->gbest_ant, nullptr, 1);
+    aco_status st = check_launch(inst, "dense update");
+    if (st != ACO_OK) return st;
+    const int blocks = (int)fmin((double)inst->num_sms * 4, (double)ceil_div(p.n, 8));
+    dense_weights_kernel<<<blocks, 256, 0, s>>>(p.n, p.alpha, inst->tau, inst->etab_d, inst->W64d, inst->W32d,
+                                                inst->rowflag, inst->errflag);
+    // counts the tours deposited this iteration
+    return check_launch(inst, "dense_weights_kernel");
+}
+
+// ------------------------------------------------------------------ diagnostic: Eq. 1 probabilities
+__global__ void step_probs_kernel(int mode, int n, int k, int city, const uint32_t* __restrict__ bits,
+                                  const CandW* __restrict__ candw, const float* __restrict__ W32d,
+                                  float* __restrict__ probs, int* __restrict__ exhausted) {
+    const int lane = threadIdx.x;
+    if (mode == ACO_MODE_LBEST_PARTIAL) {
+        bool feas = false;
+        float w = 0.f;
+        if (lane < k) {
+            const CandW e = candw[(size_t)city * k + lane];
+            feas = !((bits[e.city >> 5] >> (e.city & 31)) & 1u);
+            w = feas ? e.w : 0.f;
+        }
+        float S = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            const float v = __shfl_up_sync(FULL, S, o);
+            if (lane >= o) S = __fadd_rn(S, v);
+        }
+        const float T = __shfl_sync(FULL, S, 31);
+        const unsigned fm = __ballot_sync(FULL, feas);
+        if (lane < k) probs[lane] = fm ? __fdiv_rn(w, T) : 0.f;
+        if (lane == 0) *exhausted = fm ? 0 : 1;
+    } else {
+        float s = 0.f;
+        for (int j = lane; j < n; j += 32)
+            if (!((bits[j >> 5] >> (j & 31)) & 1u)) s = __fadd_rn(s, W32d[(size_t)city * n + j]);
+        for (int o = 16; o; o >>= 1) s = __fadd_rn(s, __shfl_xor_sync(FULL, s, o));
+        for (int j = lane; j < n; j += 32) {
+            const bool v = (bits[j >> 5] >> (j & 31)) & 1u;
+            probs[j] = v ? 0.f : __fdiv_rn(W32d[(size_t)city * n + j], s);
+        }
+        if (lane == 0) *exhausted = 0;
+    }
+}
+
+aco_status launch_step_probs(aco_instance* inst, int32_t city, const uint32_t* bits, float* probs, int32_t* exhausted) {
+    step_probs_kernel<<<1, 32, 0, inst->stream>>>(inst->p.mode, inst->p.n, inst->p.k, city, bits, inst->candw,
+                                                  inst->W32d, probs, exhausted);
+    return check_launch(inst, "step_probs_kernel");
+}

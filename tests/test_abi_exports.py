@@ -1,0 +1,65 @@
+"""The C-ABI library builds, loads and exports every entry point include/aco.h declares (no GPU)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "aco.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(aco_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ["aco_create_instance", "aco_build_candidates", "aco_construct_tours", "aco_update_pheromone",
+                     "aco_tour_lengths", "aco_destroy_instance"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1709_03187_gb300 import build
+
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_python_binding_has_every_entry_point():
+    import paper_1709_03187_gb300 as pkg
+
+    for n in _declared():
+        if n in ("aco_status_string", "aco_last_error"):
+            continue
+        assert hasattr(pkg, n), n
+
+
+def test_struct_layouts_match_ctypes(tmp_path):
+    """sizeof/offsetof of the ABI structs as a C compiler sees the header == the binding's."""
+    from paper_1709_03187_gb300._ffi import Params, Stats
+
+    prog = tmp_path / "sz.c"
+    prog.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "aco.h"\n'
+                    'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(aco_params), sizeof(aco_stats),'
+                    ' offsetof(aco_params, seed), offsetof(aco_params, fallback), offsetof(aco_stats, gbest));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert out == [ctypes.sizeof(Params), ctypes.sizeof(Stats), Params.seed.offset, Params.fallback.offset,
+                   Stats.gbest.offset]
+
+
+def test_status_strings_without_gpu():
+    from paper_1709_03187_gb300 import build
+
+    lib = ctypes.CDLL(build.build())
+    lib.aco_status_string.restype = ctypes.c_char_p
+    assert lib.aco_status_string(0) == b"ok"
+    assert lib.aco_status_string(1) == b"invalid argument"
