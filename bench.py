@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Benchmark: PartialACO iterations on the 200,000-city clustered workload on GB300s.
+
+One step = one ACO iteration of the whole colony (1024 ants): tour construction (PartialACO
+rebuild of at most 1% of every ant's l_best by Eq. 1 over 16-nearest candidate lists) and the
+pheromone update (l_best commit, C_gbest, candidate-edge pheromone rebuild).  Setup (candidate
+lists, initial tours) is untimed.  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs an independent replica colony (seed + rank): the workload is one
+instance and the method has no exchange step at this scale, so the N-GPU figure is weak-scaled
+replica throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import aco_synth  # noqa: E402
+
+METRIC = "city decisions/s and ACO iterations/s at n=200K on 1 GB300; % of mem roofline"
+L2_FLUSH_BYTES = 512 << 20  # > 126 MB L2
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="lbest200k", choices=sorted(aco_synth.WORKLOADS))
+    ap.add_argument("--ants", type=int, default=0, help="override m (profiling of smaller cases)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=32, help="ants in the oracle's timed sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.15)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for ln in f:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ algorithmic bytes
+def construct_bytes(decisions: int, k: int, m: int) -> int:
+    """Algorithmic bytes of one construction launch.
+
+    Per decision: the candidate row (k x (4 B city + 4 B FP32 weight)) and the 4 B segment write.
+    Per rebuilt city: its old l_best entry (bitset set-up, 4 B), the new segment read back (4 B)
+    and one coordinate pair for each of the old and the new path (2 x 16 B).  Per ant: the two
+    closing coordinate pairs of each path (64 B).
+    """
+    return decisions * (8 * k + 4) + decisions * (4 + 4 + 32) + 64 * m
+
+
+def rebuild_bytes(n: int, m: int, k: int) -> int:
+    """Algorithmic bytes of one pheromone rebuild: the n x m table of neighbour ranks (2 B per
+    city and ant), eta^beta in (8 B), FP64 weight out (8 B) and FP32 weight out (4 B) per
+    candidate edge, and the m per-ant weights (8 B)."""
+    return 2 * n * m + n * k * (8 + 8 + 4) + 8 * m
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1709_03187_gb300 import Colony
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    wl = aco_synth.WORKLOADS[args.workload]
+    params = dict(wl["params"])
+    if args.ants:
+        params["m"] = args.ants
+    params["seed"] = int(params["seed"]) + rank
+    n, m, k = params["n"], params["m"], params["k"]
+    xy = aco_synth.make(args.workload)
+    stream = torch.cuda.Stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    t0 = time.perf_counter()
+    col = Colony(xy, stream=stream, **params)
+    col.build_candidates()
+    col.iterate(0)  # Algorithm 1: initial tours
+    s0 = col.stats()
+    setup_s = time.perf_counter() - t0
+    it = 1
+    for _ in range(args.warmup):
+        col.iterate(it)
+        it += 1
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    evs = [(E(), E(), E()) for _ in range(args.steps)]
+    barrier()
+    st_before = col.stats()
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    with torch.cuda.stream(stream):
+        for (e0, e1, e2) in evs:
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+            e0.record(stream)
+            col.construct(it)
+            e1.record(stream)
+            col.update()
+            e2.record(stream)
+            it += 1
+    barrier()
+    clocks = sampler.stop()
+    st_after = col.stats()
+    t_con = sum(a.elapsed_time(b) for a, b, _ in evs) / 1e3
+    t_upd = sum(b.elapsed_time(c) for _, b, c in evs) / 1e3
+    t_step = t_con + t_upd
+    decisions = st_after["decisions"] - st_before["decisions"]
+    if world > 1:
+        tt = torch.tensor([t_step], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dd = torch.tensor([decisions], dtype=torch.float64, device="cuda")
+        dist.all_reduce(dd, op=dist.ReduceOp.SUM)
+        t_max, dec_all = float(tt.item()), float(dd.item())
+    else:
+        t_max, dec_all = t_step, float(decisions)
+    value = dec_all / t_max
+    its = args.steps * world / t_max
+
+    hbm_peak, peak_kind = read_peaks()
+    launches = args.steps
+    c_bytes = construct_bytes(decisions, k, m) / launches
+    r_bytes = rebuild_bytes(n, m, k)
+    c_avg = t_con / launches
+    u_avg = t_upd / launches
+    kernels = {
+        "construct_lbest_kernel": {"avg_ms": c_avg * 1e3, "alg_bytes": c_bytes,
+                                   "achieved_gbs": c_bytes / c_avg / 1e9},
+        "update (commit + gbest_q + rebuild)": {"avg_ms": u_avg * 1e3, "alg_bytes": r_bytes,
+                                                "achieved_gbs": r_bytes / u_avg / 1e9},
+    }
+    dom = "construct_lbest_kernel" if c_avg >= u_avg else "update (commit + gbest_q + rebuild)"
+    ach = kernels[dom]["achieved_gbs"]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 2), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(ach / hbm_peak, 5), "peak_source": f"{peak_kind} hbm_gbs", "traffic": None,
+                "kernels": {kn: {kk: round(v, 4) for kk, v in kv.items()} for kn, kv in kernels.items()}}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, xy, params, stream)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload.startswith("lbest"):
+        cpu = cpu_baseline_from_state(col, xy, params, it, args.cpu_sample)
+    col.close()
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "decisions/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_max / args.steps * 1e3, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "iterations_per_s": round(its, 2),
+        "config": {"workload": f"{args.workload}: n={n} clustered (200 Gaussian clusters, sigma=0.005), k={k}, m={m}, "
+                               f"f={params['max_mod_frac']}, alpha={params['alpha']}, beta={params['beta']}, "
+                               f"tau0={params['tau0']}, p_partial={params['p_partial']}",
+                   "n": n, "m": m, "k": k, "parallelism": f"replicas x{world}" if world > 1 else "single colony",
+                   "l2": "flushed (512 MB write) before every timed step, outside the events",
+                   "decisions_per_step": decisions / args.steps,
+                   "fallbacks_per_step": (st_after["fallbacks"] - st_before["fallbacks"]) / args.steps,
+                   "exact_resolves_per_step": (st_after["exact_resolves"] - st_before["exact_resolves"]) / args.steps,
+                   "improved_per_step": (st_after["improved"] - st_before["improved"]) / args.steps,
+                   "setup_s": round(setup_s, 3), "setup_decisions": s0["decisions"],
+                   "gbest_after": st_after["gbest"]},
+        "roofline": roofline,
+        "clocks": clocks,
+        "gpu_launches": 4 * args.steps,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, xy, params, stream):
+    """The same metric through the public API from host buffers: pinned coordinates copied in,
+    candidate lists, initial tours and `steps` iterations, C_gbest read back every step and the
+    best tour read back at the end.  Decisions of the whole solve / wall time."""
+    import torch
+
+    from paper_1709_03187_gb300 import Colony
+
+    host = torch.from_numpy(xy).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        dev = host.to("cuda", non_blocking=True)
+    stream.synchronize()
+    col = Colony(dev, stream=stream, **params)
+    col.build_candidates()
+    gb = []
+    for it in range(args.steps + 1):
+        col.iterate(it)
+        gb.append(col.stats()["gbest"])  # device -> host read of the step's result (8 B)
+    st = col.stats()
+    lb, cl, _ = col.state()
+    best = lb[st["gbest_ant"]].cpu()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    col.close()
+    del best
+    return {"value": round(st["decisions"] / wall, 1), "unit": "decisions/s",
+            "h2d_bytes_per_step": round(host.numel() * 8 / (args.steps + 1), 1),
+            "d2h_bytes_per_step": round(8 + 4 * params["n"] / (args.steps + 1), 1),
+            "wall_s": round(wall, 3), "iterations": args.steps + 1,
+            "note": "includes instance creation, candidate lists and the initial tours"}
+
+
+def cpu_baseline_from_state(col, xy, params, iteration, sample):
+    """The oracle timed on this host: one PartialACO iteration of `sample` ants of the same
+    colony (its l_best state taken after the GPU warm-up), with the pheromone rebuild over all m
+    ants; projected to the full colony as t_rebuild + (m / sample) * t_construct."""
+    import oracle
+
+    lb, cl, _ = col.state()
+    lb = lb.cpu().numpy()
+    n, m, k = params["n"], params["m"], params["k"]
+    cand = oracle.knn_sweep(xy, k)
+    ref = oracle.Oracle(xy, cand=cand, **{kk: v for kk, v in params.items()})
+    ref.set_lbest(lb, cl.cpu().numpy())
+    t0 = time.perf_counter()
+    ref.construct(iteration, ants=[])
+    t_rb = time.perf_counter() - t0
+    ants = np.random.default_rng(0).choice(m, size=min(sample, m), replace=False).astype(np.int32)
+    ref.reset_counters()
+    t0 = time.perf_counter()
+    ref.construct(iteration, ants=ants, rebuild=False)
+    t_cs = max(time.perf_counter() - t0, 1e-9)
+    dec = ref.counters()["decisions"]
+    full_dec = dec * m / ants.size
+    full_t = t_rb + t_cs * m / ants.size
+    return {"value": round(full_dec / full_t, 1), "unit": "decisions/s", "cores": 1, "kind": "oracle",
+            "sample": f"one iteration (iteration {iteration}) of {ants.size} of the {m} ants from the colony's "
+                      f"state after warm-up, plus the full pheromone rebuild ({t_rb:.2f} s); projected "
+                      f"t_rebuild + (m/sample) t_construct = {full_t:.2f} s for {full_dec:.0f} decisions",
+            "iterations_per_s": round(1.0 / full_t, 5)}
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    wl = aco_synth.WORKLOADS[args.workload]
+    params = dict(wl["params"])
+    n, m, k = params["n"], params["m"], params["k"]
+    xy = aco_synth.make(args.workload)
+    t0 = time.perf_counter()
+    cand = oracle.knn_sweep(xy, k) if params["mode"] == 1 else None
+    if params["mode"] == 1:
+        ref = oracle.Oracle(xy, cand=cand, **params)
+        seeds = 2
+        ref.construct(0, ants=np.arange(seeds, dtype=np.int32))  # oracle-built initial tours
+        T = ref.newtours[:seeds]
+        lb = np.ascontiguousarray(T[np.arange(m) % seeds])
+        ref.set_lbest(lb, oracle.tour_lengths(xy, lb))
+        t1 = time.perf_counter()
+        ref.construct(1, ants=[])
+        t_rb = time.perf_counter() - t1
+    else:
+        ref = oracle.Oracle(xy, **params)
+        t_rb = 0.0
+    setup = time.perf_counter() - t0
+    sample = max(1, min(args.cpu_sample, 4, 150 // max(1, args.warmup + args.steps)))
+    rng = np.random.default_rng(1)
+    per = []
+    for step in range(args.warmup + args.steps):
+        if params["mode"] == 1:
+            ants = rng.choice(m, size=sample, replace=False).astype(np.int32)
+            ref.reset_counters()
+            t1 = time.perf_counter()
+            ref.construct(step + 2, ants=ants, rebuild=False)
+            t_cs = max(time.perf_counter() - t1, 1e-9)
+            dec = ref.counters()["decisions"]
+            # the rebuild (measured once in set-up) plus the sampled ants projected to the colony
+            t_full = t_rb + t_cs * m / sample
+            per.append((dec * m / sample, t_full))
+        else:
+            ref.reset_counters()
+            t1 = time.perf_counter()
+            ref.iterate(step)
+            per.append((ref.counters()["decisions"], time.perf_counter() - t1))
+    timed = per[args.warmup:]
+    dec = sum(d for d, _ in timed)
+    tt = sum(t for _, t in timed)
+    value = dec / tt
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "decisions/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tt / max(1, len(timed)) * 1e3, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "n": n, "m": m, "k": k},
+           "cpu_baseline": {"value": round(value, 1), "unit": "decisions/s", "cores": 1, "kind": "oracle",
+                            "sample": f"each step: {sample} random ants of the {m}-ant colony (initial tours built "
+                                      f"by the oracle for 2 ants, repeated), pheromone rebuild over all ants "
+                                      f"({t_rb:.2f} s, measured once); step time projected as t_rebuild + "
+                                      f"(m/sample) t_construct; setup {setup:.1f} s"},
+           "e2e": {"value": round(value, 1), "unit": "decisions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

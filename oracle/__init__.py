@@ -74,6 +74,7 @@ def lib():
             "or_create": (P, [ctypes.POINTER(Params), f64p]),
             "or_destroy": (None, [P]),
             "or_construct": (None, [P, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
+            "or_construct_ex": (None, [P, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
             "or_update": (None, [P]),
             "or_get_lbest": (None, [P, i32p]),
             "or_get_clen": (None, [P, f64p]),
@@ -90,6 +91,9 @@ def lib():
             "or_cand_weights": (None, [P, f64p, u64p, u64p]),
             "or_set_lbest": (None, [P, i32p, f64p]),
             "or_step_probs": (ctypes.c_int, [P, ctypes.c_int, u8p, f64p]),
+            "or_knn_one": (None, [ctypes.c_int, f64p, ctypes.c_int, ctypes.c_int, i32p]),
+            "or_knn_sweep": (ctypes.c_int, [ctypes.c_int, f64p, ctypes.c_int, i32p]),
+            "or_create_with_cand": (P, [ctypes.POINTER(Params), f64p, i32p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -144,18 +148,42 @@ def knn(xy: np.ndarray, k: int) -> np.ndarray:
     return cand
 
 
+def knn_one(xy: np.ndarray, k: int, i: int) -> np.ndarray:
+    """Candidate list of city i by brute force (sampled checks at large n)."""
+    xy = np.ascontiguousarray(xy, np.float64)
+    row = np.zeros(k, np.int32)
+    lib().or_knn_one(xy.shape[0], xy, k, i, row)
+    return row
+
+
+def knn_sweep(xy: np.ndarray, k: int) -> np.ndarray:
+    """Exact candidate lists by an x-sweep (same keys and result as ``knn``; fast at large n)."""
+    xy = np.ascontiguousarray(xy, np.float64)
+    cand = np.zeros((xy.shape[0], k), np.int32)
+    if lib().or_knn_sweep(xy.shape[0], xy, k, cand) != 0:
+        raise ValueError("coincident cities")
+    return cand
+
+
 # ------------------------------------------------------------------ solver
 class Oracle:
-    """One colony: dense Section 2 ACO (mode 0) or the Section 3 l_best/PartialACO form (mode 1)."""
+    """One colony: dense Section 2 ACO (mode 0) or the Section 3 l_best/PartialACO form (mode 1).
+
+    ``cand`` (mode 1 only) supplies precomputed candidate lists (from ``knn`` or ``knn_sweep``)
+    instead of the O(n^2) brute force inside the oracle.
+    """
 
     def __init__(self, xy: np.ndarray, *, mode: int, n: int, m: int, k: int = 0, alpha: float = 1.0,
                  beta: float = 2.0, rho: float = 0.5, tau0: float = 1.0, max_mod_frac: float = 1.0,
-                 p_partial: float = 1.0, seed: int = 1, fallback: int = 0):
+                 p_partial: float = 1.0, seed: int = 1, fallback: int = 0, cand=None):
         self.xy = np.ascontiguousarray(xy, np.float64)
         assert self.xy.shape == (n, 2)
         self.p = Params(mode, n, m, k, alpha, beta, rho, tau0, max_mod_frac, p_partial, seed, fallback, 0)
         self.n, self.m, self.k, self.mode = n, m, k, mode
-        self._h = lib().or_create(ctypes.byref(self.p), self.xy)
+        if cand is not None:
+            self._h = lib().or_create_with_cand(ctypes.byref(self.p), self.xy, np.ascontiguousarray(cand, np.int32))
+        else:
+            self._h = lib().or_create(ctypes.byref(self.p), self.xy)
         if not self._h:
             raise ValueError("oracle rejected the instance (n < 3, bad k or coincident cities)")
 
@@ -165,12 +193,14 @@ class Oracle:
             lib().or_destroy(h)
             self._h = None
 
-    def construct(self, iteration: int, ants=None):
+    def construct(self, iteration: int, ants=None, rebuild: bool = True):
+        """Build new tours (all ants, or the listed ones).  rebuild=False reuses the pheromone of
+        the previous call (valid while the l_best population is unchanged)."""
         if ants is None:
-            lib().or_construct(self._h, iteration, None, 0)
+            lib().or_construct_ex(self._h, iteration, None, 0, int(rebuild))
         else:
             a = np.ascontiguousarray(ants, np.int32)
-            lib().or_construct(self._h, iteration, a.ctypes.data_as(ctypes.c_void_p), a.size)
+            lib().or_construct_ex(self._h, iteration, a.ctypes.data_as(ctypes.c_void_p), a.size, int(rebuild))
 
     def update(self):
         lib().or_update(self._h)

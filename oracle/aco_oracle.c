@@ -443,10 +443,11 @@ static void build_partial(or_state* st, int a, uint32_t iteration) {
     st->seg_M[a] = M;
 }
 
-/* Tour construction for every ant (ants == NULL) or for the listed ants only. */
-void or_construct(or_state* st, int iteration, const int32_t* ants, int count) {
+/* Tour construction for every ant (ants == NULL) or for the listed ants only.  rebuild = 0
+ * reuses the pheromone computed by the previous call (same l_best population). */
+void or_construct_ex(or_state* st, int iteration, const int32_t* ants, int count, int rebuild) {
     int m = st->p.m;
-    if (st->p.mode == 1) lbest_pheromone(st);
+    if (st->p.mode == 1 && rebuild) lbest_pheromone(st);
     if (!ants) count = m;
     memset(st->built, 0, sizeof(int32_t) * (size_t)m);
     for (int c = 0; c < count; ++c) {
@@ -465,6 +466,10 @@ void or_construct(or_state* st, int iteration, const int32_t* ants, int count) {
         st->newlen[a] = or_tour_length(st->p.n, st->xy, st->newtour + (size_t)a * st->p.n);
         st->built[a] = 1;
     }
+}
+
+void or_construct(or_state* st, int iteration, const int32_t* ants, int count) {
+    or_construct_ex(st, iteration, ants, count, 1);
 }
 
 /* Pheromone update.  Dense: Eq. 2 then Eq. 3-5 with every ant's new tour.
@@ -581,4 +586,110 @@ int or_step_probs(or_state* st, int i, const unsigned char* visited, double* out
     if (total == 0.0) return 1;
     for (int r = 0; r < k; ++r) out[r] = out[r] / total;
     return 0;
+}
+
+/* ------------------------------------------------------------------ large-n helpers */
+/* Candidate list of one city by brute force (the definition), for sampled checks at large n. */
+void or_knn_one(int n, const double* xy, int k, int i, int32_t* row) {
+    double kd[64];
+    int filled = 0;
+    for (int j = 0; j < n; ++j) {
+        if (j == i) continue;
+        double d2 = or_dist2(xy, i, j);
+        if (filled == k && !(d2 < kd[k - 1])) continue;
+        int pos = filled < k ? filled : k - 1;
+        while (pos > 0 && d2 < kd[pos - 1]) {
+            kd[pos] = kd[pos - 1];
+            row[pos] = row[pos - 1];
+            --pos;
+        }
+        kd[pos] = d2;
+        row[pos] = j;
+        if (filled < k) ++filled;
+    }
+}
+
+/* The same lists by an x-sweep: cities sorted by x; from each city scan outwards in x order and
+ * stop a direction once dx*dx exceeds the k-th best d^2 (d^2 >= dx*dx, so nothing further can
+ * enter).  Keys (d^2, j) as in or_knn; results identical.  O(n log n + n * slab). */
+static const double* g_sort_xy;
+static int cmp_x(const void* a, const void* b) {
+    int ia = *(const int*)a, ib = *(const int*)b;
+    double xa = g_sort_xy[2 * ia], xb = g_sort_xy[2 * ib];
+    if (xa < xb) return -1;
+    if (xa > xb) return 1;
+    return ia < ib ? -1 : (ia > ib);
+}
+
+static void keep_best(double* kd, int32_t* row, int* filled, int k, double d2, int j) {
+    if (*filled == k && !(d2 < kd[k - 1] || (d2 == kd[k - 1] && j < row[k - 1]))) return;
+    int pos = *filled < k ? *filled : k - 1;
+    while (pos > 0 && (d2 < kd[pos - 1] || (d2 == kd[pos - 1] && j < row[pos - 1]))) {
+        kd[pos] = kd[pos - 1];
+        row[pos] = row[pos - 1];
+        --pos;
+    }
+    kd[pos] = d2;
+    row[pos] = j;
+    if (*filled < k) ++*filled;
+}
+
+int or_knn_sweep(int n, const double* xy, int k, int32_t* cand) {
+    int* order = (int*)malloc(sizeof(int) * (size_t)n);
+    int* where = (int*)malloc(sizeof(int) * (size_t)n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    g_sort_xy = xy;
+    qsort(order, (size_t)n, sizeof(int), cmp_x);
+    for (int p = 0; p < n; ++p) where[order[p]] = p;
+    int dup = 0;
+    double kd[64];
+    for (int i = 0; i < n; ++i) {
+        int32_t* row = cand + (size_t)i * k;
+        int filled = 0;
+        int p0 = where[i];
+        for (int dir = -1; dir <= 1; dir += 2) {
+            for (int p = p0 + dir; p >= 0 && p < n; p += dir) {
+                int j = order[p];
+                double dx = xy[2 * i] - xy[2 * j];
+                if (filled == k && dx * dx > kd[k - 1]) break;
+                double d2 = or_dist2(xy, i, j);
+                if (d2 == 0.0) dup = 1;
+                keep_best(kd, row, &filled, k, d2, j);
+            }
+        }
+    }
+    free(order);
+    free(where);
+    return dup ? -1 : 0;
+}
+
+/* l_best-mode state from given candidate lists (skips the O(n^2) brute force at large n). */
+or_state* or_create_with_cand(const or_params* p, const double* xy, const int32_t* cand) {
+    if (p->mode != 1) return NULL;
+    if (p->n < 3 || p->m < 1 || p->k < 1 || p->k > 32 || p->k > p->n - 1) return NULL;
+    or_state* st = (or_state*)calloc(1, sizeof(or_state));
+    st->p = *p;
+    int n = p->n, m = p->m, k = p->k;
+    st->xy = (double*)malloc(sizeof(double) * 2 * (size_t)n);
+    memcpy(st->xy, xy, sizeof(double) * 2 * (size_t)n);
+    st->visited = (unsigned char*)malloc((size_t)n);
+    st->newtour = (int32_t*)malloc(sizeof(int32_t) * (size_t)m * n);
+    st->newlen = (double*)malloc(sizeof(double) * (size_t)m);
+    st->built = (int32_t*)calloc((size_t)m, sizeof(int32_t));
+    st->seg_s = (int32_t*)malloc(sizeof(int32_t) * (size_t)m);
+    st->seg_M = (int32_t*)malloc(sizeof(int32_t) * (size_t)m);
+    st->cand = (int32_t*)malloc(sizeof(int32_t) * (size_t)n * k);
+    memcpy(st->cand, cand, sizeof(int32_t) * (size_t)n * k);
+    st->etab = (double*)malloc(sizeof(double) * (size_t)n * k);
+    for (int i = 0; i < n; ++i)
+        for (int r = 0; r < k; ++r)
+            st->etab[(size_t)i * k + r] = eta_pow(st->xy, i, st->cand[(size_t)i * k + r], p->beta);
+    st->lbest = (int32_t*)calloc((size_t)m * n, sizeof(int32_t));
+    st->clen = (double*)malloc(sizeof(double) * (size_t)m);
+    for (int a = 0; a < m; ++a) st->clen[a] = INFINITY;
+    st->q = (uint64_t*)calloc((size_t)m, sizeof(uint64_t));
+    st->Q = (uint64_t*)calloc((size_t)n * k, sizeof(uint64_t));
+    st->succ = (int32_t*)malloc(sizeof(int32_t) * (size_t)m * n);
+    st->pred = (int32_t*)malloc(sizeof(int32_t) * (size_t)m * n);
+    return st;
 }

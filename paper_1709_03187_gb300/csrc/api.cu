@@ -48,7 +48,8 @@ static void free_all(aco_instance* inst) {
                     inst->cell_fill, inst->candw, inst->cand, inst->etab, inst->W64, inst->rowflag, inst->lbest,
                     inst->nb, inst->nbrank, inst->clen, inst->cfix, inst->q, inst->gbest, inst->gbest_ant,
                     inst->seg, inst->antit, inst->accq, inst->tau, inst->etab_d, inst->W64d, inst->W32d,
-                    inst->tours, inst->succ_d, inst->pred_d, inst->counters, inst->errflag};
+                    inst->tours, inst->succ_d, inst->pred_d, inst->counters, inst->errflag, inst->xy32,
+                    inst->ulist, inst->uxy};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -136,6 +137,14 @@ extern "C" aco_status aco_create_instance(const double* xy_dev, const aco_params
         ok &= dalloc(&inst->seg, m * n, &total);
         ok &= dalloc(&inst->antit, m, &total);
         ok &= dalloc(&inst->accq, m * n, &total);
+        long long fm = (long long)floor(p->max_mod_frac * (double)n);
+        long long pmin = n - fm;
+        if (pmin < 1) pmin = 1;
+        if (pmin > n - 1) pmin = n - 1;
+        inst->ucap = (int32_t)(n - pmin);
+        ok &= dalloc(&inst->ulist, m * inst->ucap, &total);
+        ok &= dalloc(&inst->uxy, m * inst->ucap, &total);
+        ok &= dalloc(&inst->xy32, n, &total);
     } else {
         ok &= dalloc(&inst->tau, n * n, &total);
         ok &= dalloc(&inst->etab_d, n * n, &total);
@@ -182,6 +191,7 @@ extern "C" aco_status aco_create_instance(const double* xy_dev, const aco_params
     }
     free(hxy);
     const double diag = hypot(xmax - xmin, ymax - ymin);
+    inst->coord_r = nextafterf((float)fmax(fmax(fabs(xmin), fabs(xmax)), fmax(fabs(ymin), fabs(ymax))), INFINITY);
     if (!finite || !(diag * (double)n < 1073741824.0)) {
         snprintf(g_create_err, sizeof(g_create_err), "coordinates must be finite with bbox diagonal * n < 2^30");
         free_all(inst);

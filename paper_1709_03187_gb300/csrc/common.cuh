@@ -221,6 +221,11 @@ struct aco_instance {
     int32_t* seg;          // m*n new cities of the iteration
     AntIter* antit;        // m
     unsigned long long* accq;  // m*n scratch of the exhausted-list rule (kept zero between uses)
+    float2* xy32;          // n FP32 coordinates (distance screen of the exhausted-list rule)
+    int32_t* ulist;        // m*ucap remaining discarded cities of each ant's partial rebuild
+    float2* uxy;           // m*ucap their FP32 coordinates
+    int32_t ucap;          // largest rebuilt count, n - max(1, n - floor(f n))
+    float coord_r;         // max |coordinate| (rounded up)
 
     // dense mode
     double* tau;           // n*n

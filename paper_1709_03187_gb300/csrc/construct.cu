@@ -8,28 +8,38 @@
 // u * total.  The FP32 screen is accepted only when u * total is at least 32 * 2^-24 * total
 // away from both bounding prefix sums, which is more than the worst-case FP32 error, so the
 // pick equals the FP64 sequential wheel's pick.  Otherwise (or when a row's weights are not
-// FP32-normal) the decision is re-evaluated exactly: the FP64 weights summed in rank order,
-// exactly as Eq. 1 is defined on the host side.
+// FP32-normal, marked by negative screen weights) the decision is re-evaluated exactly: the
+// FP64 weights summed in rank order, exactly as Eq. 1 is defined.  The rows of every unvisited
+// candidate are prefetched into L1 while the current decision is computed, so the next row is
+// usually an L1 hit.
 //
 // Exhausted list (every candidate visited): argmax over the unvisited cities of
 // tau_ij^alpha eta_ij^beta (ties to the lowest index), where tau_ij = tau0 + Q_ij 2^-32 and Q_ij
 // sums the weights of the ants whose l_best has edge (i,j) (read from the neighbour table of
-// city i).  In a partial rebuild the unvisited cities are the remaining discarded ones; in a
-// full construction the unboosted maximum is the nearest unvisited city, found exactly by a
-// ring search over the city grid.
+// city i).  For cities with Q_ij = 0 the weight only falls with d_ij, so:
+//   * partial rebuild: the remaining discarded cities sit in a compacted per-ant list with FP32
+//     coordinates; an FP32 distance screen with a rigorous error bound keeps the near-nearest
+//     cities, and only those get the exact FP64 weight;
+//   * full construction: the nearest unvisited city is found exactly by a ring search over the
+//     city grid;
+// and the few unvisited l_best neighbours of city i get their exact boosted weight.
 #include <float.h>
 #include <math.h>
 
 #include "common.cuh"
 
 #define FULL 0xffffffffu
+#define TOUCH_CAP 64
 
 struct LbestArgs {
     int n, m, k;
     double alpha, beta, tau0, f, p_partial;
     unsigned long long seed;
     int fallback, iteration, initialized;
+    int ucap;       // capacity of the per-ant remaining-city list
+    float coord_r;  // max |coordinate| (FP32 screen error bound)
     const double* __restrict__ xy;
+    const float2* __restrict__ xy32;
     const GridDesc* __restrict__ grid;
     const int* __restrict__ city_cell;
     const int* __restrict__ cell_start;
@@ -37,7 +47,6 @@ struct LbestArgs {
     const double* __restrict__ cell_xy;
     const CandW* __restrict__ candw;
     const double* __restrict__ W64;
-    const uint8_t* __restrict__ rowflag;
     const int* __restrict__ lbest;
     const int* __restrict__ nb;
     const unsigned long long* __restrict__ q;
@@ -45,11 +54,17 @@ struct LbestArgs {
     int* __restrict__ seg;
     AntIter* __restrict__ antit;
     unsigned long long* __restrict__ accq;
+    int* __restrict__ ulist;
+    float2* __restrict__ uxy;
     unsigned long long* __restrict__ counters;
     int* __restrict__ errflag;
 };
 
 __device__ __forceinline__ bool is_visited(const uint32_t* bits, int c) { return (bits[c >> 5] >> (c & 31)) & 1u; }
+
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
 
 // FP64 sequential wheel over the candidate row (rank order), identical to Eq. 1's definition.
 // Returns the picked rank or -1 when no unvisited candidate has a positive weight.
@@ -78,180 +93,271 @@ __device__ __forceinline__ double weight_of(const LbestArgs& A, double tau0pow, 
     return __dmul_rn(tp, eta_pow_from_d2(d2, A.beta));
 }
 
-// (w desc, city asc) warp argmax; returns the winner's city (uniform) and its weight.
-__device__ __forceinline__ int warp_argmax(double& w, int& c, double& d2) {
+__device__ __forceinline__ bool better(double w, int c, double bw, int bc) { return w > bw || (w == bw && c < bc); }
+
+// (w desc, city asc) warp argmax; every lane ends with the winner.
+__device__ __forceinline__ void warp_argmax(double& w, int& c) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
         const double ow = __shfl_xor_sync(FULL, w, o);
         const int oc = __shfl_xor_sync(FULL, c, o);
-        const double od = __shfl_xor_sync(FULL, d2, o);
-        if (ow > w || (ow == w && oc < c)) { w = ow; c = oc; d2 = od; }
+        if (better(ow, oc, w, c)) { w = ow; c = oc; }
     }
-    return c;
 }
 
-// Add the l_best weights of the unvisited neighbours of `cur` into accq (city-indexed, per ant).
-// clear = true undoes it (sets the touched entries back to zero).
-__device__ void boost_pass(const LbestArgs& A, int a, int cur, const uint32_t* bits, bool clear, int lane) {
-    if (!A.initialized) return;
+// Unvisited l_best neighbours of `cur` with their exact boosted weight: argmax into (bw, bc).
+// accq (per ant, city-indexed, zero between uses) accumulates the integer pheromone of each
+// neighbour; the touched cities are listed in shared memory and cleared afterwards.
+__device__ void boosted_neighbours(const LbestArgs& A, int a, int cur, const uint32_t* bits, int* touched, int lane,
+                                   double qx, double qy, double tau0pow, double& bw, int& bc) {
     unsigned long long* acc = A.accq + (size_t)a * A.n;
-    const int* row = A.nb + (size_t)cur * A.m * 2;
-    for (int b = lane; b < A.m; b += 32) {
-        const int2 e = *reinterpret_cast<const int2*>(row + 2 * b);
-        if (!is_visited(bits, e.x)) {
-            if (clear) acc[e.x] = 0ull; else atomicAdd(&acc[e.x], A.q[b]);
+    const int2* row = reinterpret_cast<const int2*>(A.nb + (size_t)cur * A.m * 2);  // (succ, pred) per ant
+    int nt = 0;
+    bool overflow = false;
+    for (int base = 0; base < A.m; base += 128) {
+        int2 v[4];
+        unsigned long long qq[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int b = base + 32 * h + lane;
+            v[h] = b < A.m ? row[b] : make_int2(-1, -1);
+            qq[h] = b < A.m ? A.q[b] : 0ull;
         }
-        if (!is_visited(bits, e.y)) {
-            if (clear) acc[e.y] = 0ull; else atomicAdd(&acc[e.y], A.q[b]);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int x = (e & 1) ? v[e >> 1].y : v[e >> 1].x;
+            const bool un = x >= 0 && !is_visited(bits, x);
+            if (un) atomicAdd(&acc[x], qq[e >> 1]);
+            const unsigned b = __ballot_sync(FULL, un);
+            if (un) {
+                const int pos = nt + __popc(b & ((1u << lane) - 1u));
+                if (pos < TOUCH_CAP) touched[pos] = x;
+            }
+            nt += __popc(b);
+        }
+    }
+    if (nt > TOUCH_CAP) { overflow = true; nt = TOUCH_CAP; }
+    __syncwarp();
+    // every touched city (duplicates give the same value) with its final sum
+    for (int t = lane; t < nt; t += 32) {
+        const int x = touched[t];
+        const double d2 = dist2(qx, qy, A.xy[2 * x], A.xy[2 * x + 1]);
+        const double w = weight_of(A, tau0pow, __ldcg(&acc[x]), d2);
+        if (better(w, x, bw, bc)) { bw = w; bc = x; }
+    }
+    if (overflow) {  // rare: more touched entries than the list holds -- rescan the row
+        for (int b = lane; b < 2 * A.m; b += 32) {
+            const int x = A.nb[(size_t)cur * A.m * 2 + b];
+            if (is_visited(bits, x)) continue;
+            const double d2 = dist2(qx, qy, A.xy[2 * x], A.xy[2 * x + 1]);
+            const double w = weight_of(A, tau0pow, __ldcg(&acc[x]), d2);
+            if (better(w, x, bw, bc)) { bw = w; bc = x; }
         }
     }
     __syncwarp();
+    for (int t = lane; t < nt; t += 32) acc[touched[t]] = 0ull;
+    if (overflow)
+        for (int b = lane; b < 2 * A.m; b += 32) {
+            const int x = A.nb[(size_t)cur * A.m * 2 + b];
+            if (!is_visited(bits, x)) acc[x] = 0ull;
+        }
+    __syncwarp();
+}
+
+// Error bound of the FP32 squared distance d2f against the exact FP64 one, for coordinates of
+// magnitude <= R rounded to FP32: |d2f - d2| <= 2^-21 (2 R sqrt(d2) + 2 d2) + 2^-44 R^2 (generous).
+__device__ __forceinline__ float d2_bound(float d2, float R) {
+    return __fadd_rn(__fmul_rn(0x1.0p-21f, __fadd_rn(__fmul_rn(2.f * R, __fsqrt_rn(d2)), __fmul_rn(2.f, d2))),
+                     __fmul_rn(0x1.0p-44f, __fmul_rn(R, R)));
+}
+
+// Partial rebuild: argmax over the remaining discarded cities (compacted list, FP32 screen).
+__device__ void remaining_argmax(const LbestArgs& A, int a, int cur, const uint32_t* bits, int& ucount, int lane,
+                                 double qx, double qy, double tau0pow, double& bw, int& bc) {
+    int* ul = A.ulist + (size_t)a * A.ucap;
+    float2* uxy = A.uxy + (size_t)a * A.ucap;
+    const float2 q32 = A.xy32[cur];
+    float best = FLT_MAX;
+    int cnt = 0;
+    for (int base = 0; base < ucount; base += 32) {
+        const int idx = base + lane;
+        int id = -1;
+        float2 p = make_float2(0.f, 0.f);
+        if (idx < ucount) {
+            id = ul[idx];
+            p = uxy[idx];
+        }
+        const bool keep = id >= 0 && !is_visited(bits, id);
+        const unsigned b = __ballot_sync(FULL, keep);
+        if (keep) {
+            const int pos = cnt + __popc(b & ((1u << lane) - 1u));
+            ul[pos] = id;
+            uxy[pos] = p;
+            const float dx = __fsub_rn(p.x, q32.x), dy = __fsub_rn(p.y, q32.y);
+            best = fminf(best, __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)));
+        }
+        cnt += __popc(b);
+    }
+    ucount = cnt;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) best = fminf(best, __shfl_xor_sync(FULL, best, o));
+    __syncwarp();
+    if (cnt == 0) return;
+    const float R = A.coord_r;
+    const float hi = __fadd_rn(__fmul_rn(best, 1.0f + 0x1.0p-18f), __fmul_rn(2.f, d2_bound(best, R)));
+    const float thr = __fadd_rn(hi, __fmul_rn(2.f, d2_bound(hi, R)));
+    for (int idx = lane; idx < cnt; idx += 32) {
+        const float2 p = uxy[idx];
+        const float dx = __fsub_rn(p.x, q32.x), dy = __fsub_rn(p.y, q32.y);
+        const float d2f = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+        if (d2f <= thr) {
+            const int x = ul[idx];
+            const double d2 = dist2(qx, qy, A.xy[2 * x], A.xy[2 * x + 1]);
+            const double w = __dmul_rn(tau0pow, eta_pow_from_d2(d2, A.beta));
+            if (better(w, x, bw, bc)) { bw = w; bc = x; }
+        }
+    }
+}
+
+// Full construction: nearest unvisited city by a ring search over the grid (weight at tau0).
+__device__ void nearest_unvisited(const LbestArgs& A, int cur, const uint32_t* bits, int lane, double qx, double qy,
+                                  double tau0pow, double& bw, int& bc) {
+    const GridDesc g = *A.grid;
+    const int cell = A.city_cell[cur];
+    const int cx = cell % g.gx, cy = cell / g.gx;
+    double nd = DBL_MAX;
+    for (int r = 0;; ++r) {
+        const int ncell = r == 0 ? 1 : 8 * r;
+        for (int c0 = 0; c0 < ncell; c0 += 32) {
+            int pb = 0, pe = 0;
+            if (c0 + lane < ncell) {
+                int x, y;
+                const int idx = c0 + lane;
+                if (r == 0) { x = cx; y = cy; }
+                else if (idx < 2 * r + 1) { x = cx - r + idx; y = cy - r; }
+                else if (idx < 4 * r + 2) { x = cx - r + (idx - 2 * r - 1); y = cy + r; }
+                else if (idx < 6 * r + 1) { x = cx - r; y = cy - r + 1 + (idx - 4 * r - 2); }
+                else { x = cx + r; y = cy - r + 1 + (idx - 6 * r - 1); }
+                if (x >= 0 && y >= 0 && x < g.gx && y < g.gy) {
+                    const int c = y * g.gx + x;
+                    pb = A.cell_start[c];
+                    pe = A.cell_start[c + 1];
+                }
+            }
+            for (; pb < pe; ++pb) {
+                const int x = A.cell_city[pb];
+                if (is_visited(bits, x)) continue;
+                const double d2 = dist2(qx, qy, A.cell_xy[2 * pb], A.cell_xy[2 * pb + 1]);
+                if (!(d2 <= __dmul_rn(nd, 1.0 + 0x1.0p-40))) continue;  // cannot reach the best weight
+                const double w = __dmul_rn(tau0pow, eta_pow_from_d2(d2, A.beta));
+                if (better(w, x, bw, bc)) { bw = w; bc = x; }
+                nd = fmin(nd, d2);
+            }
+        }
+        double wd = nd;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) wd = fmin(wd, __shfl_xor_sync(FULL, wd, o));
+        const double lb = ring_lower_bound(g, qx, qy, cx, cy, r);
+        if (lb < 0.0) break;
+        if (wd < DBL_MAX && __dmul_rn(lb, lb) > __dmul_rn(wd, 1.0 + 0x1.0p-40)) break;
+    }
+}
+
+// Eq. 1 wheel over every unvisited city in index order (fallback = 1), FP64, sequential order.
+__device__ int wheel_all_unvisited(const LbestArgs& A, int a, int cur, double u, const uint32_t* bits, int* touched,
+                                   int lane, double qx, double qy, double tau0pow) {
+    const int n = A.n;
+    unsigned long long* acc = A.accq + (size_t)a * n;
+    // integer pheromone of the unvisited l_best neighbours into acc (cleared below)
+    const int* row = A.nb + (size_t)cur * A.m * 2;
+    if (A.initialized)
+        for (int b = lane; b < 2 * A.m; b += 32) {
+            const int x = row[b];
+            if (!is_visited(bits, x)) atomicAdd(&acc[x], A.q[b >> 1]);
+        }
+    __syncwarp();
+    const int W = (n + 31) >> 5;
+    double tot = 0.0;
+    int lowest = -1, last = -1, choice = -1;
+    for (int pass = 0; pass < 2 && choice < 0; ++pass) {
+        const double target = __dmul_rn(u, tot);
+        double cum = 0.0;
+        for (int wb = 0; wb < W && choice < 0; wb += 32) {
+            const int wi = wb + lane;
+            uint32_t free_bits = 0;
+            if (wi < W) {
+                free_bits = ~bits[wi];
+                if (wi == W - 1 && (n & 31)) free_bits &= (1u << (n & 31)) - 1u;
+            }
+            unsigned nz = __ballot_sync(FULL, free_bits != 0);
+            while (nz && choice < 0) {
+                const int src = __ffs(nz) - 1;
+                nz &= nz - 1;
+                uint32_t fb = __shfl_sync(FULL, free_bits, src);
+                const int base = (wb + src) << 5;
+                while (fb) {
+                    const int x = base + __ffs(fb) - 1;
+                    fb &= fb - 1;
+                    const double d2 = dist2(qx, qy, A.xy[2 * x], A.xy[2 * x + 1]);
+                    const double w = weight_of(A, tau0pow, __ldcg(&acc[x]), d2);
+                    if (pass == 0) {
+                        if (lowest < 0) lowest = x;
+                        tot = __dadd_rn(tot, w);
+                        if (w > 0.0) last = x;
+                    } else {
+                        cum = __dadd_rn(cum, w);
+                        if (w > 0.0 && cum > target) { choice = x; break; }
+                    }
+                }
+            }
+        }
+        if (pass == 0 && last < 0) choice = lowest;
+    }
+    if (choice < 0) choice = last;
+    __syncwarp();
+    if (A.initialized)
+        for (int b = lane; b < 2 * A.m; b += 32) {
+            const int x = row[b];
+            if (!is_visited(bits, x)) acc[x] = 0ull;
+        }
+    __syncwarp();
+    (void)touched;
+    return choice;
 }
 
 // Exhausted-list rule.  Returns the chosen city (uniform across the warp).
-__device__ int exhausted_choice(const LbestArgs& A, int a, int cur, double u, bool partial, int s, int P, int M,
-                                const uint32_t* bits, int lane) {
-    const int n = A.n;
-    const unsigned long long* acc = A.accq + (size_t)a * n;
+__device__ int exhausted_choice(const LbestArgs& A, int a, int cur, double u, bool partial, int& ucount,
+                                const uint32_t* bits, int* touched, int lane) {
     const double qx = A.xy[2 * cur], qy = A.xy[2 * cur + 1];
     const double tau0pow = powr(A.tau0, A.alpha);
-    boost_pass(A, a, cur, bits, false, lane);
-    int choice = -1;
+    int choice;
     if (A.fallback == 0) {
-        double bw = -1.0, bd = DBL_MAX;
+        double bw = -1.0;
         int bc = 0x7fffffff;
-        if (partial) {
-            const int* L = A.lbest + (size_t)a * n;
-            for (int t = lane; t < M; t += 32) {
-                const int x = L[(s + P + t) % n];
-                if (is_visited(bits, x)) continue;
-                const double d2 = dist2(qx, qy, A.xy[2 * x], A.xy[2 * x + 1]);
-                const double w = weight_of(A, tau0pow, acc[x], d2);
-                if (w > bw || (w == bw && x < bc)) { bw = w; bc = x; bd = d2; }
-            }
-            choice = warp_argmax(bw, bc, bd);
-        } else {
-            // boosted neighbours with their true weight
-            if (A.initialized) {
-                const int* row = A.nb + (size_t)cur * A.m * 2;
-                for (int b = lane; b < 2 * A.m; b += 32) {
-                    const int x = row[b];
-                    if (is_visited(bits, x)) continue;
-                    const double d2 = dist2(qx, qy, A.xy[2 * x], A.xy[2 * x + 1]);
-                    const double w = weight_of(A, tau0pow, acc[x], d2);
-                    if (w > bw || (w == bw && x < bc)) { bw = w; bc = x; bd = d2; }
-                }
-            }
-            // unboosted maximum = nearest unvisited city: ring search over the grid
-            const GridDesc g = *A.grid;
-            const int cell = A.city_cell[cur];
-            const int cx = cell % g.gx, cy = cell / g.gx;
-            double nd = DBL_MAX, nw = -1.0;  // lane-local best of the search (weight at tau0)
-            int nc = 0x7fffffff;
-            for (int r = 0;; ++r) {
-                const int ncell = r == 0 ? 1 : 8 * r;
-                for (int c0 = 0; c0 < ncell; c0 += 32) {
-                    int pb = 0, pe = 0;
-                    if (c0 + lane < ncell) {
-                        int x, y;
-                        const int idx = c0 + lane;
-                        if (r == 0) { x = cx; y = cy; }
-                        else if (idx < 2 * r + 1) { x = cx - r + idx; y = cy - r; }
-                        else if (idx < 4 * r + 2) { x = cx - r + (idx - 2 * r - 1); y = cy + r; }
-                        else if (idx < 6 * r + 1) { x = cx - r; y = cy - r + 1 + (idx - 4 * r - 2); }
-                        else { x = cx + r; y = cy - r + 1 + (idx - 6 * r - 1); }
-                        if (x >= 0 && y >= 0 && x < g.gx && y < g.gy) {
-                            const int c = y * g.gx + x;
-                            pb = A.cell_start[c];
-                            pe = A.cell_start[c + 1];
-                        }
-                    }
-                    for (; pb < pe; ++pb) {
-                        const int x = A.cell_city[pb];
-                        if (is_visited(bits, x)) continue;
-                        const double d2 = dist2(qx, qy, A.cell_xy[2 * pb], A.cell_xy[2 * pb + 1]);
-                        if (!(d2 <= __dmul_rn(nd, 1.0 + 0x1.0p-40))) continue;  // cannot tie the best weight
-                        const double w = __dmul_rn(tau0pow, eta_pow_from_d2(d2, A.beta));
-                        if (w > nw || (w == nw && x < nc)) {
-                            nw = w; nc = x;
-                            nd = fmin(nd, d2);
-                        }
-                    }
-                }
-                // warp-uniform best distance so far
-                double wd = nd;
-#pragma unroll
-                for (int o = 16; o; o >>= 1) wd = fmin(wd, __shfl_xor_sync(FULL, wd, o));
-                const double lb = ring_lower_bound(g, qx, qy, cx, cy, r);
-                if (lb < 0.0) break;
-                if (wd < DBL_MAX && __dmul_rn(lb, lb) > __dmul_rn(wd, 1.0 + 0x1.0p-40)) break;
-            }
-            double dd = nd;
-            warp_argmax(nw, nc, dd);
-            // combine: the nearest city's tau0 weight vs the boosted neighbours' true weights
-            double cbw = bw, cbd = bd;
-            int cbc = bc;
-            warp_argmax(cbw, cbc, cbd);
-            if (nw > cbw || (nw == cbw && nc < cbc)) { cbw = nw; cbc = nc; }
-            choice = cbc;
-        }
+        if (A.initialized) boosted_neighbours(A, a, cur, bits, touched, lane, qx, qy, tau0pow, bw, bc);
+        if (partial) remaining_argmax(A, a, cur, bits, ucount, lane, qx, qy, tau0pow, bw, bc);
+        else nearest_unvisited(A, cur, bits, lane, qx, qy, tau0pow, bw, bc);
+        warp_argmax(bw, bc);
+        choice = bc;
+        if (bw < 0.0) choice = -1;
     } else {
-        // Eq. 1 wheel over every unvisited city in index order (FP64, sequential: all lanes
-        // evaluate the same sums; the words of the bitset are screened in parallel).
-        const int W = (n + 31) >> 5;
-        double tot = 0.0;
-        int lowest = -1, last = -1;
-        for (int pass = 0; pass < 2 && choice < 0; ++pass) {
-            const double target = __dmul_rn(u, tot);
-            double cum = 0.0;
-            for (int wb = 0; wb < W && choice < 0; wb += 32) {
-                const int wi = wb + lane;
-                uint32_t free_bits = 0;
-                if (wi < W) {
-                    free_bits = ~bits[wi];
-                    if (wi == W - 1 && (n & 31)) free_bits &= (1u << (n & 31)) - 1u;
-                }
-                unsigned nz = __ballot_sync(FULL, free_bits != 0);
-                while (nz && choice < 0) {
-                    const int src = __ffs(nz) - 1;
-                    nz &= nz - 1;
-                    uint32_t fb = __shfl_sync(FULL, free_bits, src);
-                    const int base = (wb + src) << 5;
-                    while (fb) {
-                        const int x = base + __ffs(fb) - 1;
-                        fb &= fb - 1;
-                        const double d2 = dist2(qx, qy, A.xy[2 * x], A.xy[2 * x + 1]);
-                        const double w = weight_of(A, tau0pow, acc[x], d2);
-                        if (pass == 0) {
-                            if (lowest < 0) lowest = x;
-                            tot = __dadd_rn(tot, w);
-                            if (w > 0.0) last = x;
-                        } else {
-                            cum = __dadd_rn(cum, w);
-                            if (w > 0.0 && cum > target) { choice = x; break; }
-                        }
-                    }
-                }
-            }
-            if (pass == 0 && last < 0) choice = lowest;
-        }
-        if (choice < 0) choice = last;
+        choice = wheel_all_unvisited(A, a, cur, u, bits, touched, lane, qx, qy, tau0pow);
     }
-    boost_pass(A, a, cur, bits, true, lane);
-    if (choice < 0) {
+    if (choice < 0 || choice >= A.n) {
         if (lane == 0) atomicOr(A.errflag, DEVERR_NO_CHOICE);
         choice = cur;
     }
     return choice;
 }
 
-// Exact length of the edges (from[e], to[e]) of a path given by a generator.
+// Exact length of one edge on the 2^-96 grid.
 __device__ __forceinline__ u128 edge_fix(const double* __restrict__ xy, int i, int j) {
     return len_to_fix(__dsqrt_rn(dist2(xy[2 * i], xy[2 * i + 1], xy[2 * j], xy[2 * j + 1])));
 }
 
 __global__ void __launch_bounds__(32) construct_lbest_kernel(LbestArgs A) {
     extern __shared__ uint32_t bits[];
+    __shared__ int touched[TOUCH_CAP];
     const int a = blockIdx.x, lane = threadIdx.x;
     const int n = A.n, k = A.k;
     const int W = (n + 31) >> 5;
@@ -266,6 +372,7 @@ __global__ void __launch_bounds__(32) construct_lbest_kernel(LbestArgs A) {
     const int* L = A.lbest + (size_t)a * n;
     int* seg = A.seg + (size_t)a * n;
     int cur, steps, s = -1, P = 0, M, start;
+    int ucount = 0;
     if (partial) {
         const Draw4 d1 = aco_draw(A.seed, 0, a, A.iteration, PURPOSE_START);
         s = (int)below(d1.x0, (uint32_t)n);
@@ -278,10 +385,18 @@ __global__ void __launch_bounds__(32) construct_lbest_kernel(LbestArgs A) {
         M = n - P;
         for (int w = lane; w < W; w += 32) bits[w] = 0xFFFFFFFFu;
         __syncwarp();
+        int* ul = A.ulist + (size_t)a * A.ucap;
+        float2* uxy = A.uxy + (size_t)a * A.ucap;
         for (int t = lane; t < M; t += 32) {
-            const int c = L[(s + P + t) % n];
+            int pos = s + P + t;
+            pos -= pos >= n ? n : 0;
+            pos -= pos >= n ? n : 0;
+            const int c = L[pos];
             atomicAnd(&bits[c >> 5], ~(1u << (c & 31)));
+            ul[t] = c;
+            uxy[t] = A.xy32[c];
         }
+        ucount = M;
         cur = L[(s + P - 1) % n];
         start = L[s];
         steps = M;
@@ -301,26 +416,33 @@ __global__ void __launch_bounds__(32) construct_lbest_kernel(LbestArgs A) {
     __syncwarp();
     const int outbase = partial ? 0 : 1;
     double my_u = 0.0;
+    float my_uf = 0.f;
     unsigned long long nfall = 0, nres = 0;
+    const CandW* rowp = A.candw + (size_t)cur * k;
     for (int t = 0; t < steps; ++t) {
         if ((t & 31) == 0) {
             const Draw4 d = aco_draw(A.seed, (uint32_t)(t + lane), a, A.iteration, PURPOSE_WHEEL);
             my_u = unit53(d.x0, d.x1);
+            my_uf = __double2float_rn(my_u);
         }
-        const double u = __shfl_sync(FULL, my_u, t & 31);
         int c = -1;
         float w = 0.f;
         bool feas = false;
         if (lane < k) {
-            const CandW e = A.candw[(size_t)cur * k + lane];
+            const CandW e = rowp[lane];
             c = e.city;
             w = e.w;
             feas = !is_visited(bits, c);
+            if (feas) {
+                const CandW* nr = A.candw + (size_t)c * k;
+                prefetch_l1(nr);
+                if (k > 16) prefetch_l1(nr + k - 1);
+            }
         }
         const unsigned fmask = __ballot_sync(FULL, feas);
         int pick = -1;
         if (fmask) {
-            bool exact = A.rowflag[cur] != 0;
+            bool exact = __any_sync(FULL, lane < k && !(w > 0.f));  // row flagged: screen weights negative
             if (!exact) {
                 float S = feas ? w : 0.f;
 #pragma unroll
@@ -329,7 +451,7 @@ __global__ void __launch_bounds__(32) construct_lbest_kernel(LbestArgs A) {
                     if (lane >= o) S = __fadd_rn(S, v);
                 }
                 const float T = __shfl_sync(FULL, S, 31);
-                const float tf = __fmul_rn(__double2float_rn(u), T);
+                const float tf = __fmul_rn(__shfl_sync(FULL, my_uf, t & 31), T);
                 const unsigned gt = __ballot_sync(FULL, feas && S > tf);
                 const float lo_all = __shfl_up_sync(FULL, S, 1);
                 exact = true;
@@ -346,7 +468,7 @@ __global__ void __launch_bounds__(32) construct_lbest_kernel(LbestArgs A) {
             }
             if (exact) {
                 ++nres;
-                pick = wheel_exact_row(A.W64 + (size_t)cur * k, fmask, k, u);
+                pick = wheel_exact_row(A.W64 + (size_t)cur * k, fmask, k, __shfl_sync(FULL, my_u, t & 31));
             }
         }
         int j;
@@ -354,8 +476,9 @@ __global__ void __launch_bounds__(32) construct_lbest_kernel(LbestArgs A) {
             j = __shfl_sync(FULL, c, pick);
         } else {
             ++nfall;
-            j = exhausted_choice(A, a, cur, u, partial, s, P, M, bits, lane);
+            j = exhausted_choice(A, a, cur, __shfl_sync(FULL, my_u, t & 31), partial, ucount, bits, touched, lane);
         }
+        rowp = A.candw + (size_t)j * k;
         if (lane == 0) {
             bits[j >> 5] |= 1u << (j & 31);
             seg[outbase + t] = j;
@@ -406,13 +529,14 @@ aco_status launch_construct_lbest(aco_instance* inst, int32_t iteration) {
     A.n = p.n; A.m = p.m; A.k = p.k;
     A.alpha = p.alpha; A.beta = p.beta; A.tau0 = p.tau0; A.f = p.max_mod_frac; A.p_partial = p.p_partial;
     A.seed = p.seed; A.fallback = p.fallback; A.iteration = iteration; A.initialized = inst->initialized ? 1 : 0;
-    A.xy = inst->xy; A.grid = inst->grid_dev; A.city_cell = inst->city_cell; A.cell_start = inst->cell_start;
-    A.cell_city = inst->cell_city; A.cell_xy = inst->cell_xy; A.candw = inst->candw; A.W64 = inst->W64;
-    A.rowflag = inst->rowflag; A.lbest = inst->lbest; A.nb = inst->nb; A.q = inst->q; A.cfix = inst->cfix;
-    A.seg = inst->seg; A.antit = inst->antit; A.accq = inst->accq; A.counters = inst->counters;
-    A.errflag = inst->errflag;
+    A.ucap = inst->ucap; A.coord_r = inst->coord_r;
+    A.xy = inst->xy; A.xy32 = inst->xy32; A.grid = inst->grid_dev; A.city_cell = inst->city_cell;
+    A.cell_start = inst->cell_start; A.cell_city = inst->cell_city; A.cell_xy = inst->cell_xy; A.candw = inst->candw;
+    A.W64 = inst->W64; A.lbest = inst->lbest; A.nb = inst->nb; A.q = inst->q; A.cfix = inst->cfix;
+    A.seg = inst->seg; A.antit = inst->antit; A.accq = inst->accq; A.ulist = inst->ulist; A.uxy = inst->uxy;
+    A.counters = inst->counters; A.errflag = inst->errflag;
     const size_t smem = sizeof(uint32_t) * (size_t)((p.n + 31) / 32);
-    if (smem > 48 * 1024) {
+    if (smem > 40 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(construct_lbest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return set_err(inst, ACO_ERR_CUDA, "smem attribute: %s", cudaGetErrorString(e));

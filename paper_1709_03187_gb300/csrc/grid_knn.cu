@@ -171,6 +171,11 @@ __global__ void dense_eta_kernel(const double* __restrict__ xy, int n, double be
     }
 }
 
+__global__ void xy32_kernel(const double* __restrict__ xy, int n, float2* __restrict__ xy32) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        xy32[i] = make_float2(__double2float_rn(xy[2 * i]), __double2float_rn(xy[2 * i + 1]));
+}
+
 aco_status launch_build_grid_and_knn(aco_instance* inst) {
     const int n = inst->p.n;
     cudaStream_t s = inst->stream;
@@ -185,6 +190,7 @@ aco_status launch_build_grid_and_knn(aco_instance* inst) {
     const int ncells = g.gx * g.gy;
     cudaMemsetAsync(inst->cell_fill, 0, sizeof(int) * ncells, s);
     const int blocks = (int)fmin((double)inst->num_sms * 8, (double)ceil_div(n, 256));
+    xy32_kernel<<<blocks, 256, 0, s>>>(inst->xy, n, inst->xy32);
     grid_count_kernel<<<blocks, 256, 0, s>>>(inst->xy, n, inst->grid_dev, inst->city_cell, inst->cell_fill);
     scan_single_block_kernel<<<1, 1024, 0, s>>>(inst->cell_fill, ncells, inst->cell_start);
     cudaMemsetAsync(inst->cell_fill, 0, sizeof(int) * ncells, s);

@@ -181,17 +181,20 @@ __global__ void __launch_bounds__(256) rebuild_kernel(int n, int m, int k, doubl
             __syncwarp();
         }
         bool flag = false;
+        float w32 = 0.f;
         if (lane < k) {
             const size_t e = (size_t)i * k + lane;
             const double tau = __dadd_rn(tau0, __dmul_rn(__ull2double_rn(Q), 0x1.0p-32));
             const double wv = __dmul_rn(powr(tau, alpha), etab[e]);
-            const float w32 = __double2float_rn(wv);
+            w32 = __double2float_rn(wv);
             if (!isfinite(wv)) atomicOr(errflag, DEVERR_NONFINITE);
             flag = !(w32 >= FLT_MIN && w32 <= FLT_MAX);
             W64[e] = wv;
-            candw[e].w = w32;
         }
         const unsigned fl = __ballot_sync(FULL, flag);
+        // a row the FP32 screen cannot represent carries negative screen weights: the
+        // construction kernel then evaluates it exactly in FP64
+        if (lane < k) candw[(size_t)i * k + lane].w = fl ? -1.0f : w32;
         if (lane == 0) rowflag[i] = fl ? 1 : 0;
     }
 }

@@ -368,3 +368,30 @@ def test_lbest_step_probs_candidate_form():
     assert not ex
     assert np.all(p[vis[cand] == 1] == 0)
     assert abs(p.sum() - 1) < 1e-15
+
+
+@pytest.mark.parametrize("gen", ["uniform", "clustered", "lattice"])
+def test_knn_sweep_and_single_query_match_definition(gen):
+    if gen == "uniform":
+        xy = aco_synth.uniform(700, 31)
+    elif gen == "clustered":
+        xy = aco_synth.clustered(700, 5, 0.02, 32)
+    else:
+        g = np.arange(25, dtype=np.float64)
+        xy = np.ascontiguousarray(np.stack(np.meshgrid(g, g), -1).reshape(-1, 2))
+    k = 12
+    ref = oracle.knn(xy, k)
+    assert np.array_equal(oracle.knn_sweep(xy, k), ref)
+    for i in range(0, xy.shape[0], 37):
+        assert np.array_equal(oracle.knn_one(xy, k, i), ref[i])
+
+
+def test_oracle_with_supplied_candidates_is_identical():
+    xy = aco_synth.clustered(120, 3, 0.05, 8)
+    kw = dict(mode=oracle.MODE_LBEST, n=120, m=6, k=7, max_mod_frac=0.4, seed=3)
+    a = oracle.Oracle(xy, **kw)
+    b = oracle.Oracle(xy, cand=oracle.knn_sweep(xy, 7), **kw)
+    for it in range(8):
+        a.iterate(it)
+        b.iterate(it)
+    assert np.array_equal(a.lbest, b.lbest) and np.array_equal(a.clen, b.clen)
