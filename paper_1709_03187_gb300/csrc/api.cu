@@ -77,7 +77,7 @@ static bool params_ok(const aco_params* p, char* why, size_t wn) {
     if (p->fallback != 0 && p->fallback != 1) return snprintf(why, wn, "fallback must be 0 or 1"), false;
     if (p->reserved != 0) return snprintf(why, wn, "reserved must be 0"), false;
     if (p->mode == ACO_MODE_DENSE && p->n > 8192) return snprintf(why, wn, "DENSE mode supports n <= 8192"), false;
-    // the visited bitset of one ant lives in shared memory (<= 200 KB)
+    // the visited bitset of one ant lives in shared memory (<= 200 KB, beside ~6 KB of buffers)
     if ((long long)(p->n + 31) / 32 * 4 > 200 * 1024) return snprintf(why, wn, "n too large for the visited bitset"), false;
     if ((long long)p->n * p->m > (1ll << 31) - 1) return snprintf(why, wn, "n*m must be < 2^31"), false;
     return true;

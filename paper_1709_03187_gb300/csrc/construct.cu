@@ -9,9 +9,9 @@
 // away from both bounding prefix sums, which is more than the worst-case FP32 error, so the
 // pick equals the FP64 sequential wheel's pick.  Otherwise (or when a row's weights are not
 // FP32-normal, marked by negative screen weights) the decision is re-evaluated exactly: the
-// FP64 weights summed in rank order, exactly as Eq. 1 is defined.  The rows of every unvisited
-// candidate are prefetched into L1 while the current decision is computed, so the next row is
-// usually an L1 hit.
+// FP64 weights summed in rank order, exactly as Eq. 1 is defined.  While the current decision
+// is computed, the rows of every unvisited candidate are copied (cp.async) into a shared-memory
+// staging buffer, so the next decision reads its row from shared memory.
 //
 // Exhausted list (every candidate visited): argmax over the unvisited cities of
 // tau_ij^alpha eta_ij^beta (ties to the lowest index), where tau_ij = tau0 + Q_ij 2^-32 and Q_ij
@@ -29,7 +29,8 @@
 #include "common.cuh"
 
 #define FULL 0xffffffffu
-#define TOUCH_CAP 64
+#define TOUCH_CAP 96   // unvisited non-candidate neighbour entries listed per exhausted step
+#define ELIST_CAP 768  // non-candidate neighbour entries listed per exhausted step
 
 struct LbestArgs {
     int n, m, k;
@@ -49,6 +50,7 @@ struct LbestArgs {
     const double* __restrict__ W64;
     const int* __restrict__ lbest;
     const int* __restrict__ nb;
+    const uint8_t* __restrict__ nbrank;
     const unsigned long long* __restrict__ q;
     const unsigned long long* __restrict__ cfix;
     int* __restrict__ seg;
@@ -61,10 +63,6 @@ struct LbestArgs {
 };
 
 __device__ __forceinline__ bool is_visited(const uint32_t* bits, int c) { return (bits[c >> 5] >> (c & 31)) & 1u; }
-
-__device__ __forceinline__ void prefetch_l1(const void* p) {
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
 
 // FP64 sequential wheel over the candidate row (rank order), identical to Eq. 1's definition.
 // Returns the picked rank or -1 when no unvisited candidate has a positive weight.
@@ -105,49 +103,99 @@ __device__ __forceinline__ void warp_argmax(double& w, int& c) {
     }
 }
 
-// Unvisited l_best neighbours of `cur` with their exact boosted weight: argmax into (bw, bc).
-// accq (per ant, city-indexed, zero between uses) accumulates the integer pheromone of each
-// neighbour; the touched cities are listed in shared memory and cleared afterwards.
-__device__ void boosted_neighbours(const LbestArgs& A, int a, int cur, const uint32_t* bits, int* touched, int lane,
+// Unvisited l_best neighbours of `cur` that are not candidates, with their exact boosted
+// weight: argmax into (bw, bc).  Only entries whose candidate rank is 0xFF (the neighbour is not
+// a candidate) can be unvisited here.  Phase A reads the whole 2-byte rank row of `cur` at once
+// and lists those entries in shared memory; phase B gathers their neighbour ids together, so the
+// step costs about two memory round trips.  accq (per ant, city-indexed, zero between uses) sums
+// the integer pheromone per city; the touched cities are listed in shared memory and cleared
+// afterwards.
+struct BoostSmem {
+    unsigned short elist[ELIST_CAP];
+    int touched[TOUCH_CAP];
+    int ecount, tcount;
+};
+
+__device__ void boosted_neighbours(const LbestArgs& A, int a, int cur, const uint32_t* bits, BoostSmem& sh, int lane,
                                    double qx, double qy, double tau0pow, double& bw, int& bc) {
     unsigned long long* acc = A.accq + (size_t)a * A.n;
-    const int2* row = reinterpret_cast<const int2*>(A.nb + (size_t)cur * A.m * 2);  // (succ, pred) per ant
-    int nt = 0;
-    bool overflow = false;
-    for (int base = 0; base < A.m; base += 128) {
-        int2 v[4];
-        unsigned long long qq[4];
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const int b = base + 32 * h + lane;
-            v[h] = b < A.m ? row[b] : make_int2(-1, -1);
-            qq[h] = b < A.m ? A.q[b] : 0ull;
-        }
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int x = (e & 1) ? v[e >> 1].y : v[e >> 1].x;
-            const bool un = x >= 0 && !is_visited(bits, x);
-            if (un) atomicAdd(&acc[x], qq[e >> 1]);
-            const unsigned b = __ballot_sync(FULL, un);
-            if (un) {
-                const int pos = nt + __popc(b & ((1u << lane) - 1u));
-                if (pos < TOUCH_CAP) touched[pos] = x;
-            }
-            nt += __popc(b);
-        }
-    }
-    if (nt > TOUCH_CAP) { overflow = true; nt = TOUCH_CAP; }
+    const uint8_t* rrow = A.nbrank + (size_t)cur * A.m * 2;
+    const int* irow = A.nb + (size_t)cur * A.m * 2;
+    const int E = 2 * A.m;  // entries: (ant, side) -> index 2*ant + side
+    if (lane == 0) { sh.ecount = 0; sh.tcount = 0; }
     __syncwarp();
-    // every touched city (duplicates give the same value) with its final sum
+    // phase A: list the non-candidate entries
+    if ((A.m & 7) == 0) {
+        for (int base = 0; base < E; base += 2048) {
+            uint4 v[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int b0 = base + h * 512 + lane * 16;
+                v[h] = b0 < E ? *reinterpret_cast<const uint4*>(rrow + b0) : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int b0 = base + h * 512 + lane * 16;
+                const uint32_t wv[4] = {v[h].x, v[h].y, v[h].z, v[h].w};
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    uint32_t msk = __vcmpeq4(wv[g], 0xFFFFFFFFu);  // 0xFF in every byte equal to 0xFF
+                    while (msk) {
+                        const int byte = (__ffs(msk) - 1) >> 3;
+                        msk &= ~(0xFFu << (8 * byte));
+                        const int pos = atomicAdd(&sh.ecount, 1);
+                        if (pos < ELIST_CAP) sh.elist[pos] = (unsigned short)(b0 + 4 * g + byte);
+                    }
+                }
+            }
+        }
+    } else {
+        for (int e = lane; e < E; e += 32)
+            if (rrow[e] == 0xFF) {
+                const int pos = atomicAdd(&sh.ecount, 1);
+                if (pos < ELIST_CAP) sh.elist[pos] = (unsigned short)e;
+            }
+    }
+    __syncwarp();
+    const int total_e = sh.ecount;
+    auto touch = [&](int x, int e) {
+        if (!is_visited(bits, x)) {
+            atomicAdd(&acc[x], A.q[e >> 1]);
+            const int pos = atomicAdd(&sh.tcount, 1);
+            if (pos < TOUCH_CAP) sh.touched[pos] = x;
+        }
+    };
+    if (total_e <= ELIST_CAP) {
+        // phase B: gather the listed neighbour ids, four per lane in flight
+        for (int t0 = 0; t0 < total_e; t0 += 128) {
+            int e4[4], x4[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int idx = t0 + 32 * h + lane;
+                e4[h] = idx < total_e ? (int)sh.elist[idx] : -1;
+                x4[h] = e4[h] >= 0 ? irow[e4[h]] : -1;
+            }
+#pragma unroll
+            for (int h = 0; h < 4; ++h)
+                if (x4[h] >= 0) touch(x4[h], e4[h]);
+        }
+    } else {  // very many non-candidate entries: gather them inline
+        for (int e = lane; e < E; e += 32)
+            if (rrow[e] == 0xFF) touch(irow[e], e);
+    }
+    __syncwarp();
+    const int total = sh.tcount;
+    const int nt = total < TOUCH_CAP ? total : TOUCH_CAP;
     for (int t = lane; t < nt; t += 32) {
-        const int x = touched[t];
+        const int x = sh.touched[t];
         const double d2 = dist2(qx, qy, A.xy[2 * x], A.xy[2 * x + 1]);
         const double w = weight_of(A, tau0pow, __ldcg(&acc[x]), d2);
         if (better(w, x, bw, bc)) { bw = w; bc = x; }
     }
-    if (overflow) {  // rare: more touched entries than the list holds -- rescan the row
-        for (int b = lane; b < 2 * A.m; b += 32) {
-            const int x = A.nb[(size_t)cur * A.m * 2 + b];
+    if (total > TOUCH_CAP) {  // rare: more touched entries than the list holds -- rescan the row
+        for (int e = lane; e < E; e += 32) {
+            if (rrow[e] != 0xFF) continue;
+            const int x = irow[e];
             if (is_visited(bits, x)) continue;
             const double d2 = dist2(qx, qy, A.xy[2 * x], A.xy[2 * x + 1]);
             const double w = weight_of(A, tau0pow, __ldcg(&acc[x]), d2);
@@ -155,10 +203,11 @@ __device__ void boosted_neighbours(const LbestArgs& A, int a, int cur, const uin
         }
     }
     __syncwarp();
-    for (int t = lane; t < nt; t += 32) acc[touched[t]] = 0ull;
-    if (overflow)
-        for (int b = lane; b < 2 * A.m; b += 32) {
-            const int x = A.nb[(size_t)cur * A.m * 2 + b];
+    for (int t = lane; t < nt; t += 32) acc[sh.touched[t]] = 0ull;
+    if (total > TOUCH_CAP)
+        for (int e = lane; e < E; e += 32) {
+            if (rrow[e] != 0xFF) continue;
+            const int x = irow[e];
             if (!is_visited(bits, x)) acc[x] = 0ull;
         }
     __syncwarp();
@@ -172,33 +221,51 @@ __device__ __forceinline__ float d2_bound(float d2, float R) {
 }
 
 // Partial rebuild: argmax over the remaining discarded cities (compacted list, FP32 screen).
+// Pass 1 (eight loads per lane in flight) compacts the list in place (visited cities drop out)
+// and keeps, per lane, the two
+// smallest screened distances and where the smallest now sits.  Only cities whose screened
+// distance is within the error bound of the minimum can carry the largest weight; they get the
+// exact FP64 weight.  A second pass over the list is needed only when some lane holds two such
+// cities.
 __device__ void remaining_argmax(const LbestArgs& A, int a, int cur, const uint32_t* bits, int& ucount, int lane,
                                  double qx, double qy, double tau0pow, double& bw, int& bc) {
     int* ul = A.ulist + (size_t)a * A.ucap;
     float2* uxy = A.uxy + (size_t)a * A.ucap;
     const float2 q32 = A.xy32[cur];
-    float best = FLT_MAX;
+    float m1 = FLT_MAX, m2 = FLT_MAX;
+    int i1 = -1;
     int cnt = 0;
-    for (int base = 0; base < ucount; base += 32) {
-        const int idx = base + lane;
-        int id = -1;
-        float2 p = make_float2(0.f, 0.f);
-        if (idx < ucount) {
-            id = ul[idx];
-            p = uxy[idx];
+    for (int base = 0; base < ucount; base += 256) {
+        int id[8];
+        float2 p[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const int idx = base + 32 * h + lane;
+            id[h] = -1;
+            p[h] = make_float2(0.f, 0.f);
+            if (idx < ucount) {
+                id[h] = ul[idx];
+                p[h] = uxy[idx];
+            }
         }
-        const bool keep = id >= 0 && !is_visited(bits, id);
-        const unsigned b = __ballot_sync(FULL, keep);
-        if (keep) {
-            const int pos = cnt + __popc(b & ((1u << lane) - 1u));
-            ul[pos] = id;
-            uxy[pos] = p;
-            const float dx = __fsub_rn(p.x, q32.x), dy = __fsub_rn(p.y, q32.y);
-            best = fminf(best, __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)));
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const bool keep = id[h] >= 0 && !is_visited(bits, id[h]);
+            const unsigned b = __ballot_sync(FULL, keep);
+            if (keep) {
+                const int pos = cnt + __popc(b & ((1u << lane) - 1u));
+                ul[pos] = id[h];
+                uxy[pos] = p[h];
+                const float dx = __fsub_rn(p[h].x, q32.x), dy = __fsub_rn(p[h].y, q32.y);
+                const float d2f = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+                if (d2f < m1) { m2 = m1; m1 = d2f; i1 = pos; }
+                else if (d2f < m2) { m2 = d2f; }
+            }
+            cnt += __popc(b);
         }
-        cnt += __popc(b);
     }
     ucount = cnt;
+    float best = m1;
 #pragma unroll
     for (int o = 16; o; o >>= 1) best = fminf(best, __shfl_xor_sync(FULL, best, o));
     __syncwarp();
@@ -206,16 +273,23 @@ __device__ void remaining_argmax(const LbestArgs& A, int a, int cur, const uint3
     const float R = A.coord_r;
     const float hi = __fadd_rn(__fmul_rn(best, 1.0f + 0x1.0p-18f), __fmul_rn(2.f, d2_bound(best, R)));
     const float thr = __fadd_rn(hi, __fmul_rn(2.f, d2_bound(hi, R)));
-    for (int idx = lane; idx < cnt; idx += 32) {
-        const float2 p = uxy[idx];
-        const float dx = __fsub_rn(p.x, q32.x), dy = __fsub_rn(p.y, q32.y);
-        const float d2f = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-        if (d2f <= thr) {
-            const int x = ul[idx];
-            const double d2 = dist2(qx, qy, A.xy[2 * x], A.xy[2 * x + 1]);
-            const double w = __dmul_rn(tau0pow, eta_pow_from_d2(d2, A.beta));
-            if (better(w, x, bw, bc)) { bw = w; bc = x; }
+    if (__any_sync(FULL, m2 <= thr)) {
+        for (int idx = lane; idx < cnt; idx += 32) {
+            const float2 p = uxy[idx];
+            const float dx = __fsub_rn(p.x, q32.x), dy = __fsub_rn(p.y, q32.y);
+            const float d2f = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+            if (d2f <= thr) {
+                const int x = ul[idx];
+                const double d2 = dist2(qx, qy, A.xy[2 * x], A.xy[2 * x + 1]);
+                const double w = __dmul_rn(tau0pow, eta_pow_from_d2(d2, A.beta));
+                if (better(w, x, bw, bc)) { bw = w; bc = x; }
+            }
         }
+    } else if (m1 <= thr) {
+        const int x = ul[i1];
+        const double d2 = dist2(qx, qy, A.xy[2 * x], A.xy[2 * x + 1]);
+        const double w = __dmul_rn(tau0pow, eta_pow_from_d2(d2, A.beta));
+        if (better(w, x, bw, bc)) { bw = w; bc = x; }
     }
 }
 
@@ -264,8 +338,8 @@ __device__ void nearest_unvisited(const LbestArgs& A, int cur, const uint32_t* b
 }
 
 // Eq. 1 wheel over every unvisited city in index order (fallback = 1), FP64, sequential order.
-__device__ int wheel_all_unvisited(const LbestArgs& A, int a, int cur, double u, const uint32_t* bits, int* touched,
-                                   int lane, double qx, double qy, double tau0pow) {
+__device__ int wheel_all_unvisited(const LbestArgs& A, int a, int cur, double u, const uint32_t* bits, int lane,
+                                   double qx, double qy, double tau0pow) {
     const int n = A.n;
     unsigned long long* acc = A.accq + (size_t)a * n;
     // integer pheromone of the unvisited l_best neighbours into acc (cleared below)
@@ -321,27 +395,26 @@ __device__ int wheel_all_unvisited(const LbestArgs& A, int a, int cur, double u,
             if (!is_visited(bits, x)) acc[x] = 0ull;
         }
     __syncwarp();
-    (void)touched;
     return choice;
 }
 
 // Exhausted-list rule.  Returns the chosen city (uniform across the warp).
 __device__ int exhausted_choice(const LbestArgs& A, int a, int cur, double u, bool partial, int& ucount,
-                                const uint32_t* bits, int* touched, int lane) {
+                                const uint32_t* bits, BoostSmem& sh, int lane) {
     const double qx = A.xy[2 * cur], qy = A.xy[2 * cur + 1];
     const double tau0pow = powr(A.tau0, A.alpha);
     int choice;
     if (A.fallback == 0) {
         double bw = -1.0;
         int bc = 0x7fffffff;
-        if (A.initialized) boosted_neighbours(A, a, cur, bits, touched, lane, qx, qy, tau0pow, bw, bc);
+        if (A.initialized) boosted_neighbours(A, a, cur, bits, sh, lane, qx, qy, tau0pow, bw, bc);
         if (partial) remaining_argmax(A, a, cur, bits, ucount, lane, qx, qy, tau0pow, bw, bc);
         else nearest_unvisited(A, cur, bits, lane, qx, qy, tau0pow, bw, bc);
         warp_argmax(bw, bc);
         choice = bc;
         if (bw < 0.0) choice = -1;
     } else {
-        choice = wheel_all_unvisited(A, a, cur, u, bits, touched, lane, qx, qy, tau0pow);
+        choice = wheel_all_unvisited(A, a, cur, u, bits, lane, qx, qy, tau0pow);
     }
     if (choice < 0 || choice >= A.n) {
         if (lane == 0) atomicOr(A.errflag, DEVERR_NO_CHOICE);
@@ -355,9 +428,27 @@ __device__ __forceinline__ u128 edge_fix(const double* __restrict__ xy, int i, i
     return len_to_fix(__dsqrt_rn(dist2(xy[2 * i], xy[2 * i + 1], xy[2 * j], xy[2 * j + 1])));
 }
 
+#define STAGE_K 16  // candidate rows are staged in shared memory for even k <= STAGE_K
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Dynamic shared memory of one ant: [staging rows (if staged)] [BoostSmem] [visited bitset].
+__host__ __device__ inline size_t stage_bytes(int k) { return (k <= STAGE_K && !(k & 1)) ? 2 * STAGE_K * STAGE_K * sizeof(CandW) : 0; }
+__host__ __device__ inline size_t boost_offset(int k) { return stage_bytes(k); }
+__host__ __device__ inline size_t bits_offset(int k) { return (boost_offset(k) + sizeof(BoostSmem) + 15) & ~(size_t)15; }
+
 __global__ void __launch_bounds__(32) construct_lbest_kernel(LbestArgs A) {
-    extern __shared__ uint32_t bits[];
-    __shared__ int touched[TOUCH_CAP];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // double-buffered copies of the candidate rows of the current city's unvisited candidates:
+    // the next city is one of them, so its row is in shared memory when the next decision starts
+    CandW(*stage)[STAGE_K][STAGE_K] = reinterpret_cast<CandW(*)[STAGE_K][STAGE_K]>(smem_raw);
+    BoostSmem& boost = *reinterpret_cast<BoostSmem*>(smem_raw + boost_offset(A.k));
+    uint32_t* bits = reinterpret_cast<uint32_t*>(smem_raw + bits_offset(A.k));
     const int a = blockIdx.x, lane = threadIdx.x;
     const int n = A.n, k = A.k;
     const int W = (n + 31) >> 5;
@@ -415,15 +506,22 @@ __global__ void __launch_bounds__(32) construct_lbest_kernel(LbestArgs A) {
     }
     __syncwarp();
     const int outbase = partial ? 0 : 1;
+    const bool staged = (k <= STAGE_K) && !(k & 1);
+    const int scan_lim = k <= 16 ? 16 : 32;  // Kogge-Stone levels needed for k lanes
     double my_u = 0.0;
     float my_uf = 0.f;
     unsigned long long nfall = 0, nres = 0;
-    const CandW* rowp = A.candw + (size_t)cur * k;
+    const CandW* rowp = A.candw + (size_t)cur * k;  // current row (global or a staged copy)
+    int wb = 0;                                      // staging buffer written this step
     for (int t = 0; t < steps; ++t) {
         if ((t & 31) == 0) {
             const Draw4 d = aco_draw(A.seed, (uint32_t)(t + lane), a, A.iteration, PURPOSE_WHEEL);
             my_u = unit53(d.x0, d.x1);
             my_uf = __double2float_rn(my_u);
+        }
+        if (staged) {  // copies issued in the previous step have landed
+            cp_async_wait_all();
+            __syncwarp();
         }
         int c = -1;
         float w = 0.f;
@@ -433,12 +531,13 @@ __global__ void __launch_bounds__(32) construct_lbest_kernel(LbestArgs A) {
             c = e.city;
             w = e.w;
             feas = !is_visited(bits, c);
-            if (feas) {
-                const CandW* nr = A.candw + (size_t)c * k;
-                prefetch_l1(nr);
-                if (k > 16) prefetch_l1(nr + k - 1);
+            if (feas && staged) {
+                const CandW* src = A.candw + (size_t)c * k;
+                CandW* dst = &stage[wb][lane][0];
+                for (int q = 0; q < k; q += 2) cp_async16(dst + q, src + q);
             }
         }
+        if (staged) cp_async_commit();
         const unsigned fmask = __ballot_sync(FULL, feas);
         int pick = -1;
         if (fmask) {
@@ -447,13 +546,15 @@ __global__ void __launch_bounds__(32) construct_lbest_kernel(LbestArgs A) {
                 float S = feas ? w : 0.f;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    const float v = __shfl_up_sync(FULL, S, o);
-                    if (lane >= o) S = __fadd_rn(S, v);
+                    if (o < scan_lim) {
+                        const float v = __shfl_up_sync(FULL, S, o);
+                        if (lane >= o) S = __fadd_rn(S, v);
+                    }
                 }
-                const float T = __shfl_sync(FULL, S, 31);
+                const float T = __shfl_sync(FULL, S, scan_lim - 1);
                 const float tf = __fmul_rn(__shfl_sync(FULL, my_uf, t & 31), T);
-                const unsigned gt = __ballot_sync(FULL, feas && S > tf);
                 const float lo_all = __shfl_up_sync(FULL, S, 1);
+                const unsigned gt = __ballot_sync(FULL, feas && S > tf);
                 exact = true;
                 if (gt) {
                     const int r = __ffs(gt) - 1;
@@ -474,11 +575,13 @@ __global__ void __launch_bounds__(32) construct_lbest_kernel(LbestArgs A) {
         int j;
         if (pick >= 0) {
             j = __shfl_sync(FULL, c, pick);
+            rowp = staged ? &stage[wb][pick][0] : A.candw + (size_t)j * k;
         } else {
             ++nfall;
-            j = exhausted_choice(A, a, cur, __shfl_sync(FULL, my_u, t & 31), partial, ucount, bits, touched, lane);
+            j = exhausted_choice(A, a, cur, __shfl_sync(FULL, my_u, t & 31), partial, ucount, bits, boost, lane);
+            rowp = A.candw + (size_t)j * k;
         }
-        rowp = A.candw + (size_t)j * k;
+        wb ^= 1;
         if (lane == 0) {
             bits[j >> 5] |= 1u << (j & 31);
             seg[outbase + t] = j;
@@ -486,6 +589,7 @@ __global__ void __launch_bounds__(32) construct_lbest_kernel(LbestArgs A) {
         __syncwarp();
         cur = j;
     }
+    if (staged) cp_async_wait_all();
     __syncwarp();
     // exact length of the new tour
     u128 acc_new = 0, acc_old = 0;
@@ -532,11 +636,12 @@ aco_status launch_construct_lbest(aco_instance* inst, int32_t iteration) {
     A.ucap = inst->ucap; A.coord_r = inst->coord_r;
     A.xy = inst->xy; A.xy32 = inst->xy32; A.grid = inst->grid_dev; A.city_cell = inst->city_cell;
     A.cell_start = inst->cell_start; A.cell_city = inst->cell_city; A.cell_xy = inst->cell_xy; A.candw = inst->candw;
-    A.W64 = inst->W64; A.lbest = inst->lbest; A.nb = inst->nb; A.q = inst->q; A.cfix = inst->cfix;
+    A.W64 = inst->W64; A.lbest = inst->lbest; A.nb = inst->nb; A.nbrank = inst->nbrank;
+    A.q = inst->q; A.cfix = inst->cfix;
     A.seg = inst->seg; A.antit = inst->antit; A.accq = inst->accq; A.ulist = inst->ulist; A.uxy = inst->uxy;
     A.counters = inst->counters; A.errflag = inst->errflag;
-    const size_t smem = sizeof(uint32_t) * (size_t)((p.n + 31) / 32);
-    if (smem > 40 * 1024) {
+    const size_t smem = bits_offset(p.k) + sizeof(uint32_t) * (size_t)((p.n + 31) / 32);
+    if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(construct_lbest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return set_err(inst, ACO_ERR_CUDA, "smem attribute: %s", cudaGetErrorString(e));
