@@ -49,7 +49,7 @@ static void free_all(aco_instance* inst) {
                     inst->nb, inst->nbrank, inst->clen, inst->cfix, inst->q, inst->gbest, inst->gbest_ant,
                     inst->seg, inst->antit, inst->accq, inst->tau, inst->etab_d, inst->W64d, inst->W32d,
                     inst->tours, inst->succ_d, inst->pred_d, inst->counters, inst->errflag, inst->xy32,
-                    inst->ulist, inst->uxy};
+                    inst->ulist, inst->uxy, inst->bel, inst->btx, inst->btq};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -136,7 +136,10 @@ extern "C" aco_status aco_create_instance(const double* xy_dev, const aco_params
         ok &= dalloc(&inst->q, m, &total);
         ok &= dalloc(&inst->seg, m * n, &total);
         ok &= dalloc(&inst->antit, m, &total);
-        ok &= dalloc(&inst->accq, m * n, &total);
+        if (p->fallback == 1) ok &= dalloc(&inst->accq, m * n, &total);
+        ok &= dalloc(&inst->bel, m * 2 * m, &total);
+        ok &= dalloc(&inst->btx, m * 2 * m, &total);
+        ok &= dalloc(&inst->btq, m * 2 * m, &total);
         long long fm = (long long)floor(p->max_mod_frac * (double)n);
         long long pmin = n - fm;
         if (pmin < 1) pmin = 1;
@@ -167,7 +170,7 @@ extern "C" aco_status aco_create_instance(const double* xy_dev, const aco_params
     cudaMemsetAsync(inst->counters, 0, sizeof(unsigned long long) * CNT_N, s);
     cudaMemsetAsync(inst->errflag, 0, sizeof(int), s);
     if (p->mode == ACO_MODE_LBEST_PARTIAL) {
-        cudaMemsetAsync(inst->accq, 0, sizeof(unsigned long long) * m * n, s);
+        if (inst->accq) cudaMemsetAsync(inst->accq, 0, sizeof(unsigned long long) * m * n, s);
         cudaMemsetAsync(inst->nb, 0xFF, sizeof(int32_t) * 2 * n * m, s);
         cudaMemsetAsync(inst->nbrank, 0xFF, 2 * n * m, s);
     }

@@ -220,7 +220,10 @@ struct aco_instance {
     int32_t* gbest_ant;        // 1
     int32_t* seg;          // m*n new cities of the iteration
     AntIter* antit;        // m
-    unsigned long long* accq;  // m*n scratch of the exhausted-list rule (kept zero between uses)
+    unsigned long long* accq;  // m*n scratch of the fallback = 1 wheel (kept zero between uses)
+    unsigned short* bel;       // m*2m per-ant list of non-candidate neighbour entries
+    int32_t* btx;              // m*2m per-ant list of unvisited non-candidate neighbours
+    unsigned long long* btq;   // m*2m and the weight of the ant of each such entry
     float2* xy32;          // n FP32 coordinates (distance screen of the exhausted-list rule)
     int32_t* ulist;        // m*ucap remaining discarded cities of each ant's partial rebuild
     float2* uxy;           // m*ucap their FP32 coordinates

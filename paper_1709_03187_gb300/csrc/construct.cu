@@ -29,8 +29,6 @@
 #include "common.cuh"
 
 #define FULL 0xffffffffu
-#define TOUCH_CAP 96   // unvisited non-candidate neighbour entries listed per exhausted step
-#define ELIST_CAP 768  // non-candidate neighbour entries listed per exhausted step
 
 struct LbestArgs {
     int n, m, k;
@@ -39,6 +37,8 @@ struct LbestArgs {
     int fallback, iteration, initialized;
     int ucap;       // capacity of the per-ant remaining-city list
     float coord_r;  // max |coordinate| (FP32 screen error bound)
+    int ia, ib;     // alpha, beta as small integers (0..16) for the FP32 screen, else -1
+    float tau0f, tau0powf;  // tau0 and tau0^alpha in FP32
     const double* __restrict__ xy;
     const float2* __restrict__ xy32;
     const GridDesc* __restrict__ grid;
@@ -56,6 +56,9 @@ struct LbestArgs {
     int* __restrict__ seg;
     AntIter* __restrict__ antit;
     unsigned long long* __restrict__ accq;
+    unsigned short* __restrict__ bel;
+    int* __restrict__ btx;
+    unsigned long long* __restrict__ btq;
     int* __restrict__ ulist;
     float2* __restrict__ uxy;
     unsigned long long* __restrict__ counters;
@@ -103,113 +106,210 @@ __device__ __forceinline__ void warp_argmax(double& w, int& c) {
     }
 }
 
-// Unvisited l_best neighbours of `cur` that are not candidates, with their exact boosted
-// weight: argmax into (bw, bc).  Only entries whose candidate rank is 0xFF (the neighbour is not
-// a candidate) can be unvisited here.  Phase A reads the whole 2-byte rank row of `cur` at once
-// and lists those entries in shared memory; phase B gathers their neighbour ids together, so the
-// step costs about two memory round trips.  accq (per ant, city-indexed, zero between uses) sums
-// the integer pheromone per city; the touched cities are listed in shared memory and cleared
-// afterwards.
+// ---------------------------------------------------------------- FP32-screened exhausted step
+// FP32 estimate of tau^alpha eta^beta from an FP32 tau and squared distance (integer exponents).
+__device__ __forceinline__ float weight_f32(float tauf, float d2f, int ia, int ib) {
+    float tp = 1.f;
+    for (int i = 0; i < ia; ++i) tp = __fmul_rn(tp, tauf);
+    float e = 1.f;
+    if ((ib & 1) == 0) {
+        const float inv = __frcp_rn(d2f);
+        for (int i = 0; i < (ib >> 1); ++i) e = __fmul_rn(e, inv);
+    } else {
+        const float inv = rsqrtf(d2f);
+        for (int i = 0; i < ib; ++i) e = __fmul_rn(e, inv);
+    }
+    return __fmul_rn(tp, e);
+}
+
+__device__ __forceinline__ void top2_push(float w, int x, float& w1, int& x1, float& w2) {
+    if (w > w1 || (w == w1 && x < x1)) {
+        w2 = w1;
+        w1 = w;
+        x1 = x;
+    } else if (w > w2) {
+        w2 = w;
+    }
+}
+
+// Unvisited l_best neighbours of `cur` that are not candidates.  Only entries whose candidate
+// rank is 0xFF (the neighbour is not a candidate) can be unvisited at an exhausted step.  Phase A
+// lists those entries of the 2-byte rank row of `cur` (the row is usually requested into
+// registers before the remaining-city scan, so its latency overlaps that scan); phase B gathers
+// their neighbour ids together and lists the unvisited ones with the weight of the ant each entry
+// belongs to.  The lists are per-ant global scratch of capacity 2m (every entry fits) and are
+// filled with warp-aggregated offsets.  The integer pheromone of a city is the sum of the weights
+// of its entries.
+#define TOUCH_SM 96  // touched lists up to this length are aggregated in shared memory
+
 struct BoostSmem {
-    unsigned short elist[ELIST_CAP];
-    int touched[TOUCH_CAP];
-    int ecount, tcount;
+    int tx[TOUCH_SM];
+    unsigned long long tq[TOUCH_SM];
 };
 
-__device__ void boosted_neighbours(const LbestArgs& A, int a, int cur, const uint32_t* bits, BoostSmem& sh, int lane,
-                                   double qx, double qy, double tau0pow, double& bw, int& bc) {
-    unsigned long long* acc = A.accq + (size_t)a * A.n;
+// For 2m <= 2048 (m a multiple of 8) each lane holds 64 bytes of the rank row.
+struct RankRow {
+    uint4 v[4];
+};
+
+__device__ __forceinline__ void load_rank_row(const LbestArgs& A, int cur, int lane, RankRow& rr) {
+    const uint8_t* rrow = A.nbrank + (size_t)cur * A.m * 2;
+    const int E = 2 * A.m;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const int b0 = h * 512 + lane * 16;
+        rr.v[h] = b0 < E ? __ldcs(reinterpret_cast<const uint4*>(rrow + b0)) : make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// Offsets for a warp-wide append: lane contributes `cnt` items; returns where they go and adds
+// the warp total to `total`.
+__device__ __forceinline__ int warp_offsets(int cnt, int& total, int lane) {
+    int inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += v;
+    }
+    const int base = total + inc - cnt;
+    total += __shfl_sync(FULL, inc, 31);
+    return base;
+}
+
+// Phase A over one 2048-byte block of the rank row held in registers.
+__device__ __forceinline__ void list_nonc(unsigned short* el, int& ne, const RankRow& rr, int base, int lane) {
+    uint32_t msk[16];
+    int c = 0;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const uint32_t wv[4] = {rr.v[h].x, rr.v[h].y, rr.v[h].z, rr.v[h].w};
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            msk[h * 4 + g] = __vcmpeq4(wv[g], 0xFFFFFFFFu);  // 0xFF in every byte equal to 0xFF
+            c += __popc(msk[h * 4 + g]) >> 3;
+        }
+    }
+    int off = warp_offsets(c, ne, lane);
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const int b0 = base + h * 512 + lane * 16;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            uint32_t mm = msk[h * 4 + g];
+            while (mm) {
+                const int byte = (__ffs(mm) - 1) >> 3;
+                mm &= ~(0xFFu << (8 * byte));
+                el[off++] = (unsigned short)(b0 + 4 * g + byte);
+            }
+        }
+    }
+}
+
+// Lists the unvisited non-candidate l_best neighbours of `cur` with their ant's weight in the
+// ant's scratch (tx, tq); returns their number.
+__device__ int collect_boosted(const LbestArgs& A, int a, int cur, const uint32_t* bits, int lane, const RankRow* pre) {
+    const size_t cap = (size_t)2 * A.m;
+    unsigned short* el = A.bel + (size_t)a * cap;
+    int* tx = A.btx + (size_t)a * cap;
+    unsigned long long* tq = A.btq + (size_t)a * cap;
     const uint8_t* rrow = A.nbrank + (size_t)cur * A.m * 2;
     const int* irow = A.nb + (size_t)cur * A.m * 2;
     const int E = 2 * A.m;  // entries: (ant, side) -> index 2*ant + side
-    if (lane == 0) { sh.ecount = 0; sh.tcount = 0; }
-    __syncwarp();
-    // phase A: list the non-candidate entries
-    if ((A.m & 7) == 0) {
+    int ne = 0;
+    if (pre) {
+        list_nonc(el, ne, *pre, 0, lane);
+    } else if ((A.m & 7) == 0) {
         for (int base = 0; base < E; base += 2048) {
-            uint4 v[4];
+            RankRow rr;
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
                 const int b0 = base + h * 512 + lane * 16;
-                v[h] = b0 < E ? *reinterpret_cast<const uint4*>(rrow + b0) : make_uint4(0u, 0u, 0u, 0u);
+                rr.v[h] = b0 < E ? __ldcs(reinterpret_cast<const uint4*>(rrow + b0)) : make_uint4(0u, 0u, 0u, 0u);
             }
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int b0 = base + h * 512 + lane * 16;
-                const uint32_t wv[4] = {v[h].x, v[h].y, v[h].z, v[h].w};
-#pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    uint32_t msk = __vcmpeq4(wv[g], 0xFFFFFFFFu);  // 0xFF in every byte equal to 0xFF
-                    while (msk) {
-                        const int byte = (__ffs(msk) - 1) >> 3;
-                        msk &= ~(0xFFu << (8 * byte));
-                        const int pos = atomicAdd(&sh.ecount, 1);
-                        if (pos < ELIST_CAP) sh.elist[pos] = (unsigned short)(b0 + 4 * g + byte);
-                    }
-                }
-            }
+            list_nonc(el, ne, rr, base, lane);
         }
     } else {
-        for (int e = lane; e < E; e += 32)
-            if (rrow[e] == 0xFF) {
-                const int pos = atomicAdd(&sh.ecount, 1);
-                if (pos < ELIST_CAP) sh.elist[pos] = (unsigned short)e;
+        for (int e0 = 0; e0 < E; e0 += 32) {
+            const int e = e0 + lane;
+            const bool f = e < E && rrow[e] == 0xFF;
+            int off = warp_offsets(f ? 1 : 0, ne, lane);
+            if (f) el[off] = (unsigned short)e;
+        }
+    }
+    __syncwarp();
+    int nt = 0;
+    for (int t0 = 0; t0 < ne; t0 += 128) {
+        int e4[4], x4[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int idx = t0 + 32 * h + lane;
+            e4[h] = idx < ne ? (int)el[idx] : -1;
+            x4[h] = e4[h] >= 0 ? __ldcs(irow + e4[h]) : -1;
+        }
+        int c = 0;
+        bool un[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            un[h] = x4[h] >= 0 && !is_visited(bits, x4[h]);
+            c += un[h] ? 1 : 0;
+        }
+        int off = warp_offsets(c, nt, lane);
+#pragma unroll
+        for (int h = 0; h < 4; ++h)
+            if (un[h]) {
+                tx[off] = x4[h];
+                tq[off] = A.q[e4[h] >> 1];
+                ++off;
             }
     }
     __syncwarp();
-    const int total_e = sh.ecount;
-    auto touch = [&](int x, int e) {
-        if (!is_visited(bits, x)) {
-            atomicAdd(&acc[x], A.q[e >> 1]);
-            const int pos = atomicAdd(&sh.tcount, 1);
-            if (pos < TOUCH_CAP) sh.touched[pos] = x;
+    return nt;
+}
+
+// Argmax over the listed cities of their weight: FP32 estimates into a top-2 (fast path) or exact
+// FP64 weights into (bw, bc).  Duplicated cities are evaluated once, with the sum of the weights
+// of all their entries.
+template <bool EXACT>
+__device__ void boosted_eval(const LbestArgs& A, int a, int cur, int nt, BoostSmem& sh, int lane, double qx,
+                             double qy, double tau0pow, double& bw, int& bc, float& w1, int& x1, float& w2,
+                             float& dmin) {
+    const size_t cap = (size_t)2 * A.m;
+    const int* gx = A.btx + (size_t)a * cap;
+    const unsigned long long* gq = A.btq + (size_t)a * cap;
+    const bool in_smem = nt <= TOUCH_SM;
+    if (in_smem) {
+        for (int t = lane; t < nt; t += 32) {
+            sh.tx[t] = gx[t];
+            sh.tq[t] = gq[t];
         }
-    };
-    if (total_e <= ELIST_CAP) {
-        // phase B: gather the listed neighbour ids, four per lane in flight
-        for (int t0 = 0; t0 < total_e; t0 += 128) {
-            int e4[4], x4[4];
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int idx = t0 + 32 * h + lane;
-                e4[h] = idx < total_e ? (int)sh.elist[idx] : -1;
-                x4[h] = e4[h] >= 0 ? irow[e4[h]] : -1;
-            }
-#pragma unroll
-            for (int h = 0; h < 4; ++h)
-                if (x4[h] >= 0) touch(x4[h], e4[h]);
-        }
-    } else {  // very many non-candidate entries: gather them inline
-        for (int e = lane; e < E; e += 32)
-            if (rrow[e] == 0xFF) touch(irow[e], e);
+        __syncwarp();
     }
-    __syncwarp();
-    const int total = sh.tcount;
-    const int nt = total < TOUCH_CAP ? total : TOUCH_CAP;
+    const int* tx = in_smem ? sh.tx : gx;
+    const unsigned long long* tq = in_smem ? sh.tq : gq;
+    const float2 q32 = A.xy32[cur];
     for (int t = lane; t < nt; t += 32) {
-        const int x = sh.touched[t];
-        const double d2 = dist2(qx, qy, A.xy[2 * x], A.xy[2 * x + 1]);
-        const double w = weight_of(A, tau0pow, __ldcg(&acc[x]), d2);
-        if (better(w, x, bw, bc)) { bw = w; bc = x; }
-    }
-    if (total > TOUCH_CAP) {  // rare: more touched entries than the list holds -- rescan the row
-        for (int e = lane; e < E; e += 32) {
-            if (rrow[e] != 0xFF) continue;
-            const int x = irow[e];
-            if (is_visited(bits, x)) continue;
+        const int x = tx[t];
+        unsigned long long Qx = 0;
+        bool first = true;
+        for (int u = 0; u < nt; ++u)
+            if (tx[u] == x) {
+                Qx += tq[u];
+                first = first && u >= t;
+            }
+        if (!first) continue;
+        if (EXACT) {
             const double d2 = dist2(qx, qy, A.xy[2 * x], A.xy[2 * x + 1]);
-            const double w = weight_of(A, tau0pow, __ldcg(&acc[x]), d2);
+            const double w = weight_of(A, tau0pow, Qx, d2);
             if (better(w, x, bw, bc)) { bw = w; bc = x; }
+        } else {
+            const float2 px = A.xy32[x];
+            const float dx = __fsub_rn(px.x, q32.x), dy = __fsub_rn(px.y, q32.y);
+            const float d2f = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+            const float tauf = __fadd_rn(A.tau0f, __fmul_rn(__ull2float_rn(Qx), 0x1.0p-32f));
+            dmin = fminf(dmin, d2f);
+            top2_push(weight_f32(tauf, d2f, A.ia, A.ib), x, w1, x1, w2);
         }
     }
-    __syncwarp();
-    for (int t = lane; t < nt; t += 32) acc[sh.touched[t]] = 0ull;
-    if (total > TOUCH_CAP)
-        for (int e = lane; e < E; e += 32) {
-            if (rrow[e] != 0xFF) continue;
-            const int x = irow[e];
-            if (!is_visited(bits, x)) acc[x] = 0ull;
-        }
     __syncwarp();
 }
 
@@ -398,6 +498,79 @@ __device__ int wheel_all_unvisited(const LbestArgs& A, int a, int cur, double u,
     return choice;
 }
 
+// Exhausted step of a partial rebuild with every weight first estimated in FP32, each with a
+// relative error bound E (FP32 coordinates and distances, reciprocal, powers, tau).  If the best
+// estimate beats the second best by more than the bounds allow, it is the exact FP64 argmax and
+// is returned without any FP64 work; otherwise -1 (the caller then evaluates exactly).  The
+// remaining list is compacted on the way.
+__device__ int partial_choice_fast(const LbestArgs& A, int a, int cur, const uint32_t* bits, int& ucount, BoostSmem& sh,
+                                   int lane, const RankRow* pre) {
+    int* ul = A.ulist + (size_t)a * A.ucap;
+    float2* uxy = A.uxy + (size_t)a * A.ucap;
+    const float2 q32 = A.xy32[cur];
+    float w1 = -1.f, w2 = -1.f, dmin = FLT_MAX;
+    int x1 = 0x7fffffff;
+    int cnt = 0;
+    for (int base = 0; base < ucount; base += 256) {
+        int id[8];
+        float2 p[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const int idx = base + 32 * h + lane;
+            id[h] = -1;
+            p[h] = make_float2(0.f, 0.f);
+            if (idx < ucount) {
+                id[h] = ul[idx];
+                p[h] = uxy[idx];
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const bool keep = id[h] >= 0 && !is_visited(bits, id[h]);
+            const unsigned b = __ballot_sync(FULL, keep);
+            if (keep) {
+                const int pos = cnt + __popc(b & ((1u << lane) - 1u));
+                ul[pos] = id[h];
+                uxy[pos] = p[h];
+                const float dx = __fsub_rn(p[h].x, q32.x), dy = __fsub_rn(p[h].y, q32.y);
+                const float d2f = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+                dmin = fminf(dmin, d2f);
+                top2_push(__fmul_rn(A.tau0powf, weight_f32(1.f, d2f, 0, A.ib)), id[h], w1, x1, w2);
+            }
+            cnt += __popc(b);
+        }
+    }
+    ucount = cnt;
+    __syncwarp();
+    if (A.initialized) {
+        const int nt = collect_boosted(A, a, cur, bits, lane, pre);
+        double bwd = -1.0;
+        int bcd = 0x7fffffff;
+        boosted_eval<false>(A, a, cur, nt, sh, lane, 0.0, 0.0, 0.0, bwd, bcd, w1, x1, w2, dmin);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const float ow1 = __shfl_xor_sync(FULL, w1, o), ow2 = __shfl_xor_sync(FULL, w2, o);
+        const int ox1 = __shfl_xor_sync(FULL, x1, o);
+        dmin = fminf(dmin, __shfl_xor_sync(FULL, dmin, o));
+        if (ow1 > w1 || (ow1 == w1 && ox1 < x1)) {
+            w2 = fmaxf(w1, ow2);
+            w1 = ow1;
+            x1 = ox1;
+        } else {
+            w2 = fmaxf(w2, ow1);
+        }
+    }
+    if (!(dmin >= 1e-30f) || !(w1 > 0.f) || !(w1 <= FLT_MAX)) return -1;
+    // relative error bound of every estimate (largest at the smallest distance)
+    const float eps_d = __fdiv_rn(__fmul_rn(1.1f, d2_bound(dmin, A.coord_r)), dmin);
+    const float E = __fmul_rn(1.25f, __fadd_rn(__fmul_rn(0.5f * (float)A.ib + 0.5f, eps_d),
+                                               __fmul_rn((float)(A.ib + A.ia + 4), 0x1.0p-22f)));
+    if (!(E < 0.25f)) return -1;
+    if (__fmul_rn(w1, 1.f - E) > __fmul_rn(w2, 1.f + E)) return x1;
+    return -1;
+}
+
 // Exhausted-list rule.  Returns the chosen city (uniform across the warp).
 __device__ int exhausted_choice(const LbestArgs& A, int a, int cur, double u, bool partial, int& ucount,
                                 const uint32_t* bits, BoostSmem& sh, int lane) {
@@ -407,9 +580,22 @@ __device__ int exhausted_choice(const LbestArgs& A, int a, int cur, double u, bo
     if (A.fallback == 0) {
         double bw = -1.0;
         int bc = 0x7fffffff;
-        if (A.initialized) boosted_neighbours(A, a, cur, bits, sh, lane, qx, qy, tau0pow, bw, bc);
+        // the rank row of `cur` is requested first; its latency overlaps the scan below
+        RankRow rr;
+        const bool pre = A.initialized && (A.m & 7) == 0 && A.m <= 1024;
+        if (pre) load_rank_row(A, cur, lane, rr);
+        if (partial && A.ia >= 0 && A.ib >= 0) {
+            const int fast = partial_choice_fast(A, a, cur, bits, ucount, sh, lane, pre ? &rr : nullptr);
+            if (fast >= 0) return fast;
+        }
         if (partial) remaining_argmax(A, a, cur, bits, ucount, lane, qx, qy, tau0pow, bw, bc);
         else nearest_unvisited(A, cur, bits, lane, qx, qy, tau0pow, bw, bc);
+        if (A.initialized) {
+            const int nt = collect_boosted(A, a, cur, bits, lane, pre ? &rr : nullptr);
+            float f1 = -1.f, f2 = -1.f, fd = FLT_MAX;
+            int fx = 0;
+            boosted_eval<true>(A, a, cur, nt, sh, lane, qx, qy, tau0pow, bw, bc, f1, fx, f2, fd);
+        }
         warp_argmax(bw, bc);
         choice = bc;
         if (bw < 0.0) choice = -1;
@@ -430,9 +616,16 @@ __device__ __forceinline__ u128 edge_fix(const double* __restrict__ xy, int i, i
 
 #define STAGE_K 16  // candidate rows are staged in shared memory for even k <= STAGE_K
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+// 16-byte async copy global -> shared, cached in L2 only, with an L2 eviction-priority policy
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, unsigned long long policy) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "l"(policy)
+                 : "memory");
+}
+__device__ __forceinline__ unsigned long long evict_last_policy() {
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
@@ -442,7 +635,7 @@ __host__ __device__ inline size_t stage_bytes(int k) { return (k <= STAGE_K && !
 __host__ __device__ inline size_t boost_offset(int k) { return stage_bytes(k); }
 __host__ __device__ inline size_t bits_offset(int k) { return (boost_offset(k) + sizeof(BoostSmem) + 15) & ~(size_t)15; }
 
-__global__ void __launch_bounds__(32) construct_lbest_kernel(LbestArgs A) {
+__global__ void __launch_bounds__(32, 8) construct_lbest_kernel(LbestArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // double-buffered copies of the candidate rows of the current city's unvisited candidates:
     // the next city is one of them, so its row is in shared memory when the next decision starts
@@ -507,6 +700,7 @@ __global__ void __launch_bounds__(32) construct_lbest_kernel(LbestArgs A) {
     __syncwarp();
     const int outbase = partial ? 0 : 1;
     const bool staged = (k <= STAGE_K) && !(k & 1);
+    const unsigned long long keep_pol = evict_last_policy();  // the candidate table stays in L2
     const int scan_lim = k <= 16 ? 16 : 32;  // Kogge-Stone levels needed for k lanes
     double my_u = 0.0;
     float my_uf = 0.f;
@@ -534,7 +728,7 @@ __global__ void __launch_bounds__(32) construct_lbest_kernel(LbestArgs A) {
             if (feas && staged) {
                 const CandW* src = A.candw + (size_t)c * k;
                 CandW* dst = &stage[wb][lane][0];
-                for (int q = 0; q < k; q += 2) cp_async16(dst + q, src + q);
+                for (int q = 0; q < k; q += 2) cp_async16(dst + q, src + q, keep_pol);
             }
         }
         if (staged) cp_async_commit();
@@ -634,11 +828,17 @@ aco_status launch_construct_lbest(aco_instance* inst, int32_t iteration) {
     A.alpha = p.alpha; A.beta = p.beta; A.tau0 = p.tau0; A.f = p.max_mod_frac; A.p_partial = p.p_partial;
     A.seed = p.seed; A.fallback = p.fallback; A.iteration = iteration; A.initialized = inst->initialized ? 1 : 0;
     A.ucap = inst->ucap; A.coord_r = inst->coord_r;
+    const bool ia_ok = p.alpha >= 0 && p.alpha <= 16 && floor(p.alpha) == p.alpha;
+    const bool ib_ok = p.beta >= 0 && p.beta <= 16 && floor(p.beta) == p.beta;
+    A.ia = ia_ok ? (int)p.alpha : -1;
+    A.ib = ib_ok ? (int)p.beta : -1;
+    A.tau0f = (float)p.tau0;
+    A.tau0powf = (float)pow(p.tau0, ia_ok ? (double)(int)p.alpha : p.alpha);
     A.xy = inst->xy; A.xy32 = inst->xy32; A.grid = inst->grid_dev; A.city_cell = inst->city_cell;
     A.cell_start = inst->cell_start; A.cell_city = inst->cell_city; A.cell_xy = inst->cell_xy; A.candw = inst->candw;
     A.W64 = inst->W64; A.lbest = inst->lbest; A.nb = inst->nb; A.nbrank = inst->nbrank;
     A.q = inst->q; A.cfix = inst->cfix;
-    A.seg = inst->seg; A.antit = inst->antit; A.accq = inst->accq; A.ulist = inst->ulist; A.uxy = inst->uxy;
+    A.seg = inst->seg; A.antit = inst->antit; A.accq = inst->accq; A.bel = inst->bel; A.btx = inst->btx; A.btq = inst->btq; A.ulist = inst->ulist; A.uxy = inst->uxy;
     A.counters = inst->counters; A.errflag = inst->errflag;
     const size_t smem = bits_offset(p.k) + sizeof(uint32_t) * (size_t)((p.n + 31) / 32);
     if (smem > 48 * 1024) {

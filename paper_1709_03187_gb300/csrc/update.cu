@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(256) rebuild_kernel(int n, int m, int k, doubl
                 for (int base = 0; base < m; base += 256) {
                     const int a0 = base + lane * 8;
                     if (a0 < m) {
-                        const uint4 v = *reinterpret_cast<const uint4*>(row + 2 * (size_t)a0);
+                        const uint4 v = __ldcs(reinterpret_cast<const uint4*>(row + 2 * (size_t)a0));
                         const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                         for (int h = 0; h < 4; ++h) {
