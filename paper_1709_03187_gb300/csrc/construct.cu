@@ -276,6 +276,38 @@ __device__ void boosted_eval(const LbestArgs& A, int a, int cur, int nt, BoostSm
     const size_t cap = (size_t)2 * A.m;
     const int* gx = A.btx + (size_t)a * cap;
     const unsigned long long* gq = A.btq + (size_t)a * cap;
+    if (nt <= 32) {  // one entry per lane; equal cities grouped by a match
+        const int x = lane < nt ? gx[lane] : -1 - lane;
+        const unsigned long long qq = lane < nt ? gq[lane] : 0ull;
+        const unsigned grp = __match_any_sync(FULL, x);
+        const int gsize = __popc(grp);
+        const int maxg = __reduce_max_sync(FULL, (unsigned)gsize);
+        unsigned long long Qx = 0;
+        unsigned g = grp;
+        for (int it = 0; it < maxg; ++it) {
+            const int src = g ? __ffs(g) - 1 : lane;
+            g &= g - 1;
+            const unsigned long long v = __shfl_sync(FULL, qq, src);
+            if (it < gsize) Qx += v;
+        }
+        if (lane < nt && lane == __ffs(grp) - 1) {
+            if (EXACT) {
+                const double d2 = dist2(qx, qy, A.xy[2 * x], A.xy[2 * x + 1]);
+                const double w = weight_of(A, tau0pow, Qx, d2);
+                if (better(w, x, bw, bc)) { bw = w; bc = x; }
+            } else {
+                const float2 q32 = A.xy32[cur];
+                const float2 px = A.xy32[x];
+                const float dx = __fsub_rn(px.x, q32.x), dy = __fsub_rn(px.y, q32.y);
+                const float d2f = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+                const float tauf = __fadd_rn(A.tau0f, __fmul_rn(__ull2float_rn(Qx), 0x1.0p-32f));
+                dmin = fminf(dmin, d2f);
+                top2_push(weight_f32(tauf, d2f, A.ia, A.ib), x, w1, x1, w2);
+            }
+        }
+        __syncwarp();
+        return;
+    }
     const bool in_smem = nt <= TOUCH_SM;
     if (in_smem) {
         for (int t = lane; t < nt; t += 32) {
@@ -510,6 +542,9 @@ __device__ int partial_choice_fast(const LbestArgs& A, int a, int cur, const uin
     const float2 q32 = A.xy32[cur];
     float w1 = -1.f, w2 = -1.f, dmin = FLT_MAX;
     int x1 = 0x7fffffff;
+    // unboosted cities: the weight only falls with the distance, so keep the two nearest
+    float d1 = FLT_MAX, d2s = FLT_MAX;
+    int y1 = 0x7fffffff;
     int cnt = 0;
     for (int base = 0; base < ucount; base += 256) {
         int id[8];
@@ -530,15 +565,27 @@ __device__ int partial_choice_fast(const LbestArgs& A, int a, int cur, const uin
             const unsigned b = __ballot_sync(FULL, keep);
             if (keep) {
                 const int pos = cnt + __popc(b & ((1u << lane) - 1u));
-                ul[pos] = id[h];
-                uxy[pos] = p[h];
+                if (pos != base + 32 * h + lane) {
+                    ul[pos] = id[h];
+                    uxy[pos] = p[h];
+                }
                 const float dx = __fsub_rn(p[h].x, q32.x), dy = __fsub_rn(p[h].y, q32.y);
                 const float d2f = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-                dmin = fminf(dmin, d2f);
-                top2_push(__fmul_rn(A.tau0powf, weight_f32(1.f, d2f, 0, A.ib)), id[h], w1, x1, w2);
+                if (d2f < d1 || (d2f == d1 && id[h] < y1)) {
+                    d2s = d1;
+                    d1 = d2f;
+                    y1 = id[h];
+                } else if (d2f < d2s) {
+                    d2s = d2f;
+                }
             }
             cnt += __popc(b);
         }
+    }
+    if (d1 < FLT_MAX) {
+        dmin = d1;
+        top2_push(__fmul_rn(A.tau0powf, weight_f32(1.f, d1, 0, A.ib)), y1, w1, x1, w2);
+        if (d2s < FLT_MAX) w2 = fmaxf(w2, __fmul_rn(A.tau0powf, weight_f32(1.f, d2s, 0, A.ib)));
     }
     ucount = cnt;
     __syncwarp();
@@ -574,6 +621,7 @@ __device__ int partial_choice_fast(const LbestArgs& A, int a, int cur, const uin
 // Exhausted-list rule.  Returns the chosen city (uniform across the warp).
 __device__ int exhausted_choice(const LbestArgs& A, int a, int cur, double u, bool partial, int& ucount,
                                 const uint32_t* bits, BoostSmem& sh, int lane) {
+    __syncwarp();  // the previous city's visited bit (set at the top of the step) is visible
     const double qx = A.xy[2 * cur], qy = A.xy[2 * cur + 1];
     const double tau0pow = powr(A.tau0, A.alpha);
     int choice;
@@ -707,6 +755,7 @@ __global__ void __launch_bounds__(32, 8) construct_lbest_kernel(LbestArgs A) {
     unsigned long long nfall = 0, nres = 0;
     const CandW* rowp = A.candw + (size_t)cur * k;  // current row (global or a staged copy)
     int wb = 0;                                      // staging buffer written this step
+    int pend = -1;                                   // chosen city whose visited bit is set next step
     for (int t = 0; t < steps; ++t) {
         if ((t & 31) == 0) {
             const Draw4 d = aco_draw(A.seed, (uint32_t)(t + lane), a, A.iteration, PURPOSE_WHEEL);
@@ -717,6 +766,9 @@ __global__ void __launch_bounds__(32, 8) construct_lbest_kernel(LbestArgs A) {
             cp_async_wait_all();
             __syncwarp();
         }
+        // the previous step's city is marked now: it is not a candidate of itself, and the
+        // warp synchronises before the next candidate test and before any exhausted step
+        if (lane == 0 && pend >= 0) atomicOr(&bits[pend >> 5], 1u << (pend & 31));
         int c = -1;
         float w = 0.f;
         bool feas = false;
@@ -735,31 +787,29 @@ __global__ void __launch_bounds__(32, 8) construct_lbest_kernel(LbestArgs A) {
         const unsigned fmask = __ballot_sync(FULL, feas);
         int pick = -1;
         if (fmask) {
-            bool exact = __any_sync(FULL, lane < k && !(w > 0.f));  // row flagged: screen weights negative
-            if (!exact) {
-                float S = feas ? w : 0.f;
+            float S = feas ? w : 0.f;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    if (o < scan_lim) {
-                        const float v = __shfl_up_sync(FULL, S, o);
-                        if (lane >= o) S = __fadd_rn(S, v);
-                    }
+            for (int o = 1; o < 32; o <<= 1) {
+                if (o < scan_lim) {
+                    const float v = __shfl_up_sync(FULL, S, o);
+                    if (lane >= o) S = __fadd_rn(S, v);
                 }
-                const float T = __shfl_sync(FULL, S, scan_lim - 1);
+            }
+            const float T = __shfl_sync(FULL, S, scan_lim - 1);
+            bool exact = !(T > 0.f);  // a flagged row carries negative screen weights
+            if (!exact) {
                 const float tf = __fmul_rn(__shfl_sync(FULL, my_uf, t & 31), T);
-                const float lo_all = __shfl_up_sync(FULL, S, 1);
-                const unsigned gt = __ballot_sync(FULL, feas && S > tf);
-                exact = true;
-                if (gt) {
-                    const int r = __ffs(gt) - 1;
-                    const float hi = __shfl_sync(FULL, S, r);
-                    const float lo = r > 0 ? __shfl_sync(FULL, lo_all, r) : 0.f;
-                    const float delta = __fmul_rn(T, 0x1.0p-19f);
-                    if (__fsub_rn(tf, lo) > delta && __fsub_rn(hi, tf) > delta) {
-                        pick = r;
-                        exact = false;
-                    }
-                }
+                float prev = __shfl_up_sync(FULL, S, 1);
+                if (lane == 0) prev = 0.f;
+                const float delta = __fmul_rn(T, 0x1.0p-19f);
+                // lane r is the pick when prefix(r-1) <= u*T < prefix(r); it is safe when u*T is
+                // farther than the FP32 error bound from both prefixes
+                const bool isp = feas && S > tf && !(prev > tf);
+                const bool safe = __fsub_rn(tf, prev) > delta && __fsub_rn(S, tf) > delta;
+                const unsigned pm = __ballot_sync(FULL, isp && safe);
+                const unsigned bad = __ballot_sync(FULL, isp && !safe);
+                if (pm && !bad) pick = __ffs(pm) - 1;
+                else exact = true;
             }
             if (exact) {
                 ++nres;
@@ -776,10 +826,8 @@ __global__ void __launch_bounds__(32, 8) construct_lbest_kernel(LbestArgs A) {
             rowp = A.candw + (size_t)j * k;
         }
         wb ^= 1;
-        if (lane == 0) {
-            bits[j >> 5] |= 1u << (j & 31);
-            seg[outbase + t] = j;
-        }
+        if (lane == 0) seg[outbase + t] = j;
+        pend = j;
         __syncwarp();
         cur = j;
     }
