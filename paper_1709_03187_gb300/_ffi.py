@@ -67,6 +67,7 @@ def lib():
             "aco_get_stats": (S, [V, ctypes.POINTER(Stats)]),
             "aco_step_probs": (S, [V, I32, V, V, V]),
             "aco_destroy_instance": (None, [V]),
+            "aco_build_candidates_noalloc": (S, [V, I32, I32, V, V]),
             "aco_status_string": (ctypes.c_char_p, [S]),
             "aco_last_error": (ctypes.c_char_p, [V]),
         }
@@ -141,6 +142,12 @@ def aco_get_stats(h) -> Stats:
 def aco_step_probs(h, city: int, visited_bits_dev, probs_out_dev, exhausted_out_dev):
     _check(lib().aco_step_probs(h, city, _ptr(visited_bits_dev), _ptr(probs_out_dev), _ptr(exhausted_out_dev)),
            "aco_step_probs", h)
+
+
+def aco_build_candidates_noalloc(xy_dev, n: int, k: int, cand_out_dev, stream=None):
+    status = lib().aco_build_candidates_noalloc(_ptr(xy_dev), n, k, _ptr(cand_out_dev), _stream_handle(stream))
+    if status != 0:
+        raise AcoError(status, "aco_build_candidates_noalloc", "")
 
 
 def aco_destroy_instance(h):

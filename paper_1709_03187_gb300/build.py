@@ -23,6 +23,7 @@ UNITS = [
     ("grid_knn.cu", []),
     ("construct.cu", []),
     ("update.cu", []),
+    ("noalloc.cu", []),
 ]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

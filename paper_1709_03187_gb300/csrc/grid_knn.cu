@@ -85,7 +85,8 @@ __device__ __forceinline__ bool key_less(double da, int ja, double db, int jb) {
     return da < db || (da == db && ja < jb);
 }
 
-// One warp per query city.
+// One warp per query city.  LISTS_ONLY: write the candidate lists only (no weight tables).
+template <bool LISTS_ONLY>
 __global__ void __launch_bounds__(256) knn_kernel(const double* __restrict__ xy, const GridDesc* __restrict__ gd,
                                                   const int* __restrict__ city_cell, const int* __restrict__ cell_start,
                                                   const int* __restrict__ cell_city, const double* __restrict__ cell_xy,
@@ -146,11 +147,13 @@ __global__ void __launch_bounds__(256) knn_kernel(const double* __restrict__ xy,
         }
         if (lane < k) {
             cand[(size_t)i * k + lane] = lj;
-            candw[(size_t)i * k + lane].city = lj;
             if (ld == 0.0) atomicOr(errflag, DEVERR_DUPLICATE);
-            const double e = eta_pow_from_d2(ld, beta);
-            if (!isfinite(e)) atomicOr(errflag, DEVERR_NONFINITE);
-            etab[(size_t)i * k + lane] = e;
+            if (!LISTS_ONLY) {
+                candw[(size_t)i * k + lane].city = lj;
+                const double e = eta_pow_from_d2(ld, beta);
+                if (!isfinite(e)) atomicOr(errflag, DEVERR_NONFINITE);
+                etab[(size_t)i * k + lane] = e;
+            }
         }
     }
 }
@@ -200,8 +203,99 @@ aco_status launch_build_grid_and_knn(aco_instance* inst) {
     if (st != ACO_OK) return st;
     const int warps_per_block = 8;
     const int kblocks = (int)fmin((double)inst->num_sms * 16, (double)ceil_div(n, warps_per_block));
-    knn_kernel<<<kblocks, 32 * warps_per_block, 0, s>>>(inst->xy, inst->grid_dev, inst->city_cell, inst->cell_start,
+    knn_kernel<false><<<kblocks, 32 * warps_per_block, 0, s>>>(inst->xy, inst->grid_dev, inst->city_cell, inst->cell_start,
                                                        inst->cell_city, inst->cell_xy, n, inst->p.k, inst->p.beta,
                                                        inst->cand, inst->candw, inst->etab, inst->errflag);
     return check_launch(inst, "knn_kernel");
+}
+
+// ---------------------------------------------------------------- device-only set-up
+// Candidate lists from caller-provided scratch, with the grid sized on the device (no host
+// staging of the coordinates).  Scratch layout (all 16-byte aligned):
+//   GridDesc | errflag | city_cell[n] | cell_fill[cap] | cell_start[cap + 1] | cell_city[n] | cell_xy[2n]
+__global__ void bbox_desc_kernel(const double* __restrict__ xy, int n, int cap_cells, GridDesc* __restrict__ gd,
+                                 int* __restrict__ errflag) {
+    __shared__ double sh[4][32];
+    __shared__ int bad_s;
+    if (threadIdx.x == 0) bad_s = 0;
+    __syncthreads();
+    double xmn = 1e308, xmx = -1e308, ymn = 1e308, ymx = -1e308;
+    bool bad = false;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double x = xy[2 * i], y = xy[2 * i + 1];
+        bad |= !(isfinite(x) && isfinite(y));
+        xmn = fmin(xmn, x); xmx = fmax(xmx, x); ymn = fmin(ymn, y); ymx = fmax(ymx, y);
+    }
+    if (bad) atomicOr(&bad_s, 1);
+    for (int o = 16; o; o >>= 1) {
+        xmn = fmin(xmn, __shfl_xor_sync(FULL, xmn, o));
+        xmx = fmax(xmx, __shfl_xor_sync(FULL, xmx, o));
+        ymn = fmin(ymn, __shfl_xor_sync(FULL, ymn, o));
+        ymx = fmax(ymx, __shfl_xor_sync(FULL, ymx, o));
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { sh[0][w] = xmn; sh[1][w] = xmx; sh[2][w] = ymn; sh[3][w] = ymx; }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+        xmn = fmin(xmn, sh[0][i]); xmx = fmax(xmx, sh[1][i]); ymn = fmin(ymn, sh[2][i]); ymx = fmax(ymx, sh[3][i]);
+    }
+    if (bad_s) { atomicOr(errflag, DEVERR_NONFINITE); xmn = ymn = 0.0; xmx = ymx = 1.0; }
+    // about two cities per cell over the bounding box, as on the host path
+    GridDesc g;
+    g.xmin = xmn; g.xmax = xmx; g.ymin = ymn; g.ymax = ymx;
+    const double wx = fmax(xmx - xmn, 1e-300), wy = fmax(ymx - ymn, 1e-300);
+    const double target = fmax(1.0, (double)(n / 2));
+    double h = sqrt(wx * wy / target);
+    if (!(h > 0)) h = fmax(wx, wy);
+    h = fmax(h, fmax(wx, wy) / 4096.0);
+    int gx = (int)fmin(4096.0, floor(wx / h) + 1), gy = (int)fmin(4096.0, floor(wy / h) + 1);
+    while ((long long)gx * gy > cap_cells) {
+        h *= 1.05;
+        gx = (int)floor(wx / h) + 1;
+        gy = (int)floor(wy / h) + 1;
+    }
+    g.h = h; g.gx = gx; g.gy = gy;
+    g.margin = 1e-6 * h + 1e-14 * (fabs(xmn) + fabs(xmx) + fabs(ymn) + fabs(ymx));
+    *gd = g;
+}
+
+__global__ void zero_ints_kernel(int* __restrict__ v, int count) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) v[i] = 0;
+}
+
+static inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+size_t knn_scratch_bytes(int max_n) {
+    const int cap = max_n / 2 + 16;
+    return align16(sizeof(GridDesc)) + 16 + align16(sizeof(int) * (size_t)max_n) + align16(sizeof(int) * (size_t)cap) +
+           align16(sizeof(int) * (size_t)(cap + 1)) + align16(sizeof(int) * (size_t)max_n) +
+           align16(sizeof(double) * 2 * (size_t)max_n);
+}
+
+// Runs the whole candidate-list build on `scratch` (knn_scratch_bytes(n) bytes) and leaves the
+// device error flags (DEVERR_*) at scratch + align16(sizeof(GridDesc)).
+cudaError_t launch_knn_on_scratch(const double* xy, int n, int k, int32_t* cand, unsigned char* scratch,
+                                  int num_sms, cudaStream_t s) {
+    const int cap = n / 2 + 16;
+    unsigned char* p = scratch;
+    GridDesc* gd = reinterpret_cast<GridDesc*>(p); p += align16(sizeof(GridDesc));
+    int* errflag = reinterpret_cast<int*>(p); p += 16;
+    int* city_cell = reinterpret_cast<int*>(p); p += align16(sizeof(int) * (size_t)n);
+    int* cell_fill = reinterpret_cast<int*>(p); p += align16(sizeof(int) * (size_t)cap);
+    int* cell_start = reinterpret_cast<int*>(p); p += align16(sizeof(int) * (size_t)(cap + 1));
+    int* cell_city = reinterpret_cast<int*>(p); p += align16(sizeof(int) * (size_t)n);
+    double* cell_xy = reinterpret_cast<double*>(p);
+    zero_ints_kernel<<<1, 32, 0, s>>>(errflag, 1);
+    bbox_desc_kernel<<<1, 1024, 0, s>>>(xy, n, cap, gd, errflag);
+    const int blocks = (int)fmin((double)num_sms * 8, (double)ceil_div(n, 256));
+    zero_ints_kernel<<<ceil_div(cap, 256), 256, 0, s>>>(cell_fill, cap);
+    grid_count_kernel<<<blocks, 256, 0, s>>>(xy, n, gd, city_cell, cell_fill);
+    scan_single_block_kernel<<<1, 1024, 0, s>>>(cell_fill, cap, cell_start);
+    zero_ints_kernel<<<ceil_div(cap, 256), 256, 0, s>>>(cell_fill, cap);
+    grid_scatter_kernel<<<blocks, 256, 0, s>>>(xy, n, city_cell, cell_start, cell_fill, cell_city, cell_xy);
+    const int kblocks = (int)fmin((double)num_sms * 16, (double)ceil_div(n, 8));
+    knn_kernel<true><<<kblocks, 256, 0, s>>>(xy, gd, city_cell, cell_start, cell_city, cell_xy, n, k, 0.0, cand,
+                                              nullptr, nullptr, errflag);
+    return cudaGetLastError();
 }
