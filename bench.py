@@ -32,6 +32,10 @@ import numpy as np  # noqa: E402
 import aco_synth  # noqa: E402
 
 METRIC = "city decisions/s and ACO iterations/s at n=200K on 1 GB300; % of mem roofline"
+# DRAM bytes (read + write) per decision of construct_lbest_kernel from one ncu capture of the
+# 200,000-city workload at m = 256 (57.9 MB for 251,025 decisions), valid for the source it was
+# taken on; the bench reports null traffic once construct.cu changes.
+CONSTRUCT_TRAFFIC = {"sha1_12": "04ddac3fafb4", "bytes_per_decision": 57897728.0 / 251025.5}
 L2_FLUSH_BYTES = 512 << 20  # > 126 MB L2
 
 
@@ -113,6 +117,13 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ algorithmic bytes
+def source_sha1(name: str) -> str:
+    import hashlib
+
+    with open(os.path.join(ROOT, "paper_1709_03187_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()[:12]
+
+
 def construct_bytes(decisions: int, k: int, m: int) -> int:
     """Algorithmic bytes of one construction launch.
 
@@ -215,8 +226,13 @@ def run_ours(args):
     }
     dom = "construct_lbest_kernel" if c_avg >= u_avg else "update (commit + gbest_q + rebuild)"
     ach = kernels[dom]["achieved_gbs"]
+    traffic = None
+    if dom == "construct_lbest_kernel" and source_sha1("construct.cu") == CONSTRUCT_TRAFFIC["sha1_12"]:
+        traffic = round(CONSTRUCT_TRAFFIC["bytes_per_decision"] * decisions / launches)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 2), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(ach / hbm_peak, 5), "peak_source": f"{peak_kind} hbm_gbs", "traffic": None,
+                "frac": round(ach / hbm_peak, 5), "peak_source": f"{peak_kind} hbm_gbs", "traffic": traffic,
+                "note": "each ant is a dependent chain of Eq. 1 decisions; a launch lasts as long as the "
+                        "longest chain, so the kernel is latency-bound",
                 "kernels": {kn: {kk: round(v, 4) for kk, v in kv.items()} for kn, kv in kernels.items()}}
 
     e2e = None
