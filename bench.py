@@ -45,7 +45,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="lbest200k", choices=sorted(aco_synth.WORKLOADS))
+    ap.add_argument("--workload", default="lbest200k", choices=sorted(aco_synth.WORKLOADS) + ["batch512"])
     ap.add_argument("--ants", type=int, default=0, help="override m (profiling of smaller cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -397,9 +397,63 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+# ------------------------------------------------------------------ batched form
+def run_batch(args):
+    """512 instances, n log-uniform in [50, 5000] (uniform cities), k = 20, m = min(n, 256),
+    f = 1, 100 iterations each.  Batched: one launch per step over all colonies, CUDA-graph
+    replay, autotuned schedule.  Per-instance: the same calls instance by instance; a stratified
+    sample of instances is timed and scaled to all 512.  Instances/s of the whole job (candidate
+    lists + initial tours + iterations; allocation excluded in both arms)."""
+    import torch
+
+    from paper_1709_03187_gb300 import Batch, Colony
+
+    torch.cuda.set_device(0)
+    count, iters = 512, 100
+    ns = aco_synth.batch_sizes(count, 50, 5000, 4)
+    xys = [aco_synth.uniform(int(n), 4000 + i) for i, n in enumerate(ns)]
+    kw = dict(k=20, alpha=1.0, beta=2.0, tau0=1.0, max_mod_frac=1.0, seed=4)
+    stream = torch.cuda.Stream()
+    b = Batch(xys, m=256, stream=stream, **kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.build_candidates()
+    b.run(0, iters + 1, tune=True)
+    stream.synchronize()
+    t_batch = time.perf_counter() - t0
+    warps, tune_ms = b.schedule()
+    best = b.best()
+    b.close()
+    order = np.argsort(ns)
+    sample = order[np.linspace(0, count - 1, args.cpu_sample if args.cpu_sample <= 64 else 24).astype(int)]
+    t_inst = 0.0
+    for i in sample:
+        n = int(ns[i])
+        col = Colony(xys[i], mode=1, n=n, m=min(n, 256), stream=stream, **dict(kw, seed=4 + int(i)))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        col.build_candidates()
+        for it in range(iters + 1):
+            col.iterate(it)
+        stream.synchronize()
+        t_inst += time.perf_counter() - t0
+        col.close()
+    t_inst_all = t_inst * count / len(sample)
+    out = {"metric": "instances/s (batched form vs per-instance launches)", "workload": "batch512: 512 instances, n "
+           "log-uniform in [50, 5000], uniform cities, k=20, m=min(n,256), f=1, 101 iterations incl. initial tours",
+           "batched_instances_per_s": round(count / t_batch, 2), "batched_s": round(t_batch, 3),
+           "per_instance_instances_per_s": round(count / t_inst_all, 3),
+           "per_instance_s_estimated": round(t_inst_all, 2), "per_instance_sample": int(len(sample)),
+           "speedup": round(t_inst_all / t_batch, 1), "schedule_warps_per_block": warps,
+           "tune_ms": [round(float(x), 3) for x in tune_ms], "mean_gbest": float(np.mean(best))}
+    print(json.dumps(out))
+
+
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.workload == "batch512" and args.impl == "ours":
+        run_batch(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

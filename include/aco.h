@@ -142,6 +142,38 @@ aco_status aco_get_stats(aco_instance* inst, aco_stats* out_host);
 aco_status aco_step_probs(aco_instance* inst, int32_t city, const uint32_t* visited_bits_dev,
                           float* probs_out_dev, int32_t* exhausted_out_dev);
 
+/* ------------------------------------------------------------------ batched colonies
+ * Many independent instances of uneven size solved together: the same method and parameters
+ * per instance (Section 3, Algorithm 1), with all of a batch's colonies advanced by single
+ * launches per step, iterations replayed as a captured CUDA graph, and the launch schedule
+ * (ants per block) chosen by timing live iterations.  Results equal running every instance
+ * alone with the single-colony calls above. */
+typedef struct aco_batch aco_batch; /* opaque */
+
+/* xy_dev: the instances' coordinates concatenated (sum n_i rows of 2 FP64); n_host: count sizes.
+ * p: shared parameters (mode must be ACO_MODE_LBEST_PARTIAL; p->n is ignored; instance i gets
+ * m_i = min(n_i, p->m) ants and seed p->seed + i).  stream: cudaStream_t for all of the batch's
+ * work; NULL makes the batch create its own non-blocking stream (iterations are captured as a
+ * CUDA graph, which the legacy default stream cannot be).  Allocates everything.  Synchronises. */
+aco_status aco_batch_create(const double* xy_dev, const int32_t* n_host, int32_t count, const aco_params* p,
+                            void* stream, aco_batch** out);
+/* Candidate lists and eta^beta tables of every instance (as aco_build_candidates).  Synchronises. */
+aco_status aco_batch_build_candidates(aco_batch* b);
+/* `iterations` iterations of every colony, keyed first_iteration, first_iteration + 1, ...  The
+ * first call builds the initial tours in its first iteration.  tune != 0: the first (up to four)
+ * iterations of the first tuned call are timed with 1, 2, 4 and 8 ants per block and the fastest
+ * schedule is kept.  Enqueued on the batch's stream. */
+aco_status aco_batch_run(aco_batch* b, int32_t first_iteration, int32_t iterations, int32_t tune);
+/* l_best tours (instance i at offset sum_{j<i} m_j n_j, row-major m_i x n_i) and lengths
+ * (offset sum_{j<i} m_j); either pointer may be NULL.  Synchronises. */
+aco_status aco_batch_get_state(aco_batch* b, int32_t* lbest_out_dev, double* clen_out_dev);
+/* C_gbest of every instance (count doubles).  Synchronises. */
+aco_status aco_batch_get_best(aco_batch* b, double* best_len_host);
+/* The schedule in use (ants per block) and the tuning times (4 floats, ms; 0 if not tuned). */
+aco_status aco_batch_schedule(const aco_batch* b, int32_t* warps_out, float* tune_ms_out4);
+const char* aco_batch_last_error(const aco_batch* b);
+void aco_batch_destroy(aco_batch* b);
+
 /* Candidate lists (the same exact lists as aco_build_candidates) for callers that cannot allocate
  * device memory.  The paper has no counterpart: this is a deployment variant of the library.
  * The working memory is a fixed array inside the library (about 1.8 MB per GPU, held until the

@@ -21,9 +21,14 @@ __all__ = [
     "ACO_MODE_DENSE", "ACO_MODE_LBEST_PARTIAL", "AcoError", "Params", "Stats", "Colony", "lib", "library_path",
     "aco_create_instance", "aco_build_candidates", "aco_construct_tours", "aco_update_pheromone",
     "aco_tour_lengths", "aco_get_state", "aco_set_state", "aco_get_stats", "aco_step_probs",
-    "aco_destroy_instance", "aco_build_candidates_noalloc",
+    "aco_destroy_instance", "aco_build_candidates_noalloc", "aco_batch_create", "aco_batch_build_candidates",
+    "aco_batch_run", "aco_batch_get_state", "aco_batch_get_best", "aco_batch_schedule", "aco_batch_destroy",
+    "Batch",
 ]
 
+from .batch import Batch  # noqa: E402
+from ._ffi import (aco_batch_build_candidates, aco_batch_create, aco_batch_destroy, aco_batch_get_best,  # noqa: E402
+                   aco_batch_get_state, aco_batch_run, aco_batch_schedule)
 from ._ffi import (aco_build_candidates, aco_build_candidates_noalloc, aco_construct_tours, aco_create_instance, aco_destroy_instance,  # noqa: E402
                    aco_get_state, aco_get_stats, aco_set_state, aco_step_probs, aco_tour_lengths,
                    aco_update_pheromone)

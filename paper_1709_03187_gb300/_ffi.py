@@ -68,6 +68,14 @@ def lib():
             "aco_step_probs": (S, [V, I32, V, V, V]),
             "aco_destroy_instance": (None, [V]),
             "aco_build_candidates_noalloc": (S, [V, I32, I32, V, V]),
+            "aco_batch_create": (S, [V, V, I32, ctypes.POINTER(Params), V, ctypes.POINTER(V)]),
+            "aco_batch_build_candidates": (S, [V]),
+            "aco_batch_run": (S, [V, I32, I32, I32]),
+            "aco_batch_get_state": (S, [V, V, V]),
+            "aco_batch_get_best": (S, [V, V]),
+            "aco_batch_schedule": (S, [V, V, V]),
+            "aco_batch_last_error": (ctypes.c_char_p, [V]),
+            "aco_batch_destroy": (None, [V]),
             "aco_status_string": (ctypes.c_char_p, [S]),
             "aco_last_error": (ctypes.c_char_p, [V]),
         }
@@ -142,6 +150,57 @@ def aco_get_stats(h) -> Stats:
 def aco_step_probs(h, city: int, visited_bits_dev, probs_out_dev, exhausted_out_dev):
     _check(lib().aco_step_probs(h, city, _ptr(visited_bits_dev), _ptr(probs_out_dev), _ptr(exhausted_out_dev)),
            "aco_step_probs", h)
+
+
+def _bcheck(status: int, where: str, b):
+    if status != 0:
+        msg = lib().aco_batch_last_error(b) if b else b""
+        raise AcoError(status, where, msg.decode() if msg else "")
+
+
+def aco_batch_create(xy_dev, n_host, params: Params, stream=None):
+    import numpy as np
+
+    ns = np.ascontiguousarray(n_host, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _bcheck(lib().aco_batch_create(_ptr(xy_dev), ns.ctypes.data_as(ctypes.c_void_p), int(ns.size),
+                                   ctypes.byref(params), _stream_handle(stream), ctypes.byref(h)),
+            "aco_batch_create", None)
+    return h.value
+
+
+def aco_batch_build_candidates(b):
+    _bcheck(lib().aco_batch_build_candidates(b), "aco_batch_build_candidates", b)
+
+
+def aco_batch_run(b, first_iteration: int, iterations: int, tune: bool = False):
+    _bcheck(lib().aco_batch_run(b, first_iteration, iterations, 1 if tune else 0), "aco_batch_run", b)
+
+
+def aco_batch_get_state(b, lbest_out_dev=None, clen_out_dev=None):
+    _bcheck(lib().aco_batch_get_state(b, _ptr(lbest_out_dev), _ptr(clen_out_dev)), "aco_batch_get_state", b)
+
+
+def aco_batch_get_best(b, count: int):
+    import numpy as np
+
+    out = np.zeros(count, np.float64)
+    _bcheck(lib().aco_batch_get_best(b, out.ctypes.data_as(ctypes.c_void_p)), "aco_batch_get_best", b)
+    return out
+
+
+def aco_batch_schedule(b):
+    import numpy as np
+
+    w = ctypes.c_int32()
+    ms = np.zeros(4, np.float32)
+    _bcheck(lib().aco_batch_schedule(b, ctypes.byref(w), ms.ctypes.data_as(ctypes.c_void_p)), "aco_batch_schedule", b)
+    return int(w.value), ms
+
+
+def aco_batch_destroy(b):
+    if b:
+        lib().aco_batch_destroy(b)
 
 
 def aco_build_candidates_noalloc(xy_dev, n: int, k: int, cand_out_dev, stream=None):

@@ -24,6 +24,7 @@ UNITS = [
     ("construct.cu", []),
     ("update.cu", []),
     ("noalloc.cu", []),
+    ("batch.cu", []),
 ]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -1,0 +1,319 @@
+// batch.cu -- many independent colonies of uneven size in single launches.
+//
+// A batch owns one colony per instance (same parameters, n_i cities, m_i = min(n_i, m) ants,
+// seed + i).  Each iteration is four launches over every colony at once:
+//   construction (ant slots ordered longest instance first; `warps` ants per block),
+//   commit (one block per ant slot), C_gbest and weights (one block per colony),
+//   pheromone rebuild (block map over every colony's cities),
+// plus a one-thread increment of the device iteration counter.  After the initial tours, the
+// iteration is captured once as a CUDA graph and replayed.  The schedule does not change any
+// result (each ant's work is deterministic), so the autotuner times live iterations with 1, 2, 4
+// and 8 ants per block and keeps the fastest.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+
+struct LbestArgs;  // defined in construct.cu
+void fill_lbest_args(const aco_instance* inst, int32_t iteration, LbestArgs& A);
+size_t construct_smem_per_ant(int n, int k);
+cudaError_t launch_construct_batch(const LbestArgs* args, const int2* slot, const int* iteration, int slots,
+                                   int smem_per_ant, int warps, cudaStream_t s);
+void fill_commit_args(const aco_instance* inst, CommitArgs& C);
+void fill_gbest_args(const aco_instance* inst, int keep_prev, GbestArgs& G);
+void fill_rebuild_args(const aco_instance* inst, int use_ants, RebuildArgs& R);
+cudaError_t launch_update_batch(const CommitArgs* cargs, const int2* slot, int slots, const GbestArgs* gargs,
+                                int count, const RebuildArgs* rargs, const int4* blockmap, int rblocks, int m_cap,
+                                int k, cudaStream_t s);
+size_t lbest_args_size();
+void fill_lbest_args_bytes(const aco_instance* inst, int32_t iteration, void* out);
+
+__global__ void bump_iteration_kernel(int* it) { *it += 1; }
+
+static const int kWarpChoices[4] = {1, 2, 4, 8};
+
+struct aco_batch {
+    int count = 0;
+    aco_params p{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;  // created by the batch (the caller passed NULL)
+    std::vector<aco_instance*> inst;
+    std::vector<int> n_i, m_i;
+    std::vector<long long> city_off, ant_off, tour_off;
+    void* d_largs = nullptr;  // LbestArgs[count]
+    CommitArgs* d_cargs = nullptr;
+    GbestArgs* d_gargs = nullptr;
+    RebuildArgs* d_rargs = nullptr;
+    int2* d_slot = nullptr;
+    int4* d_rmap = nullptr;
+    int* d_iter = nullptr;
+    int slots = 0, rblocks = 0, smem_per_ant = 0, m_cap = 0;
+    int warps = 1;
+    bool tuned = false;
+    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool built = false, initialized = false;
+    int iterations = 0;
+    float tune_ms[4] = {0, 0, 0, 0};
+    char err[512] = {0};
+};
+
+static aco_status berr(aco_batch* b, aco_status s, const char* msg) {
+    if (b) snprintf(b->err, sizeof(b->err), "%s", msg);
+    return s;
+}
+
+extern "C" const char* aco_batch_last_error(const aco_batch* b) { return b ? b->err : ""; }
+
+static void free_batch(aco_batch* b) {
+    for (auto& g : b->graph)
+        if (g) cudaGraphExecDestroy(g);
+    for (aco_instance* i : b->inst) aco_destroy_instance(i);
+    void* ptrs[] = {b->d_largs, b->d_cargs, b->d_gargs, b->d_rargs, b->d_slot, b->d_rmap, b->d_iter};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+extern "C" aco_status aco_batch_create(const double* xy_dev, const int32_t* n_host, int32_t count, const aco_params* p,
+                                       void* stream, aco_batch** out) {
+    if (!xy_dev || !n_host || !p || !out || count < 1) return ACO_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (p->mode != ACO_MODE_LBEST_PARTIAL) return ACO_ERR_INVALID_ARG;
+    aco_batch* b = new (std::nothrow) aco_batch();
+    if (!b) return ACO_ERR_OOM;
+    b->count = count;
+    b->p = *p;
+    b->stream = (cudaStream_t)stream;
+    if (!b->stream) {  // graph capture needs a stream other than the legacy default stream
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return ACO_ERR_CUDA;
+        }
+        b->own_stream = true;
+    }
+    stream = b->stream;
+    long long coff = 0, aoff = 0, toff = 0;
+    for (int i = 0; i < count; ++i) {
+        aco_params q = *p;
+        q.n = n_host[i];
+        q.m = p->m < n_host[i] ? p->m : n_host[i];
+        q.seed = p->seed + (uint64_t)i;
+        aco_instance* ins = nullptr;
+        aco_status st = aco_create_instance(xy_dev + 2 * coff, &q, stream, &ins);
+        if (st != ACO_OK) {
+            free_batch(b);
+            delete b;
+            return st;
+        }
+        b->inst.push_back(ins);
+        b->n_i.push_back(q.n);
+        b->m_i.push_back(q.m);
+        b->city_off.push_back(coff);
+        b->ant_off.push_back(aoff);
+        b->tour_off.push_back(toff);
+        coff += q.n;
+        aoff += q.m;
+        toff += (long long)q.m * q.n;
+    }
+    // schedule: ant slots of the largest instances first (their chains are the longest)
+    std::vector<int> order(count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->n_i[x] > b->n_i[y]; });
+    std::vector<int2> slot;
+    for (int i : order)
+        for (int a = 0; a < b->m_i[i]; ++a) slot.push_back(make_int2(i, a));
+    std::vector<int4> rmap;
+    for (int i : order)
+        for (int c0 = 0; c0 < b->n_i[i]; c0 += 64) rmap.push_back(make_int4(i, c0, std::min(c0 + 64, b->n_i[i]), 0));
+    b->slots = (int)slot.size();
+    b->rblocks = (int)rmap.size();
+    for (int i = 0; i < count; ++i) {
+        b->smem_per_ant = std::max(b->smem_per_ant, (int)construct_smem_per_ant(b->n_i[i], p->k));
+        b->m_cap = std::max(b->m_cap, b->m_i[i]);
+    }
+    bool ok = cudaMalloc(&b->d_largs, lbest_args_size() * count) == cudaSuccess;
+    ok &= cudaMalloc(&b->d_cargs, sizeof(CommitArgs) * count) == cudaSuccess;
+    ok &= cudaMalloc(&b->d_gargs, sizeof(GbestArgs) * count) == cudaSuccess;
+    ok &= cudaMalloc(&b->d_rargs, sizeof(RebuildArgs) * count) == cudaSuccess;
+    ok &= cudaMalloc(&b->d_slot, sizeof(int2) * slot.size()) == cudaSuccess;
+    ok &= cudaMalloc(&b->d_rmap, sizeof(int4) * rmap.size()) == cudaSuccess;
+    ok &= cudaMalloc(&b->d_iter, sizeof(int)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_batch(b);
+        delete b;
+        return ACO_ERR_OOM;
+    }
+    cudaMemcpy(b->d_slot, slot.data(), sizeof(int2) * slot.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_rmap, rmap.data(), sizeof(int4) * rmap.size(), cudaMemcpyHostToDevice);
+    *out = b;
+    return ACO_OK;
+}
+
+extern "C" aco_status aco_batch_build_candidates(aco_batch* b) {
+    if (!b) return ACO_ERR_INVALID_ARG;
+    for (aco_instance* i : b->inst) {
+        aco_status st = aco_build_candidates(i, nullptr);
+        if (st != ACO_OK) return berr(b, st, aco_last_error(i));
+    }
+    b->built = true;
+    return ACO_OK;
+}
+
+// Descriptors of every colony (initialized flag as the instances stand now).
+static aco_status upload_args(aco_batch* b, int32_t iteration) {
+    const size_t la = lbest_args_size();
+    std::vector<unsigned char> L(la * b->count);
+    std::vector<CommitArgs> C(b->count);
+    std::vector<GbestArgs> G(b->count);
+    std::vector<RebuildArgs> R(b->count);
+    for (int i = 0; i < b->count; ++i) {
+        fill_lbest_args_bytes(b->inst[i], iteration, L.data() + la * i);
+        fill_commit_args(b->inst[i], C[i]);
+        fill_gbest_args(b->inst[i], 0, G[i]);
+        fill_rebuild_args(b->inst[i], 1, R[i]);
+        R[i].m_cap = b->m_cap;
+    }
+    cudaStream_t s = b->stream;
+    cudaMemcpyAsync(b->d_largs, L.data(), L.size(), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(b->d_cargs, C.data(), sizeof(CommitArgs) * b->count, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(b->d_gargs, G.data(), sizeof(GbestArgs) * b->count, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(b->d_rargs, R.data(), sizeof(RebuildArgs) * b->count, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(b->d_iter, &iteration, sizeof(int), cudaMemcpyHostToDevice, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return berr(b, ACO_ERR_CUDA, "descriptor upload failed");
+    return ACO_OK;
+}
+
+static cudaError_t enqueue_iteration(aco_batch* b, int warps) {
+    cudaError_t e = launch_construct_batch(reinterpret_cast<const LbestArgs*>(b->d_largs), b->d_slot, b->d_iter,
+                                           b->slots, b->smem_per_ant, warps, b->stream);
+    if (e != cudaSuccess) return e;
+    e = launch_update_batch(b->d_cargs, b->d_slot, b->slots, b->d_gargs, b->count, b->d_rargs, b->d_rmap, b->rblocks,
+                            b->m_cap, b->p.k, b->stream);
+    if (e != cudaSuccess) return e;
+    bump_iteration_kernel<<<1, 1, 0, b->stream>>>(b->d_iter);
+    return cudaGetLastError();
+}
+
+static aco_status graph_for(aco_batch* b, int choice) {
+    if (b->graph[choice]) return ACO_OK;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return berr(b, ACO_ERR_CUDA, "stream capture could not begin");
+    cudaError_t e = enqueue_iteration(b, kWarpChoices[choice]);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return berr(b, ACO_ERR_CUDA, "iteration capture failed");
+    }
+    e = cudaGraphInstantiate(&b->graph[choice], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b->graph[choice] = nullptr;
+        return berr(b, ACO_ERR_CUDA, "graph instantiation failed");
+    }
+    return ACO_OK;
+}
+
+extern "C" aco_status aco_batch_run(aco_batch* b, int32_t first_iteration, int32_t iterations, int32_t tune) {
+    if (!b || iterations < 0 || first_iteration < 0) return ACO_ERR_INVALID_ARG;
+    if (!b->built) return berr(b, ACO_ERR_STATE, "run before build_candidates");
+    if (iterations == 0) return ACO_OK;
+    if (!b->initialized) {  // initial tours (Algorithm 1, lines 1-3): every ant builds a full tour
+        aco_status st = upload_args(b, first_iteration);
+        if (st != ACO_OK) return st;
+        if (enqueue_iteration(b, b->warps) != cudaSuccess) return berr(b, ACO_ERR_CUDA, "initial iteration failed");
+        for (aco_instance* i : b->inst) {
+            i->initialized = true;
+            i->iterations++;
+        }
+        b->initialized = true;
+        b->iterations++;
+        ++first_iteration;
+        --iterations;
+        st = upload_args(b, first_iteration);  // descriptors now say "initialized"
+        if (st != ACO_OK) return st;
+    } else {
+        cudaMemcpyAsync(b->d_iter, &first_iteration, sizeof(int), cudaMemcpyHostToDevice, b->stream);
+    }
+    int done = 0;
+    if (tune && !b->tuned) {  // time live iterations with each schedule, keep the fastest
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        int best_choice = 0;
+        for (int c = 0; c < 4 && done < iterations; ++c, ++done) {
+            aco_status st = graph_for(b, c);
+            if (st != ACO_OK) return st;
+            cudaEventRecord(e0, b->stream);
+            cudaGraphLaunch(b->graph[c], b->stream);
+            cudaEventRecord(e1, b->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            b->tune_ms[c] = ms;
+            if (ms < best) { best = ms; best_choice = c; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        b->warps = kWarpChoices[best_choice];
+        b->tuned = true;
+    }
+    int choice = 0;
+    while (kWarpChoices[choice] != b->warps) ++choice;
+    aco_status st = graph_for(b, choice);
+    if (st != ACO_OK) return st;
+    for (; done < iterations; ++done)
+        if (cudaGraphLaunch(b->graph[choice], b->stream) != cudaSuccess) return berr(b, ACO_ERR_CUDA, "graph launch failed");
+    for (aco_instance* i : b->inst) i->iterations += iterations;
+    b->iterations += iterations;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return berr(b, ACO_ERR_CUDA, cudaGetErrorString(e));
+    return ACO_OK;
+}
+
+extern "C" aco_status aco_batch_get_state(aco_batch* b, int32_t* lbest_out_dev, double* clen_out_dev) {
+    if (!b) return ACO_ERR_INVALID_ARG;
+    for (int i = 0; i < b->count; ++i) {
+        aco_status st = aco_get_state(b->inst[i], lbest_out_dev ? lbest_out_dev + b->tour_off[i] : nullptr,
+                                      clen_out_dev ? clen_out_dev + b->ant_off[i] : nullptr, nullptr);
+        if (st != ACO_OK) return berr(b, st, aco_last_error(b->inst[i]));
+    }
+    return ACO_OK;
+}
+
+extern "C" aco_status aco_batch_get_best(aco_batch* b, double* best_len_host) {
+    if (!b || !best_len_host) return ACO_ERR_INVALID_ARG;
+    for (int i = 0; i < b->count; ++i) {
+        aco_stats s;
+        aco_status st = aco_get_stats(b->inst[i], &s);
+        if (st != ACO_OK) return berr(b, st, aco_last_error(b->inst[i]));
+        best_len_host[i] = s.gbest;
+    }
+    return ACO_OK;
+}
+
+extern "C" aco_status aco_batch_schedule(const aco_batch* b, int32_t* warps_out, float* tune_ms_out4) {
+    if (!b) return ACO_ERR_INVALID_ARG;
+    if (warps_out) *warps_out = b->warps;
+    if (tune_ms_out4)
+        for (int c = 0; c < 4; ++c) tune_ms_out4[c] = b->tune_ms[c];
+    return ACO_OK;
+}
+
+extern "C" void aco_batch_destroy(aco_batch* b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    free_batch(b);
+    delete b;
+}

@@ -178,6 +178,43 @@ struct CandW {
 
 enum : int { CNT_DECISIONS = 0, CNT_FALLBACKS, CNT_RESOLVES, CNT_IMPROVED, CNT_PARTIAL, CNT_FULL, CNT_N };
 
+// ------------------------------------------------------------------ update kernel arguments
+struct CommitArgs {
+    int n, m, k;
+    const int* cand;
+    int* lbest;
+    int* nb;
+    uint8_t* nbrank;
+    const int* seg;
+    const AntIter* antit;
+    double* clen;
+    unsigned long long* cfix;
+    unsigned long long* counters;
+};
+
+struct GbestArgs {
+    int m;
+    const double* clen;
+    double* gbest;
+    int* gbest_ant;
+    unsigned long long* q;
+    int keep_prev;
+};
+
+struct RebuildArgs {
+    int n, m, k;
+    double tau0, alpha;
+    int use_ants;
+    int m_cap;  // shared-memory slots for per-ant weights (largest m of a batch)
+    const uint8_t* nbrank;
+    const unsigned long long* q;
+    const double* etab;
+    CandW* candw;
+    double* W64;
+    uint8_t* rowflag;
+    int* errflag;
+};
+
 // ------------------------------------------------------------------ instance
 struct aco_instance {
     aco_params p;

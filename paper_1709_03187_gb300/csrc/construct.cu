@@ -65,6 +65,15 @@ struct LbestArgs {
     int* __restrict__ errflag;
 };
 
+// Batched launches: ant slot -> (instance, ant); per-instance descriptors; device iteration.
+struct BatchMap {
+    const LbestArgs* args;
+    const int2* slot;
+    const int* iteration;
+    int slots;
+    int smem_per_ant;
+};
+
 __device__ __forceinline__ bool is_visited(const uint32_t* bits, int c) { return (bits[c >> 5] >> (c & 31)) & 1u; }
 
 // FP64 sequential wheel over the candidate row (rank order), identical to Eq. 1's definition.
@@ -683,21 +692,38 @@ __host__ __device__ inline size_t stage_bytes(int k) { return (k <= STAGE_K && !
 __host__ __device__ inline size_t boost_offset(int k) { return stage_bytes(k); }
 __host__ __device__ inline size_t bits_offset(int k) { return (boost_offset(k) + sizeof(BoostSmem) + 15) & ~(size_t)15; }
 
-__global__ void __launch_bounds__(32, 8) construct_lbest_kernel(LbestArgs A) {
+// One warp per ant.  Single colony: block b is ant b and the descriptor is the launch
+// parameter.  Batched colonies (BATCH): warp w of block b takes ant slot b * warps + w, which
+// names (instance, ant); the descriptor comes from the per-instance array and the iteration
+// from device memory, so one captured launch serves every iteration.
+template <bool BATCH, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS, 8 / WARPS) construct_lbest_kernel(const __grid_constant__ LbestArgs Ap,
+                                                                                   const __grid_constant__ BatchMap B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int a = blockIdx.x, inst = 0;
+    if (BATCH) {
+        const int slot = blockIdx.x * WARPS + warp;
+        if (slot >= B.slots) return;  // no block-wide synchronisation below: warps are independent
+        const int2 sa = B.slot[slot];
+        inst = sa.x;
+        a = sa.y;
+    }
+    const LbestArgs& A = BATCH ? B.args[inst] : Ap;
+    const int iteration = BATCH ? *B.iteration : Ap.iteration;
+    unsigned char* my_smem = smem_raw + (BATCH ? (size_t)warp * B.smem_per_ant : 0);
     // double-buffered copies of the candidate rows of the current city's unvisited candidates:
     // the next city is one of them, so its row is in shared memory when the next decision starts
-    CandW(*stage)[STAGE_K][STAGE_K] = reinterpret_cast<CandW(*)[STAGE_K][STAGE_K]>(smem_raw);
-    BoostSmem& boost = *reinterpret_cast<BoostSmem*>(smem_raw + boost_offset(A.k));
-    uint32_t* bits = reinterpret_cast<uint32_t*>(smem_raw + bits_offset(A.k));
-    const int a = blockIdx.x, lane = threadIdx.x;
+    CandW(*stage)[STAGE_K][STAGE_K] = reinterpret_cast<CandW(*)[STAGE_K][STAGE_K]>(my_smem);
+    BoostSmem& boost = *reinterpret_cast<BoostSmem*>(my_smem + boost_offset(A.k));
+    uint32_t* bits = reinterpret_cast<uint32_t*>(my_smem + bits_offset(A.k));
     const int n = A.n, k = A.k;
     const int W = (n + 31) >> 5;
     bool partial = false;
     if (A.initialized) {
         partial = true;
         if (A.p_partial < 1.0) {
-            const Draw4 d = aco_draw(A.seed, 0, a, A.iteration, PURPOSE_COIN);
+            const Draw4 d = aco_draw(A.seed, 0, a, iteration, PURPOSE_COIN);
             partial = unit53(d.x0, d.x1) < A.p_partial;
         }
     }
@@ -706,13 +732,13 @@ __global__ void __launch_bounds__(32, 8) construct_lbest_kernel(LbestArgs A) {
     int cur, steps, s = -1, P = 0, M, start;
     int ucount = 0;
     if (partial) {
-        const Draw4 d1 = aco_draw(A.seed, 0, a, A.iteration, PURPOSE_START);
+        const Draw4 d1 = aco_draw(A.seed, 0, a, iteration, PURPOSE_START);
         s = (int)below(d1.x0, (uint32_t)n);
         long long fm = (long long)floor(__dmul_rn(A.f, (double)n));
         long long pmin = (long long)n - fm;
         if (pmin < 1) pmin = 1;
         if (pmin > n - 1) pmin = n - 1;
-        const Draw4 d2 = aco_draw(A.seed, 0, a, A.iteration, PURPOSE_KEEP);
+        const Draw4 d2 = aco_draw(A.seed, 0, a, iteration, PURPOSE_KEEP);
         P = (int)pmin + (int)below(d2.x0, (uint32_t)(n - pmin));
         M = n - P;
         for (int w = lane; w < W; w += 32) bits[w] = 0xFFFFFFFFu;
@@ -733,7 +759,7 @@ __global__ void __launch_bounds__(32, 8) construct_lbest_kernel(LbestArgs A) {
         start = L[s];
         steps = M;
     } else {
-        const Draw4 d1 = aco_draw(A.seed, 0, a, A.iteration, PURPOSE_START);
+        const Draw4 d1 = aco_draw(A.seed, 0, a, iteration, PURPOSE_START);
         start = (int)below(d1.x0, (uint32_t)n);
         for (int w = lane; w < W; w += 32) bits[w] = 0u;
         __syncwarp();
@@ -758,7 +784,7 @@ __global__ void __launch_bounds__(32, 8) construct_lbest_kernel(LbestArgs A) {
     int pend = -1;                                   // chosen city whose visited bit is set next step
     for (int t = 0; t < steps; ++t) {
         if ((t & 31) == 0) {
-            const Draw4 d = aco_draw(A.seed, (uint32_t)(t + lane), a, A.iteration, PURPOSE_WHEEL);
+            const Draw4 d = aco_draw(A.seed, (uint32_t)(t + lane), a, iteration, PURPOSE_WHEEL);
             my_u = unit53(d.x0, d.x1);
             my_uf = __double2float_rn(my_u);
         }
@@ -869,8 +895,7 @@ __global__ void __launch_bounds__(32, 8) construct_lbest_kernel(LbestArgs A) {
     }
 }
 
-aco_status launch_construct_lbest(aco_instance* inst, int32_t iteration) {
-    LbestArgs A;
+void fill_lbest_args(const aco_instance* inst, int32_t iteration, LbestArgs& A) {
     const aco_params& p = inst->p;
     A.n = p.n; A.m = p.m; A.k = p.k;
     A.alpha = p.alpha; A.beta = p.beta; A.tau0 = p.tau0; A.f = p.max_mod_frac; A.p_partial = p.p_partial;
@@ -888,14 +913,59 @@ aco_status launch_construct_lbest(aco_instance* inst, int32_t iteration) {
     A.q = inst->q; A.cfix = inst->cfix;
     A.seg = inst->seg; A.antit = inst->antit; A.accq = inst->accq; A.bel = inst->bel; A.btx = inst->btx; A.btq = inst->btq; A.ulist = inst->ulist; A.uxy = inst->uxy;
     A.counters = inst->counters; A.errflag = inst->errflag;
-    const size_t smem = bits_offset(p.k) + sizeof(uint32_t) * (size_t)((p.n + 31) / 32);
+}
+
+size_t lbest_args_size() { return sizeof(LbestArgs); }
+
+void fill_lbest_args_bytes(const aco_instance* inst, int32_t iteration, void* out) {
+    fill_lbest_args(inst, iteration, *reinterpret_cast<LbestArgs*>(out));
+}
+
+// Dynamic shared memory of one ant slot (16-byte multiple).
+size_t construct_smem_per_ant(int n, int k) {
+    return (bits_offset(k) + sizeof(uint32_t) * (size_t)((n + 31) / 32) + 15) & ~(size_t)15;
+}
+
+aco_status launch_construct_lbest(aco_instance* inst, int32_t iteration) {
+    LbestArgs A;
+    fill_lbest_args(inst, iteration, A);
+    const aco_params& p = inst->p;
+    const size_t smem = construct_smem_per_ant(p.n, p.k);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(construct_lbest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(construct_lbest_kernel<false, 1>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return set_err(inst, ACO_ERR_CUDA, "smem attribute: %s", cudaGetErrorString(e));
     }
-    construct_lbest_kernel<<<p.m, 32, smem, inst->stream>>>(A);
+    BatchMap none{};
+    construct_lbest_kernel<false, 1><<<p.m, 32, smem, inst->stream>>>(A, none);
     return check_launch(inst, "construct_lbest_kernel");
+}
+
+// Batched launch: `slots` ant slots, `warps` ants per block (1, 2, 4 or 8).
+cudaError_t launch_construct_batch(const LbestArgs* args, const int2* slot, const int* iteration, int slots,
+                                   int smem_per_ant, int warps, cudaStream_t s) {
+    BatchMap B{args, slot, iteration, slots, smem_per_ant};
+    LbestArgs dummy{};
+    const size_t smem = (size_t)smem_per_ant * warps;
+    const int blocks = (slots + warps - 1) / warps;
+#define ACO_BATCH_LAUNCH(W)                                                                                     \
+    case W:                                                                                                     \
+        if (smem > 48 * 1024) {                                                                                 \
+            cudaError_t e = cudaFuncSetAttribute(construct_lbest_kernel<true, W>,                               \
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
+            if (e != cudaSuccess) return e;                                                                     \
+        }                                                                                                       \
+        construct_lbest_kernel<true, W><<<blocks, 32 * W, smem, s>>>(dummy, B);                                 \
+        break;
+    switch (warps) {
+        ACO_BATCH_LAUNCH(1)
+        ACO_BATCH_LAUNCH(2)
+        ACO_BATCH_LAUNCH(4)
+        ACO_BATCH_LAUNCH(8)
+        default: return cudaErrorInvalidValue;
+    }
+#undef ACO_BATCH_LAUNCH
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ dense mode (Section 2)

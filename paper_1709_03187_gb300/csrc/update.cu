@@ -40,23 +40,29 @@ __device__ __forceinline__ void set_neighbours(int* __restrict__ nb, uint8_t* __
     nbrank[e + 1] = rank_of(cand, k, c, pred);
 }
 
-// One warp per ant.
-__global__ void __launch_bounds__(32) commit_kernel(int n, int m, int k, const int* __restrict__ cand,
-                                                    int* __restrict__ lbest, int* __restrict__ nb,
-                                                    uint8_t* __restrict__ nbrank, const int* __restrict__ seg,
-                                                    const AntIter* __restrict__ antit, double* __restrict__ clen,
-                                                    unsigned long long* __restrict__ cfix,
-                                                    unsigned long long* __restrict__ counters) {
-    const int a = blockIdx.x, lane = threadIdx.x;
-    const AntIter it = antit[a];
-    if (!(it.newlen < clen[a])) return;
-    int* L = lbest + (size_t)a * n;
-    const int* S = seg + (size_t)a * n;
+// One warp per ant.  Batched colonies: block b is ant slot b, naming (instance, ant).
+template <bool BATCH>
+__global__ void __launch_bounds__(32) commit_kernel(const __grid_constant__ CommitArgs Cp,
+                                                    const CommitArgs* __restrict__ batch, const int2* __restrict__ slot,
+                                                    int slots) {
+    int a = blockIdx.x, inst = 0;
+    if (BATCH) {
+        if ((int)blockIdx.x >= slots) return;
+        const int2 sa = slot[blockIdx.x];
+        inst = sa.x;
+        a = sa.y;
+    }
+    const CommitArgs& C = BATCH ? batch[inst] : Cp;
+    const int n = C.n, m = C.m, k = C.k, lane = threadIdx.x;
+    const AntIter it = C.antit[a];
+    if (!(it.newlen < C.clen[a])) return;
+    int* L = C.lbest + (size_t)a * n;
+    const int* S = C.seg + (size_t)a * n;
     if (it.s < 0) {
         for (int t = lane; t < n; t += 32) L[t] = S[t];
         __syncwarp();
         for (int t = lane; t < n; t += 32)
-            set_neighbours(nb, nbrank, cand, m, k, a, S[t], S[t + 1 == n ? 0 : t + 1], S[t == 0 ? n - 1 : t - 1]);
+            set_neighbours(C.nb, C.nbrank, C.cand, m, k, a, S[t], S[t + 1 == n ? 0 : t + 1], S[t == 0 ? n - 1 : t - 1]);
     } else {
         const int e = L[(it.s + it.P - 1) % n];
         const int start = L[it.s];
@@ -66,36 +72,38 @@ __global__ void __launch_bounds__(32) commit_kernel(int n, int m, int k, const i
         for (int t = lane; t < M; t += 32) {
             const int pc = t == 0 ? e : S[t - 1];
             const int sc = t == M - 1 ? start : S[t + 1];
-            set_neighbours(nb, nbrank, cand, m, k, a, S[t], sc, pc);
+            set_neighbours(C.nb, C.nbrank, C.cand, m, k, a, S[t], sc, pc);
         }
         if (lane == 0) {
             const size_t ee = ((size_t)e * m + a) * 2;
-            nb[ee] = S[0];
-            nbrank[ee] = rank_of(cand, k, e, S[0]);
+            C.nb[ee] = S[0];
+            C.nbrank[ee] = rank_of(C.cand, k, e, S[0]);
             const size_t es = ((size_t)start * m + a) * 2 + 1;
-            nb[es] = S[M - 1];
-            nbrank[es] = rank_of(cand, k, start, S[M - 1]);
+            C.nb[es] = S[M - 1];
+            C.nbrank[es] = rank_of(C.cand, k, start, S[M - 1]);
         }
     }
     if (lane == 0) {
-        clen[a] = it.newlen;
-        cfix[2 * a] = it.fix_lo;
-        cfix[2 * a + 1] = it.fix_hi;
-        atomicAdd(&counters[CNT_IMPROVED], 1ull);
+        C.clen[a] = it.newlen;
+        C.cfix[2 * a] = it.fix_lo;
+        C.cfix[2 * a + 1] = it.fix_hi;
+        atomicAdd(&C.counters[CNT_IMPROVED], 1ull);
     }
 }
 
-// Single block: C_gbest, its ant, and the per-ant deposit weights.  keep_prev: fold in the
-// previous g_best (dense mode keeps the best over all iterations).
-__global__ void gbest_q_kernel(int m, const double* __restrict__ clen, double* __restrict__ gbest,
-                               int* __restrict__ gbest_ant, unsigned long long* __restrict__ q, int keep_prev) {
+// One block per colony: C_gbest, its ant, and the per-ant deposit weights.  keep_prev: fold in
+// the previous g_best (dense mode keeps the best over all iterations).
+template <bool BATCH>
+__global__ void gbest_q_kernel(const __grid_constant__ GbestArgs Gp, const GbestArgs* __restrict__ batch) {
+    const GbestArgs& G = BATCH ? batch[blockIdx.x] : Gp;
+    const int m = G.m;
     __shared__ double sv[32];
     __shared__ int si[32];
     __shared__ double cg_s;
     double v = DBL_MAX * 2;  // +inf
     int idx = 0x7fffffff;
     for (int a = threadIdx.x; a < m; a += blockDim.x) {
-        const double c = clen[a];
+        const double c = G.clen[a];
         if (c < v || (c == v && a < idx)) { v = c; idx = a; }
     }
     for (int o = 16; o; o >>= 1) {
@@ -108,43 +116,52 @@ __global__ void gbest_q_kernel(int m, const double* __restrict__ clen, double* _
     if (threadIdx.x == 0) {
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
             if (sv[w] < v || (sv[w] == v && si[w] < idx)) { v = sv[w]; idx = si[w]; }
-        if (keep_prev && !(v < *gbest)) {
-            v = *gbest;
-            idx = *gbest_ant;
+        if (G.keep_prev && !(v < *G.gbest)) {
+            v = *G.gbest;
+            idx = *G.gbest_ant;
         }
-        *gbest = v;
-        *gbest_ant = idx;
+        *G.gbest = v;
+        *G.gbest_ant = idx;
         cg_s = v;
     }
     __syncthreads();
-    if (q) {
+    if (G.q) {
         const double cg = cg_s;
         for (int a = threadIdx.x; a < m; a += blockDim.x)
-            q[a] = __double2ull_rn(__dmul_rn(__ddiv_rn(cg, clen[a]), 4294967296.0));
+            G.q[a] = __double2ull_rn(__dmul_rn(__ddiv_rn(cg, G.clen[a]), 4294967296.0));
     }
 }
 
 // One warp per city; lane-private histograms in shared memory (conflict-free column per lane).
-template <bool VEC>
-__global__ void __launch_bounds__(256) rebuild_kernel(int n, int m, int k, double tau0, double alpha, int use_ants,
-                                                      const uint8_t* __restrict__ nbrank,
-                                                      const unsigned long long* __restrict__ q,
-                                                      const double* __restrict__ etab, CandW* __restrict__ candw,
-                                                      double* __restrict__ W64, uint8_t* __restrict__ rowflag,
-                                                      int* __restrict__ errflag) {
+// Single colony: warps stride over all cities.  Batched colonies: block b covers the city range
+// blockmap[b] = (instance, first city, end city) of one instance.
+template <bool BATCH>
+__global__ void __launch_bounds__(256) rebuild_kernel(const __grid_constant__ RebuildArgs Rp,
+                                                      const RebuildArgs* __restrict__ batch,
+                                                      const int4* __restrict__ blockmap) {
     extern __shared__ unsigned long long sm[];
+    int4 bm = make_int4(0, 0, 0, 0);
+    if (BATCH) bm = blockmap[blockIdx.x];
+    const RebuildArgs& R = BATCH ? batch[bm.x] : Rp;
+    const int n = R.n, m = R.m, k = R.k, use_ants = R.use_ants;
+    const double tau0 = R.tau0, alpha = R.alpha;
     const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned long long* qs = sm;                                  // m
-    unsigned long long* hist = sm + m + (size_t)w * k * 32;      // [k][32]
+    const int m_cap = BATCH ? R.m_cap : m;
+    unsigned long long* qs = sm;                                      // m
+    unsigned long long* hist = sm + m_cap + (size_t)w * k * 32;      // [k][32]
     if (use_ants)
-        for (int a = threadIdx.x; a < m; a += blockDim.x) qs[a] = q[a];
+        for (int a = threadIdx.x; a < m; a += blockDim.x) qs[a] = R.q[a];
     __syncthreads();
-    for (int i = blockIdx.x * warps + w; i < n; i += gridDim.x * warps) {
+    const bool vec = (m & 7) == 0;
+    const int i0 = BATCH ? bm.y + w : blockIdx.x * warps + w;
+    const int iend = BATCH ? bm.z : n;
+    const int istep = BATCH ? warps : gridDim.x * warps;
+    for (int i = i0; i < iend; i += istep) {
         unsigned long long Q = 0;
         if (use_ants) {
             for (int r = 0; r < k; ++r) hist[r * 32 + lane] = 0ull;
-            const uint8_t* row = nbrank + (size_t)i * m * 2;
-            if (VEC) {
+            const uint8_t* row = R.nbrank + (size_t)i * m * 2;
+            if (vec) {
                 for (int base = 0; base < m; base += 256) {
                     const int a0 = base + lane * 8;
                     if (a0 < m) {
@@ -185,39 +202,68 @@ __global__ void __launch_bounds__(256) rebuild_kernel(int n, int m, int k, doubl
         if (lane < k) {
             const size_t e = (size_t)i * k + lane;
             const double tau = __dadd_rn(tau0, __dmul_rn(__ull2double_rn(Q), 0x1.0p-32));
-            const double wv = __dmul_rn(powr(tau, alpha), etab[e]);
+            const double wv = __dmul_rn(powr(tau, alpha), R.etab[e]);
             w32 = __double2float_rn(wv);
-            if (!isfinite(wv)) atomicOr(errflag, DEVERR_NONFINITE);
+            if (!isfinite(wv)) atomicOr(R.errflag, DEVERR_NONFINITE);
             flag = !(w32 >= FLT_MIN && w32 <= FLT_MAX);
-            W64[e] = wv;
+            R.W64[e] = wv;
         }
         const unsigned fl = __ballot_sync(FULL, flag);
         // a row the FP32 screen cannot represent carries negative screen weights: the
         // construction kernel then evaluates it exactly in FP64
-        if (lane < k) candw[(size_t)i * k + lane].w = fl ? -1.0f : w32;
-        if (lane == 0) rowflag[i] = fl ? 1 : 0;
+        if (lane < k) R.candw[(size_t)i * k + lane].w = fl ? -1.0f : w32;
+        if (lane == 0) R.rowflag[i] = fl ? 1 : 0;
     }
+}
+
+void fill_commit_args(const aco_instance* inst, CommitArgs& C) {
+    C.n = inst->p.n; C.m = inst->p.m; C.k = inst->p.k; C.cand = inst->cand; C.lbest = inst->lbest; C.nb = inst->nb;
+    C.nbrank = inst->nbrank; C.seg = inst->seg; C.antit = inst->antit; C.clen = inst->clen; C.cfix = inst->cfix;
+    C.counters = inst->counters;
+}
+
+void fill_gbest_args(const aco_instance* inst, int keep_prev, GbestArgs& G) {
+    G.m = inst->p.m; G.clen = inst->clen; G.gbest = inst->gbest; G.gbest_ant = inst->gbest_ant;
+    G.q = inst->p.mode == ACO_MODE_LBEST_PARTIAL ? inst->q : nullptr; G.keep_prev = keep_prev;
+}
+
+void fill_rebuild_args(const aco_instance* inst, int use_ants, RebuildArgs& R) {
+    const aco_params& p = inst->p;
+    R.n = p.n; R.m = p.m; R.k = p.k; R.tau0 = p.tau0; R.alpha = p.alpha; R.use_ants = use_ants; R.m_cap = p.m;
+    R.nbrank = inst->nbrank; R.q = inst->q; R.etab = inst->etab; R.candw = inst->candw; R.W64 = inst->W64;
+    R.rowflag = inst->rowflag; R.errflag = inst->errflag;
+}
+
+size_t rebuild_smem_bytes(int m_cap, int k, int warps) {
+    return sizeof(unsigned long long) * ((size_t)m_cap + (size_t)warps * k * 32);
 }
 
 static aco_status launch_rebuild(aco_instance* inst, int use_ants) {
     const aco_params& p = inst->p;
     const int warps = 8;
-    const size_t smem = sizeof(unsigned long long) * ((size_t)p.m + (size_t)warps * p.k * 32);
+    RebuildArgs R;
+    fill_rebuild_args(inst, use_ants, R);
+    const size_t smem = rebuild_smem_bytes(p.m, p.k, warps);
     const int blocks = (int)fmin((double)inst->num_sms * 4, (double)ceil_div(p.n, warps));
-    const bool vec = (p.m % 8) == 0;
-    if (vec) {
-        cudaFuncSetAttribute(rebuild_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        rebuild_kernel<true><<<blocks, 32 * warps, smem, inst->stream>>>(p.n, p.m, p.k, p.tau0, p.alpha, use_ants,
-                                                                        inst->nbrank, inst->q, inst->etab, inst->candw,
-                                                                        inst->W64, inst->rowflag, inst->errflag);
-    } else {
-        cudaFuncSetAttribute(rebuild_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        rebuild_kernel<false><<<blocks, 32 * warps, smem, inst->stream>>>(p.n, p.m, p.k, p.tau0, p.alpha, use_ants,
-                                                                         inst->nbrank, inst->q, inst->etab,
-                                                                         inst->candw, inst->W64, inst->rowflag,
-                                                                         inst->errflag);
-    }
+    cudaFuncSetAttribute(rebuild_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    rebuild_kernel<false><<<blocks, 32 * warps, smem, inst->stream>>>(R, nullptr, nullptr);
     return check_launch(inst, "rebuild_kernel");
+}
+
+// Batched update: commit (one block per ant slot), C_gbest (one block per colony), rebuild
+// (block map over every colony's cities).
+cudaError_t launch_update_batch(const CommitArgs* cargs, const int2* slot, int slots, const GbestArgs* gargs,
+                                int count, const RebuildArgs* rargs, const int4* blockmap, int rblocks, int m_cap,
+                                int k, cudaStream_t s) {
+    CommitArgs c0{};
+    commit_kernel<true><<<slots, 32, 0, s>>>(c0, cargs, slot, slots);
+    GbestArgs g0{};
+    gbest_q_kernel<true><<<count, 256, 0, s>>>(g0, gargs);
+    RebuildArgs r0{};
+    const size_t smem = rebuild_smem_bytes(m_cap, k, 8);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(rebuild_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    rebuild_kernel<true><<<rblocks, 256, smem, s>>>(r0, rargs, blockmap);
+    return cudaGetLastError();
 }
 
 __global__ void fill_inf_kernel(double* __restrict__ v, int count) {
@@ -235,11 +281,14 @@ aco_status launch_lbest_init_weights(aco_instance* inst) {
 
 aco_status launch_update_lbest(aco_instance* inst) {
     const aco_params& p = inst->p;
-    commit_kernel<<<p.m, 32, 0, inst->stream>>>(p.n, p.m, p.k, inst->cand, inst->lbest, inst->nb, inst->nbrank,
-                                                 inst->seg, inst->antit, inst->clen, inst->cfix, inst->counters);
+    CommitArgs C;
+    fill_commit_args(inst, C);
+    commit_kernel<false><<<p.m, 32, 0, inst->stream>>>(C, nullptr, nullptr, 0);
     aco_status st = check_launch(inst, "commit_kernel");
     if (st != ACO_OK) return st;
-    gbest_q_kernel<<<1, 1024, 0, inst->stream>>>(p.m, inst->clen, inst->gbest, inst->gbest_ant, inst->q, 0);
+    GbestArgs G;
+    fill_gbest_args(inst, 0, G);
+    gbest_q_kernel<false><<<1, 1024, 0, inst->stream>>>(G, nullptr);
     st = check_launch(inst, "gbest_q_kernel");
     if (st != ACO_OK) return st;
     return launch_rebuild(inst, 1);
@@ -304,7 +353,9 @@ aco_status launch_set_lbest(aco_instance* inst, const int32_t* lbest) {
         p.n, p.m, p.k, inst->cand, inst->lbest, inst->nb, inst->nbrank);
     aco_status st = check_launch(inst, "set_lbest");
     if (st != ACO_OK) return st;
-    gbest_q_kernel<<<1, 1024, 0, s>>>(p.m, inst->clen, inst->gbest, inst->gbest_ant, inst->q, 0);
+    GbestArgs G;
+    fill_gbest_args(inst, 0, G);
+    gbest_q_kernel<false><<<1, 1024, 0, s>>>(G, nullptr);
     st = check_launch(inst, "gbest_q_kernel");
     if (st != ACO_OK) return st;
     return launch_rebuild(inst, 1);
@@ -389,7 +440,9 @@ aco_status launch_update_dense(aco_instance* inst) {
     const double keep = 1.0 - p.rho;
     dense_tau_kernel<<<(int)fmin((double)inst->num_sms * 8, (double)ceil_div(nn, 256)), 256, 0, s>>>(
         p.n, p.m, keep, inst->succ_d, inst->pred_d, inst->clen, inst->tau);
-    gbest_q_kernel<<<1, 1024, 0, s>>>(p.m, inst->clen, inst->gbest, inst->gbest_ant, nullptr, 1);
+    GbestArgs G;
+    fill_gbest_args(inst, 1, G);
+    gbest_q_kernel<false><<<1, 1024, 0, s>>>(G, nullptr);
     aco_status st = check_launch(inst, "dense update");
     if (st != ACO_OK) return st;
     const int blocks = (int)fmin((double)inst->num_sms * 4, (double)ceil_div(p.n, 8));
