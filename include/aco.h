@@ -160,17 +160,19 @@ aco_status aco_batch_create(const double* xy_dev, const int32_t* n_host, int32_t
 /* Candidate lists and eta^beta tables of every instance (as aco_build_candidates).  Synchronises. */
 aco_status aco_batch_build_candidates(aco_batch* b);
 /* `iterations` iterations of every colony, keyed first_iteration, first_iteration + 1, ...  The
- * first call builds the initial tours in its first iteration.  tune != 0: the first (up to four)
- * iterations of the first tuned call are timed with 1, 2, 4 and 8 ants per block and the fastest
- * schedule is kept.  Enqueued on the batch's stream. */
+ * first call builds the initial tours in its first iteration.  tune != 0: the first (up to eight)
+ * iterations of the first tuned call are timed with eight launch schedules (ants per block 1-4 and
+ * a register cap per thread) and the fastest is kept.  Enqueued on the batch's stream. */
 aco_status aco_batch_run(aco_batch* b, int32_t first_iteration, int32_t iterations, int32_t tune);
 /* l_best tours (instance i at offset sum_{j<i} m_j n_j, row-major m_i x n_i) and lengths
  * (offset sum_{j<i} m_j); either pointer may be NULL.  Synchronises. */
 aco_status aco_batch_get_state(aco_batch* b, int32_t* lbest_out_dev, double* clen_out_dev);
 /* C_gbest of every instance (count doubles).  Synchronises. */
 aco_status aco_batch_get_best(aco_batch* b, double* best_len_host);
-/* The schedule in use (ants per block) and the tuning times (4 floats, ms; 0 if not tuned). */
-aco_status aco_batch_schedule(const aco_batch* b, int32_t* warps_out, float* tune_ms_out4);
+/* The schedule in use (ants per block, minimum resident blocks per SM) and the tuning times
+ * (8 floats, ms per iteration; 0 where not tuned).  Any pointer may be NULL. */
+aco_status aco_batch_schedule(const aco_batch* b, int32_t* warps_out, int32_t* min_blocks_out,
+                              float* tune_ms_out8);
 const char* aco_batch_last_error(const aco_batch* b);
 void aco_batch_destroy(aco_batch* b);
 

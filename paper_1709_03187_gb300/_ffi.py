@@ -73,7 +73,7 @@ def lib():
             "aco_batch_run": (S, [V, I32, I32, I32]),
             "aco_batch_get_state": (S, [V, V, V]),
             "aco_batch_get_best": (S, [V, V]),
-            "aco_batch_schedule": (S, [V, V, V]),
+            "aco_batch_schedule": (S, [V, V, V, V]),
             "aco_batch_last_error": (ctypes.c_char_p, [V]),
             "aco_batch_destroy": (None, [V]),
             "aco_status_string": (ctypes.c_char_p, [S]),
@@ -193,9 +193,11 @@ def aco_batch_schedule(b):
     import numpy as np
 
     w = ctypes.c_int32()
-    ms = np.zeros(4, np.float32)
-    _bcheck(lib().aco_batch_schedule(b, ctypes.byref(w), ms.ctypes.data_as(ctypes.c_void_p)), "aco_batch_schedule", b)
-    return int(w.value), ms
+    mb = ctypes.c_int32()
+    ms = np.zeros(8, np.float32)
+    _bcheck(lib().aco_batch_schedule(b, ctypes.byref(w), ctypes.byref(mb), ms.ctypes.data_as(ctypes.c_void_p)),
+            "aco_batch_schedule", b)
+    return (int(w.value), int(mb.value)), ms
 
 
 def aco_batch_destroy(b):

@@ -7,8 +7,9 @@
 //   pheromone rebuild (block map over every colony's cities),
 // plus a one-thread increment of the device iteration counter.  After the initial tours, the
 // iteration is captured once as a CUDA graph and replayed.  The schedule does not change any
-// result (each ant's work is deterministic), so the autotuner times live iterations with 1, 2, 4
-// and 8 ants per block and keeps the fastest.
+// result (each ant's work is deterministic), so the autotuner times live iterations with each
+// launch schedule -- ants per block and a register cap (minimum resident blocks per SM) -- and
+// keeps the fastest.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -24,7 +25,8 @@ struct LbestArgs;  // defined in construct.cu
 void fill_lbest_args(const aco_instance* inst, int32_t iteration, LbestArgs& A);
 size_t construct_smem_per_ant(int n, int k);
 cudaError_t launch_construct_batch(const LbestArgs* args, const int2* slot, const int* iteration, int slots,
-                                   int smem_per_ant, int warps, cudaStream_t s);
+                                   int smem_per_ant, int config, cudaStream_t s);
+extern const int kBatchConfigs[ACO_BATCH_CONFIGS][2];
 void fill_commit_args(const aco_instance* inst, CommitArgs& C);
 void fill_gbest_args(const aco_instance* inst, int keep_prev, GbestArgs& G);
 void fill_rebuild_args(const aco_instance* inst, int use_ants, RebuildArgs& R);
@@ -36,7 +38,6 @@ void fill_lbest_args_bytes(const aco_instance* inst, int32_t iteration, void* ou
 
 __global__ void bump_iteration_kernel(int* it) { *it += 1; }
 
-static const int kWarpChoices[4] = {1, 2, 4, 8};
 
 struct aco_batch {
     int count = 0;
@@ -54,12 +55,12 @@ struct aco_batch {
     int4* d_rmap = nullptr;
     int* d_iter = nullptr;
     int slots = 0, rblocks = 0, smem_per_ant = 0, m_cap = 0;
-    int warps = 1;
+    int config = 0;  // index into kBatchConfigs
     bool tuned = false;
-    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaGraphExec_t graph[ACO_BATCH_CONFIGS] = {};
     bool built = false, initialized = false;
     int iterations = 0;
-    float tune_ms[4] = {0, 0, 0, 0};
+    float tune_ms[ACO_BATCH_CONFIGS] = {};
     char err[512] = {0};
 };
 
@@ -191,9 +192,9 @@ static aco_status upload_args(aco_batch* b, int32_t iteration) {
     return ACO_OK;
 }
 
-static cudaError_t enqueue_iteration(aco_batch* b, int warps) {
+static cudaError_t enqueue_iteration(aco_batch* b, int config) {
     cudaError_t e = launch_construct_batch(reinterpret_cast<const LbestArgs*>(b->d_largs), b->d_slot, b->d_iter,
-                                           b->slots, b->smem_per_ant, warps, b->stream);
+                                           b->slots, b->smem_per_ant, config, b->stream);
     if (e != cudaSuccess) return e;
     e = launch_update_batch(b->d_cargs, b->d_slot, b->slots, b->d_gargs, b->count, b->d_rargs, b->d_rmap, b->rblocks,
                             b->m_cap, b->p.k, b->stream);
@@ -207,7 +208,7 @@ static aco_status graph_for(aco_batch* b, int choice) {
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return berr(b, ACO_ERR_CUDA, "stream capture could not begin");
-    cudaError_t e = enqueue_iteration(b, kWarpChoices[choice]);
+    cudaError_t e = enqueue_iteration(b, choice);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess || !g) {
         if (g) cudaGraphDestroy(g);
@@ -231,7 +232,7 @@ extern "C" aco_status aco_batch_run(aco_batch* b, int32_t first_iteration, int32
     if (!b->initialized) {  // initial tours (Algorithm 1, lines 1-3): every ant builds a full tour
         aco_status st = upload_args(b, first_iteration);
         if (st != ACO_OK) return st;
-        if (enqueue_iteration(b, b->warps) != cudaSuccess) return berr(b, ACO_ERR_CUDA, "initial iteration failed");
+        if (enqueue_iteration(b, b->config) != cudaSuccess) return berr(b, ACO_ERR_CUDA, "initial iteration failed");
         for (aco_instance* i : b->inst) {
             i->initialized = true;
             i->iterations++;
@@ -252,7 +253,7 @@ extern "C" aco_status aco_batch_run(aco_batch* b, int32_t first_iteration, int32
         cudaEventCreate(&e1);
         float best = 1e30f;
         int best_choice = 0;
-        for (int c = 0; c < 4 && done < iterations; ++c, ++done) {
+        for (int c = 0; c < ACO_BATCH_CONFIGS && done < iterations; ++c, ++done) {
             aco_status st = graph_for(b, c);
             if (st != ACO_OK) return st;
             cudaEventRecord(e0, b->stream);
@@ -266,11 +267,10 @@ extern "C" aco_status aco_batch_run(aco_batch* b, int32_t first_iteration, int32
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        b->warps = kWarpChoices[best_choice];
+        b->config = best_choice;
         b->tuned = true;
     }
-    int choice = 0;
-    while (kWarpChoices[choice] != b->warps) ++choice;
+    const int choice = b->config;
     aco_status st = graph_for(b, choice);
     if (st != ACO_OK) return st;
     for (; done < iterations; ++done)
@@ -303,11 +303,13 @@ extern "C" aco_status aco_batch_get_best(aco_batch* b, double* best_len_host) {
     return ACO_OK;
 }
 
-extern "C" aco_status aco_batch_schedule(const aco_batch* b, int32_t* warps_out, float* tune_ms_out4) {
+extern "C" aco_status aco_batch_schedule(const aco_batch* b, int32_t* warps_out, int32_t* min_blocks_out,
+                                         float* tune_ms_out8) {
     if (!b) return ACO_ERR_INVALID_ARG;
-    if (warps_out) *warps_out = b->warps;
-    if (tune_ms_out4)
-        for (int c = 0; c < 4; ++c) tune_ms_out4[c] = b->tune_ms[c];
+    if (warps_out) *warps_out = kBatchConfigs[b->config][0];
+    if (min_blocks_out) *min_blocks_out = kBatchConfigs[b->config][1];
+    if (tune_ms_out8)
+        for (int c = 0; c < ACO_BATCH_CONFIGS; ++c) tune_ms_out8[c] = b->tune_ms[c];
     return ACO_OK;
 }
 

@@ -17,6 +17,7 @@
 #include "../../include/aco.h"
 
 #define ACO_MAX_K 32
+#define ACO_BATCH_CONFIGS 8  // launch schedules the batch autotuner times
 
 typedef unsigned __int128 u128;
 

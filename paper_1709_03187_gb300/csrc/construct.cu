@@ -696,8 +696,8 @@ __host__ __device__ inline size_t bits_offset(int k) { return (boost_offset(k) +
 // parameter.  Batched colonies (BATCH): warp w of block b takes ant slot b * warps + w, which
 // names (instance, ant); the descriptor comes from the per-instance array and the iteration
 // from device memory, so one captured launch serves every iteration.
-template <bool BATCH, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS, 8 / WARPS) construct_lbest_kernel(const __grid_constant__ LbestArgs Ap,
+template <bool BATCH, int WARPS, int MINB>
+__global__ void __launch_bounds__(32 * WARPS, MINB) construct_lbest_kernel(const __grid_constant__ LbestArgs Ap,
                                                                                    const __grid_constant__ BatchMap B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -932,36 +932,45 @@ aco_status launch_construct_lbest(aco_instance* inst, int32_t iteration) {
     const aco_params& p = inst->p;
     const size_t smem = construct_smem_per_ant(p.n, p.k);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(construct_lbest_kernel<false, 1>,
+        cudaError_t e = cudaFuncSetAttribute(construct_lbest_kernel<false, 1, 8>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return set_err(inst, ACO_ERR_CUDA, "smem attribute: %s", cudaGetErrorString(e));
     }
     BatchMap none{};
-    construct_lbest_kernel<false, 1><<<p.m, 32, smem, inst->stream>>>(A, none);
+    construct_lbest_kernel<false, 1, 8><<<p.m, 32, smem, inst->stream>>>(A, none);
     return check_launch(inst, "construct_lbest_kernel");
 }
 
-// Batched launch: `slots` ant slots, `warps` ants per block (1, 2, 4 or 8).
+// Batched launch schedules: (ants per block, minimum resident blocks per SM).  The second
+// number caps the registers per thread (65536 / (32 * ants * blocks)), trading register spills
+// for more concurrent ant chains.
+extern const int kBatchConfigs[ACO_BATCH_CONFIGS][2] = {{1, 8}, {1, 16}, {1, 24}, {1, 32}, {2, 8}, {2, 16}, {4, 4}, {4, 8}};
+
 cudaError_t launch_construct_batch(const LbestArgs* args, const int2* slot, const int* iteration, int slots,
-                                   int smem_per_ant, int warps, cudaStream_t s) {
+                                   int smem_per_ant, int config, cudaStream_t s) {
     BatchMap B{args, slot, iteration, slots, smem_per_ant};
     LbestArgs dummy{};
+    const int warps = kBatchConfigs[config][0];
     const size_t smem = (size_t)smem_per_ant * warps;
     const int blocks = (slots + warps - 1) / warps;
-#define ACO_BATCH_LAUNCH(W)                                                                                     \
-    case W:                                                                                                     \
+#define ACO_BATCH_LAUNCH(C, W, MB)                                                                              \
+    case C:                                                                                                     \
         if (smem > 48 * 1024) {                                                                                 \
-            cudaError_t e = cudaFuncSetAttribute(construct_lbest_kernel<true, W>,                               \
+            cudaError_t e = cudaFuncSetAttribute(construct_lbest_kernel<true, W, MB>,                           \
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
             if (e != cudaSuccess) return e;                                                                     \
         }                                                                                                       \
-        construct_lbest_kernel<true, W><<<blocks, 32 * W, smem, s>>>(dummy, B);                                 \
+        construct_lbest_kernel<true, W, MB><<<blocks, 32 * W, smem, s>>>(dummy, B);                             \
         break;
-    switch (warps) {
-        ACO_BATCH_LAUNCH(1)
-        ACO_BATCH_LAUNCH(2)
-        ACO_BATCH_LAUNCH(4)
-        ACO_BATCH_LAUNCH(8)
+    switch (config) {
+        ACO_BATCH_LAUNCH(0, 1, 8)
+        ACO_BATCH_LAUNCH(1, 1, 16)
+        ACO_BATCH_LAUNCH(2, 1, 24)
+        ACO_BATCH_LAUNCH(3, 1, 32)
+        ACO_BATCH_LAUNCH(4, 2, 8)
+        ACO_BATCH_LAUNCH(5, 2, 16)
+        ACO_BATCH_LAUNCH(6, 4, 4)
+        ACO_BATCH_LAUNCH(7, 4, 8)
         default: return cudaErrorInvalidValue;
     }
 #undef ACO_BATCH_LAUNCH

@@ -42,10 +42,10 @@ def test_batch_equals_instances_run_alone(tune):
         assert np.array_equal(got[i][1], cl.cpu().numpy())
         assert best[i] == cl.min().item()
         col.close()
-    w, ms = b.schedule()
-    assert w in (1, 2, 4, 8)
+    (w, mb), ms = b.schedule()
+    assert w in (1, 2, 4) and mb in (4, 8, 16, 24, 32)
     if tune:
-        assert np.all(ms > 0)
+        assert np.all(ms[:6] > 0)  # six tuned iterations in the second call
     b.close()
 
 
