@@ -21,7 +21,8 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["uniform", "clustered", "mixed", "make", "batch_sizes", "WORKLOADS"]
+__all__ = ["uniform", "clustered", "mixed", "make", "batch_sizes", "permutations", "bf16_values", "mlp_weights",
+           "edge_scores", "WORKLOADS"]
 
 
 def _dedupe(xy: np.ndarray, rng: np.random.Generator, redraw) -> np.ndarray:
@@ -96,3 +97,35 @@ def batch_sizes(count: int, lo: int, hi: int, seed: int) -> np.ndarray:
     """Instance sizes log-uniform in [lo, hi] (the batched workload's ragged sizes)."""
     rng = np.random.default_rng(seed)
     return np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi + 1), size=count))).astype(np.int64).clip(lo, hi)
+
+
+# ------------------------------------------------------------------ inputs of the learned proposal
+def permutations(count: int, n: int, seed: int) -> np.ndarray:
+    """`count` independent uniformly random tours of n cities, int32 [count][n]."""
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.permutation(n) for _ in range(count)]).astype(np.int32)
+
+
+def bf16_values(shape, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    """Uniform values in [lo, hi) truncated to BF16 (the top 16 bits of their FP32 pattern),
+    returned as float32."""
+    rng = np.random.default_rng(seed)
+    x = (lo + (hi - lo) * rng.random(shape)).astype(np.float32)
+    return (x.view(np.uint32) & np.uint32(0xFFFF0000)).view(np.float32)
+
+
+def mlp_weights(seed: int, inputs: int = 16, hidden: int = 64) -> np.ndarray:
+    """Initial weights of the edge-scoring network as one float32 vector (W1 [hidden][inputs],
+    W2 [hidden][hidden], w3 [hidden]): zero-mean normals with He scaling (variance 2 / fan-in,
+    fan-in 6 for W1 whose inputs 6.. are always zero)."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.normal(0.0, np.sqrt(2.0 / 6), (hidden, inputs))
+    W2 = rng.normal(0.0, np.sqrt(2.0 / hidden), (hidden, hidden))
+    w3 = rng.normal(0.0, np.sqrt(1.0 / hidden), hidden)
+    return np.concatenate([W1.ravel(), W2.ravel(), w3]).astype(np.float32)
+
+
+def edge_scores(n: int, k: int, seed: int) -> np.ndarray:
+    """Positive float32 scores [n][k], log-uniform over six decades."""
+    rng = np.random.default_rng(seed)
+    return np.exp(rng.uniform(-7.0, 7.0, (n, k))).astype(np.float32)

@@ -94,6 +94,7 @@ def lib():
             "or_knn_one": (None, [ctypes.c_int, f64p, ctypes.c_int, ctypes.c_int, i32p]),
             "or_knn_sweep": (ctypes.c_int, [ctypes.c_int, f64p, ctypes.c_int, i32p]),
             "or_create_with_cand": (P, [ctypes.POINTER(Params), f64p, i32p]),
+            "or_set_edge_scores": (None, [P, ctypes.c_void_p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -282,6 +283,17 @@ class Oracle:
 
     def set_lbest(self, lbest: np.ndarray, clen: np.ndarray):
         lib().or_set_lbest(self._h, np.ascontiguousarray(lbest, np.int32), np.ascontiguousarray(clen, np.float64))
+
+    def set_edge_scores(self, score):
+        """Learned proposal: score[i, r] replaces eta^beta on candidate edge (i, cand[i, r]); None
+        restores the plain heuristic."""
+        if score is None:
+            lib().or_set_edge_scores(self._h, None)
+            return
+        s = np.ascontiguousarray(score, np.float64).reshape(self.n, self.k)
+        if not np.all(np.isfinite(s)) or not np.all(s > 0):
+            raise ValueError("edge scores must be finite and > 0")
+        lib().or_set_edge_scores(self._h, s.ctypes.data)
 
     def step_probs(self, i: int, visited: np.ndarray):
         """Eq. 1 probabilities at city i; returns (probs, exhausted)."""

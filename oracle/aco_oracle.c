@@ -553,6 +553,17 @@ void or_cand_weights(or_state* st, double* W, uint64_t* Q_out, uint64_t* q_out) 
     if (q_out) memcpy(q_out, st->q, sizeof(uint64_t) * (size_t)st->p.m);
 }
 
+/* Learned proposal: the per-candidate-edge score s_ir replaces eta_ij^beta (j = cand[i][r]) in
+ * Eq. 1 for candidate edges; edges outside the candidate list keep eta^beta.  NULL restores the
+ * plain heuristic.  Scores must be finite and > 0. */
+void or_set_edge_scores(or_state* st, const double* score) {
+    int n = st->p.n, k = st->p.k;
+    for (int i = 0; i < n; ++i)
+        for (int r = 0; r < k; ++r)
+            st->etab[(size_t)i * k + r] =
+                score ? score[(size_t)i * k + r] : eta_pow(st->xy, i, st->cand[(size_t)i * k + r], st->p.beta);
+}
+
 /* Replace the l_best population (checkpoint restore / teacher forcing). */
 void or_set_lbest(or_state* st, const int32_t* lbest, const double* clen) {
     memcpy(st->lbest, lbest, sizeof(int32_t) * (size_t)st->p.m * st->p.n);
