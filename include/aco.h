@@ -189,6 +189,75 @@ void aco_batch_destroy(aco_batch* b);
 aco_status aco_build_candidates_noalloc(const double* xy_dev, int32_t n, int32_t k, int32_t* cand_out_dev,
                                         void* stream);
 
+/* A borrowed handle of instance i of a batch (valid until aco_batch_destroy), for the calls that
+ * read or retune one colony: aco_get_state, aco_get_stats, aco_edge_features, aco_tour_labels,
+ * aco_set_edge_scores.  Its work goes to the batch's stream.  Advancing it with
+ * aco_construct_tours / aco_update_pheromone is not supported while it belongs to a batch. */
+aco_status aco_batch_instance(aco_batch* b, int32_t i, aco_instance** out);
+
+/* ------------------------------------------------------------------ learned edge proposal
+ * An extension of the method, not in the paper: a small network scores every candidate edge
+ * (i, cand[i][r]) and the score stands in for eta_ij^beta of Eq. 1 (Section 2) on candidate
+ * edges; edges outside the candidate lists (the exhausted-list rule) keep eta^beta, and NULL
+ * scores restore the plain heuristic everywhere.
+ *
+ * Features (one row of 16 BF16 values per candidate edge, rows in (city, rank) order), with
+ * j = cand[i][r] and dbar_i the mean distance from i to its k candidates:
+ *   x0 = d_ij / dbar_i, x1 = r / (k - 1), x2 = (x_j - x_i) / dbar_i, x3 = (y_j - y_i) / dbar_i,
+ *   x4 = deg_j / 32 (deg_j = distinct neighbours of j in the l_best tours of ants 0 .. D-1),
+ *   x5 = 1, x6 .. x15 = 0.
+ * Network (weights as one FP32 vector of ACO_MLP_WEIGHTS entries: W1 [64][16], W2 [64][64],
+ * w3 [64], row-major, used as BF16; products accumulate in FP32 on the tensor cores):
+ *   h1 = relu(W1 x) with h1[63] = 1;  h2 = relu(W2 h1) with h2[63] = 1;  z = w3 . h2;
+ *   score = exp(min(max(z, -60), 60)).
+ * Training target: per city, the softmax of z over its k candidate edges against the
+ * candidate ranks that are its neighbours in a best tour (a bitmask per city; cities without
+ * such a rank are left out); cross-entropy loss, Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the
+ * FP32 weights.  W1's row 63 and columns 6..15 and W2's row 63 are held at zero. */
+#define ACO_MLP_WEIGHTS (64 * 16 + 64 * 64 + 64)
+typedef struct aco_mlp aco_mlp; /* opaque: weights, optimiser state and training scratch */
+
+/* w_host: ACO_MLP_WEIGHTS initial FP32 weights (finite).  max_rows: the most candidate-edge rows
+ * one aco_mlp_backward call or one aco_mlp_train batch may hold (16 .. 2^30; about 600 bytes of
+ * device memory per row).  stream: cudaStream_t for all of this network's work (NULL = legacy
+ * default stream).  Allocates everything.  Synchronises. */
+aco_status aco_mlp_create(const float* w_host, int64_t max_rows, void* stream, aco_mlp** out);
+/* The FP32 weights (ACO_MLP_WEIGHTS floats).  Synchronises. */
+aco_status aco_mlp_get_weights(aco_mlp* h, float* w_host);
+/* z_dev and/or score_dev (rows floats each; either may be NULL, not both) for rows of BF16
+ * features X_dev (rows * 16 BF16 bit patterns).  No row limit.  Enqueued. */
+aco_status aco_mlp_forward(aco_mlp* h, const uint16_t* X_dev, int64_t rows, float* z_dev, float* score_dev);
+/* Gradient of scale * (summed loss over `cities` cities of k rows each, k <= 32) with respect to
+ * the weights into grad_dev (ACO_MLP_WEIGHTS floats, may be NULL: then kept inside for
+ * aco_mlp_adam) and the scaled loss into loss_dev[0] (may be NULL).  cities * k <= max_rows.
+ * Deterministic (fixed-order reductions).  Enqueued. */
+aco_status aco_mlp_backward(aco_mlp* h, const uint16_t* X_dev, const uint32_t* target_dev, int32_t cities,
+                            int32_t k, float scale, float* grad_dev, float* loss_dev);
+/* One Adam step with grad_dev (NULL = the gradient the last aco_mlp_backward kept) and learning
+ * rate lr >= 0.  Enqueued. */
+aco_status aco_mlp_adam(aco_mlp* h, const float* grad_dev, float lr);
+/* `steps` training steps over the data in order, batch_cities cities (batch_cities * k <= max_rows)
+ * per step, wrapping around: backward with scale 1 / (cities in the step), then Adam.  Mean loss
+ * of step t into loss_dev[t] (may be NULL).  Enqueued. */
+aco_status aco_mlp_train(aco_mlp* h, const uint16_t* X_dev, const uint32_t* target_dev, int32_t cities, int32_t k,
+                         int32_t batch_cities, int32_t steps, float lr, float* loss_dev);
+const char* aco_mlp_last_error(const aco_mlp* h);
+void aco_mlp_destroy(aco_mlp* h);
+
+/* Features of the instance's candidate edges into X_dev (n * k * 16 BF16), with the degree count
+ * over the l_best tours of ants 0 .. degree_ants-1 (1 <= degree_ants <= min(m, 16)).  Needs
+ * candidate lists and l_best tours (ACO_ERR_STATE otherwise).  Enqueued. */
+aco_status aco_edge_features(aco_instance* inst, int32_t degree_ants, uint16_t* X_dev);
+/* Per city (n uint32) the bitmask of candidate ranks holding its two neighbours in the best
+ * l_best tour (length C_gbest).  Needs l_best tours and k <= 32.  Enqueued. */
+aco_status aco_tour_labels(aco_instance* inst, uint32_t* target_dev);
+/* score_dev: n * k FP32 scores (finite, > 0) that replace eta^beta on the candidate edges from
+ * now on (until the next aco_build_candidates), or NULL to restore eta^beta.  The Eq. 1 weights
+ * are recomputed at once.  Not between aco_construct_tours and aco_update_pheromone
+ * (ACO_ERR_STATE).  Synchronises when score_dev is given (a non-finite or non-positive score
+ * gives ACO_ERR_INVALID_ARG and leaves the scores in use unchanged). */
+aco_status aco_set_edge_scores(aco_instance* inst, const float* score_dev);
+
 void aco_destroy_instance(aco_instance* inst);
 const char* aco_status_string(aco_status s);
 const char* aco_last_error(const aco_instance* inst);

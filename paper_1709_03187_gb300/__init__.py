@@ -23,7 +23,9 @@ __all__ = [
     "aco_tour_lengths", "aco_get_state", "aco_set_state", "aco_get_stats", "aco_step_probs",
     "aco_destroy_instance", "aco_build_candidates_noalloc", "aco_batch_create", "aco_batch_build_candidates",
     "aco_batch_run", "aco_batch_get_state", "aco_batch_get_best", "aco_batch_schedule", "aco_batch_destroy",
-    "Batch",
+    "Batch", "aco_batch_instance", "ACO_MLP_WEIGHTS", "aco_mlp_create", "aco_mlp_get_weights", "aco_mlp_forward",
+    "aco_mlp_backward", "aco_mlp_adam", "aco_mlp_train", "aco_mlp_destroy", "aco_edge_features", "aco_tour_labels",
+    "aco_set_edge_scores", "EdgeScorer",
 ]
 
 from .batch import Batch  # noqa: E402
@@ -32,3 +34,7 @@ from ._ffi import (aco_batch_build_candidates, aco_batch_create, aco_batch_destr
 from ._ffi import (aco_build_candidates, aco_build_candidates_noalloc, aco_construct_tours, aco_create_instance, aco_destroy_instance,  # noqa: E402
                    aco_get_state, aco_get_stats, aco_set_state, aco_step_probs, aco_tour_lengths,
                    aco_update_pheromone)
+from ._ffi import (ACO_MLP_WEIGHTS, aco_batch_instance, aco_edge_features, aco_mlp_adam,  # noqa: E402
+                   aco_mlp_backward, aco_mlp_create, aco_mlp_destroy, aco_mlp_forward, aco_mlp_get_weights,
+                   aco_mlp_train, aco_set_edge_scores, aco_tour_labels)
+from .learned import EdgeScorer  # noqa: E402

@@ -76,6 +76,18 @@ def lib():
             "aco_batch_schedule": (S, [V, V, V, V]),
             "aco_batch_last_error": (ctypes.c_char_p, [V]),
             "aco_batch_destroy": (None, [V]),
+            "aco_batch_instance": (S, [V, I32, ctypes.POINTER(V)]),
+            "aco_mlp_create": (S, [V, ctypes.c_int64, V, ctypes.POINTER(V)]),
+            "aco_mlp_get_weights": (S, [V, V]),
+            "aco_mlp_forward": (S, [V, V, ctypes.c_int64, V, V]),
+            "aco_mlp_backward": (S, [V, V, V, I32, I32, ctypes.c_float, V, V]),
+            "aco_mlp_adam": (S, [V, V, ctypes.c_float]),
+            "aco_mlp_train": (S, [V, V, V, I32, I32, I32, I32, ctypes.c_float, V]),
+            "aco_mlp_last_error": (ctypes.c_char_p, [V]),
+            "aco_mlp_destroy": (None, [V]),
+            "aco_edge_features": (S, [V, I32, V]),
+            "aco_tour_labels": (S, [V, V]),
+            "aco_set_edge_scores": (S, [V, V]),
             "aco_status_string": (ctypes.c_char_p, [S]),
             "aco_last_error": (ctypes.c_char_p, [V]),
         }
@@ -214,3 +226,75 @@ def aco_build_candidates_noalloc(xy_dev, n: int, k: int, cand_out_dev, stream=No
 def aco_destroy_instance(h):
     if h:
         lib().aco_destroy_instance(h)
+
+
+def aco_batch_instance(b, i: int):
+    h = ctypes.c_void_p()
+    _bcheck(lib().aco_batch_instance(b, i, ctypes.byref(h)), "aco_batch_instance", b)
+    return h.value
+
+
+# ------------------------------------------------------------------ learned edge proposal
+ACO_MLP_WEIGHTS = 64 * 16 + 64 * 64 + 64
+
+
+def _mcheck(status: int, where: str, h):
+    if status != 0:
+        msg = lib().aco_mlp_last_error(h) if h else b""
+        raise AcoError(status, where, msg.decode() if msg else "")
+
+
+def aco_mlp_create(w_host, max_rows: int, stream=None):
+    import numpy as np
+
+    w = np.ascontiguousarray(w_host, dtype=np.float32)
+    if w.size != ACO_MLP_WEIGHTS:
+        raise ValueError(f"expected {ACO_MLP_WEIGHTS} weights, got {w.size}")
+    h = ctypes.c_void_p()
+    _mcheck(lib().aco_mlp_create(w.ctypes.data_as(ctypes.c_void_p), int(max_rows), _stream_handle(stream),
+                                 ctypes.byref(h)), "aco_mlp_create", None)
+    return h.value
+
+
+def aco_mlp_get_weights(h):
+    import numpy as np
+
+    out = np.zeros(ACO_MLP_WEIGHTS, np.float32)
+    _mcheck(lib().aco_mlp_get_weights(h, out.ctypes.data_as(ctypes.c_void_p)), "aco_mlp_get_weights", h)
+    return out
+
+
+def aco_mlp_forward(h, X_dev, rows: int, z_dev=None, score_dev=None):
+    _mcheck(lib().aco_mlp_forward(h, _ptr(X_dev), int(rows), _ptr(z_dev), _ptr(score_dev)), "aco_mlp_forward", h)
+
+
+def aco_mlp_backward(h, X_dev, target_dev, cities: int, k: int, scale: float, grad_dev=None, loss_dev=None):
+    _mcheck(lib().aco_mlp_backward(h, _ptr(X_dev), _ptr(target_dev), cities, k, scale, _ptr(grad_dev),
+                                   _ptr(loss_dev)), "aco_mlp_backward", h)
+
+
+def aco_mlp_adam(h, grad_dev, lr: float):
+    _mcheck(lib().aco_mlp_adam(h, _ptr(grad_dev), lr), "aco_mlp_adam", h)
+
+
+def aco_mlp_train(h, X_dev, target_dev, cities: int, k: int, batch_cities: int, steps: int, lr: float,
+                  loss_dev=None):
+    _mcheck(lib().aco_mlp_train(h, _ptr(X_dev), _ptr(target_dev), cities, k, batch_cities, steps, lr,
+                                _ptr(loss_dev)), "aco_mlp_train", h)
+
+
+def aco_mlp_destroy(h):
+    if h:
+        lib().aco_mlp_destroy(h)
+
+
+def aco_edge_features(h, degree_ants: int, X_dev):
+    _check(lib().aco_edge_features(h, degree_ants, _ptr(X_dev)), "aco_edge_features", h)
+
+
+def aco_tour_labels(h, target_dev):
+    _check(lib().aco_tour_labels(h, _ptr(target_dev)), "aco_tour_labels", h)
+
+
+def aco_set_edge_scores(h, score_dev=None):
+    _check(lib().aco_set_edge_scores(h, _ptr(score_dev)), "aco_set_edge_scores", h)

@@ -25,6 +25,7 @@ UNITS = [
     ("update.cu", []),
     ("noalloc.cu", []),
     ("batch.cu", []),
+    ("mlp.cu", []),
 ]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -49,7 +49,7 @@ static void free_all(aco_instance* inst) {
                     inst->nb, inst->nbrank, inst->clen, inst->cfix, inst->q, inst->gbest, inst->gbest_ant,
                     inst->seg, inst->antit, inst->accq, inst->tau, inst->etab_d, inst->W64d, inst->W32d,
                     inst->tours, inst->succ_d, inst->pred_d, inst->counters, inst->errflag, inst->xy32,
-                    inst->ulist, inst->uxy, inst->bel, inst->btx, inst->btq};
+                    inst->ulist, inst->uxy, inst->bel, inst->btx, inst->btq, inst->deg};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -148,6 +148,7 @@ extern "C" aco_status aco_create_instance(const double* xy_dev, const aco_params
         ok &= dalloc(&inst->ulist, m * inst->ucap, &total);
         ok &= dalloc(&inst->uxy, m * inst->ucap, &total);
         ok &= dalloc(&inst->xy32, n, &total);
+        ok &= dalloc(&inst->deg, n, &total);
     } else {
         ok &= dalloc(&inst->tau, n * n, &total);
         ok &= dalloc(&inst->etab_d, n * n, &total);
@@ -232,7 +233,7 @@ extern "C" void aco_destroy_instance(aco_instance* inst) {
     delete inst;
 }
 
-static aco_status sync_and_check(aco_instance* inst, const char* what) {
+aco_status sync_and_check(aco_instance* inst, const char* what) {
     cudaError_t e = cudaStreamSynchronize(inst->stream);
     if (e != cudaSuccess) return set_err(inst, ACO_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
     int flag = 0;
@@ -243,6 +244,7 @@ static aco_status sync_and_check(aco_instance* inst, const char* what) {
         if (flag & DEVERR_DUPLICATE) return set_err(inst, ACO_ERR_INVALID_ARG, "%s: coincident cities", what);
         if (flag & DEVERR_BAD_TOUR) return set_err(inst, ACO_ERR_INVALID_ARG, "%s: tour index out of range", what);
         if (flag & DEVERR_NONFINITE) return set_err(inst, ACO_ERR_INVALID_ARG, "%s: non-finite weight", what);
+        if (flag & DEVERR_BAD_SCORE) return set_err(inst, ACO_ERR_INVALID_ARG, "%s: edge score not finite and > 0", what);
         return set_err(inst, ACO_ERR_CUDA, "%s: device error flag %d", what, flag);
     }
     return ACO_OK;
@@ -267,6 +269,7 @@ extern "C" aco_status aco_build_candidates(aco_instance* inst, int32_t* cand_out
     inst->cand_built = true;
     inst->constructed = false;
     inst->initialized = false;
+    inst->scored = false;
     return ACO_OK;
 }
 

@@ -313,6 +313,12 @@ extern "C" aco_status aco_batch_schedule(const aco_batch* b, int32_t* warps_out,
     return ACO_OK;
 }
 
+extern "C" aco_status aco_batch_instance(aco_batch* b, int32_t i, aco_instance** out) {
+    if (!b || !out || i < 0 || i >= b->count) return ACO_ERR_INVALID_ARG;
+    *out = b->inst[i];
+    return ACO_OK;
+}
+
 extern "C" void aco_batch_destroy(aco_batch* b) {
     if (!b) return;
     cudaStreamSynchronize(b->stream);

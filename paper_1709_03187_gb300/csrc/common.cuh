@@ -131,6 +131,7 @@ enum : int {
     DEVERR_BAD_TOUR = 2,       // tour index out of range
     DEVERR_NONFINITE = 4,      // eta^beta or a weight is not finite
     DEVERR_NO_CHOICE = 8,      // an ant found no unvisited city (internal inconsistency)
+    DEVERR_BAD_SCORE = 16,     // an edge score that is not finite and > 0
 };
 
 // ------------------------------------------------------------------ grid
@@ -267,6 +268,8 @@ struct aco_instance {
     float2* uxy;           // m*ucap their FP32 coordinates
     int32_t ucap;          // largest rebuilt count, n - max(1, n - floor(f n))
     float coord_r;         // max |coordinate| (rounded up)
+    int32_t* deg;          // n degree-in-best-tours scratch of the edge features
+    bool scored;           // candidate edges carry learned scores instead of eta^beta
 
     // dense mode
     double* tau;           // n*n
@@ -285,6 +288,8 @@ struct aco_instance {
 // ------------------------------------------------------------------ host helpers
 aco_status set_err(aco_instance* inst, aco_status s, const char* fmt, ...);
 aco_status check_launch(aco_instance* inst, const char* what);
+aco_status sync_and_check(aco_instance* inst, const char* what);
+aco_status launch_reweight(aco_instance* inst);
 
 // kernels launched from the API (defined in the .cu files)
 aco_status launch_build_grid_and_knn(aco_instance* inst);

@@ -1,0 +1,715 @@
+// mlp.cu -- learned edge proposal: a 3-layer MLP that scores candidate edges in place of
+// eta^beta, with its training on the GPU.
+//
+// Network (per candidate edge, row-major rows of 16 BF16 inputs):
+//   h1 = relu(W1 x)      W1: 64 x 16   (input 5 is the constant 1: column 5 of W1 is the bias)
+//   h1[63] = 1           (constant unit: column 63 of W2 is the layer-2 bias)
+//   h2 = relu(W2 h1)     W2: 64 x 64
+//   h2[63] = 1           (constant unit: w3[63] is the output bias)
+//   z  = w3 . h2         score = exp(z)
+// BF16 weights and activations, FP32 accumulation on the tensor cores (mma m16n8k16), the
+// hidden activations rounded to BF16 between layers.
+//
+// Training objective: for every city, the softmax of z over its k candidate edges against the
+// best tour's edges among them (cross-entropy; each of the city's best-tour neighbours that is a
+// candidate carries equal target mass).  Gradients:
+//   dz = softmax(z) - y;  dh2 = dz w3 * [h2 > 0];  dh1 = dh2 W2 * [h1 > 0]  (constant units 0)
+//   dW2 = dh2^T h1;  dW1 = dh1^T x;  dw3 = dz^T h2
+// The weight gradients are split-K over blocks with per-block partial sums and a fixed-order
+// reduction, so a training step is deterministic.  Adam on FP32 master weights.
+#include <cuda_bf16.h>
+#include <float.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "common.cuh"
+
+#define FULL 0xffffffffu
+#define MLP_IN 16
+#define MLP_H 64
+
+typedef __nv_bfloat16 bf16;
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// D = A(16x16 bf16, row) * B(16x8 bf16, col) + C (fp32)
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+struct MlpWeights {  // BF16 copies used by the kernels
+    const bf16* W1;  // [64][16]
+    const bf16* W2;  // [64][64]
+    const bf16* w3;  // [64]
+};
+
+// Stage the BF16 weights in shared memory (W2 also transposed for the backward pass).
+struct MlpSmem {
+    bf16 W1[MLP_H * MLP_IN];
+    bf16 W2[MLP_H * MLP_H];
+    bf16 W2T[MLP_H * MLP_H];
+    float w3[MLP_H];
+};
+
+__device__ void load_weights(MlpSmem& sh, const MlpWeights& w) {
+    for (int i = threadIdx.x; i < MLP_H * MLP_IN; i += blockDim.x) sh.W1[i] = w.W1[i];
+    for (int i = threadIdx.x; i < MLP_H * MLP_H; i += blockDim.x) {
+        sh.W2[i] = w.W2[i];
+        const int r = i / MLP_H, c = i % MLP_H;
+        sh.W2T[c * MLP_H + r] = w.W2[i];
+    }
+    for (int i = threadIdx.x; i < MLP_H; i += blockDim.x) sh.w3[i] = __bfloat162float(w.w3[i]);
+    __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// Forward of 16 rows starting at r0 (rows >= R are zero inputs).  Returns z for rows g and g+8
+// (g = lane >> 2) in lanes with t == 0; optionally stores h1, h2 (BF16) for the backward pass.
+__device__ void forward16(const MlpSmem& sh, const bf16* __restrict__ X, long long r0, long long R, int lane, bf16* h1out,
+                          bf16* h2out, float& z_lo, float& z_hi) {
+    const int g = lane >> 2, t = lane & 3;
+    const long long ra = r0 + g, rb = r0 + g + 8;
+    uint32_t a[4];
+    a[0] = ra < R ? ld32(X + (size_t)ra * MLP_IN + 2 * t) : 0u;
+    a[1] = rb < R ? ld32(X + (size_t)rb * MLP_IN + 2 * t) : 0u;
+    a[2] = ra < R ? ld32(X + (size_t)ra * MLP_IN + 8 + 2 * t) : 0u;
+    a[3] = rb < R ? ld32(X + (size_t)rb * MLP_IN + 8 + 2 * t) : 0u;
+    // layer 1: 8 output tiles of 8 units
+    float h1[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        h1[j][0] = h1[j][1] = h1[j][2] = h1[j][3] = 0.f;
+        const uint32_t b[2] = {ld32(&sh.W1[(8 * j + g) * MLP_IN + 2 * t]), ld32(&sh.W1[(8 * j + g) * MLP_IN + 8 + 2 * t])};
+        mma_bf16(h1[j], a, b);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int col = 8 * j + 2 * t + (e & 1);
+            float v = fmaxf(h1[j][e], 0.f);
+            if (col == MLP_H - 1) v = 1.f;
+            h1[j][e] = bf16_round(v);
+        }
+    }
+    if (h1out) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (ra < R) *reinterpret_cast<uint32_t*>(h1out + (size_t)ra * MLP_H + 8 * j + 2 * t) = pack_bf16(h1[j][0], h1[j][1]);
+            if (rb < R) *reinterpret_cast<uint32_t*>(h1out + (size_t)rb * MLP_H + 8 * j + 2 * t) = pack_bf16(h1[j][2], h1[j][3]);
+        }
+    }
+    // layer 2: A fragments from the layer-1 accumulators (k-step s = tiles 2s, 2s+1)
+    float h2[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) h2[j][0] = h2[j][1] = h2[j][2] = h2[j][3] = 0.f;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const uint32_t as[4] = {pack_bf16(h1[2 * s][0], h1[2 * s][1]), pack_bf16(h1[2 * s][2], h1[2 * s][3]),
+                                pack_bf16(h1[2 * s + 1][0], h1[2 * s + 1][1]),
+                                pack_bf16(h1[2 * s + 1][2], h1[2 * s + 1][3])};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t b[2] = {ld32(&sh.W2[(8 * j + g) * MLP_H + 16 * s + 2 * t]),
+                                   ld32(&sh.W2[(8 * j + g) * MLP_H + 16 * s + 8 + 2 * t])};
+            mma_bf16(h2[j], as, b);
+        }
+    }
+    float zl = 0.f, zh = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int col = 8 * j + 2 * t + (e & 1);
+            float v = fmaxf(h2[j][e], 0.f);
+            if (col == MLP_H - 1) v = 1.f;
+            v = bf16_round(v);
+            h2[j][e] = v;
+            if (e < 2) zl = __fmaf_rn(v, sh.w3[col], zl);
+            else zh = __fmaf_rn(v, sh.w3[col], zh);
+        }
+    }
+    if (h2out) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (ra < R) *reinterpret_cast<uint32_t*>(h2out + (size_t)ra * MLP_H + 8 * j + 2 * t) = pack_bf16(h2[j][0], h2[j][1]);
+            if (rb < R) *reinterpret_cast<uint32_t*>(h2out + (size_t)rb * MLP_H + 8 * j + 2 * t) = pack_bf16(h2[j][2], h2[j][3]);
+        }
+    }
+    // layer 3: reduce the four partial dot products of each row
+    zl += __shfl_xor_sync(FULL, zl, 1);
+    zl += __shfl_xor_sync(FULL, zl, 2);
+    zh += __shfl_xor_sync(FULL, zh, 1);
+    zh += __shfl_xor_sync(FULL, zh, 2);
+    z_lo = zl;
+    z_hi = zh;
+}
+
+// z and/or score = exp(z) (z clamped to [-60, 60]), optionally h1 and h2, for R rows; 4 warps
+// per block, 16 rows per warp per step.
+__global__ void __launch_bounds__(128) mlp_forward_kernel(MlpWeights w, const bf16* __restrict__ X, long long R,
+                                                          float* __restrict__ z, float* __restrict__ score,
+                                                          bf16* __restrict__ h1, bf16* __restrict__ h2) {
+    __shared__ MlpSmem sh;
+    load_weights(sh, w);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    for (long long r0 = (blockIdx.x * 4LL + warp) * 16; r0 < R; r0 += gridDim.x * 64LL) {
+        float zl, zh;
+        forward16(sh, X, r0, R, lane, h1, h2, zl, zh);
+        if (t == 0) {
+            if (r0 + g < R) {
+                if (z) z[r0 + g] = zl;
+                if (score) score[r0 + g] = __expf(fminf(fmaxf(zl, -60.f), 60.f));
+            }
+            if (r0 + g + 8 < R) {
+                if (z) z[r0 + g + 8] = zh;
+                if (score) score[r0 + g + 8] = __expf(fminf(fmaxf(zh, -60.f), 60.f));
+            }
+        }
+    }
+}
+
+// Softmax cross-entropy per city over its k consecutive rows.  target: per city a bitmask of
+// the candidate ranks that are best-tour neighbours (cities with no such rank are skipped).
+// dz[row] = softmax - y; loss per city into city_loss (0 when skipped).
+__global__ void mlp_loss_kernel(const float* __restrict__ z, const uint32_t* __restrict__ target, int cities, int k,
+                                float* __restrict__ dz, float* __restrict__ city_loss) {
+    const int lane = threadIdx.x & 31;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < cities; c += (gridDim.x * blockDim.x) >> 5) {
+        const uint32_t tm = target[c];
+        const float zi = lane < k ? z[(size_t)c * k + lane] : -FLT_MAX;
+        float mx = zi;
+        for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
+        const float e = lane < k ? __expf(zi - mx) : 0.f;
+        float se = e;
+        for (int o = 16; o; o >>= 1) se += __shfl_xor_sync(FULL, se, o);
+        const int nt = __popc(tm);
+        const float y = (nt > 0 && ((tm >> lane) & 1u)) ? 1.f / (float)nt : 0.f;
+        const float p = e / se;
+        if (lane < k) dz[(size_t)c * k + lane] = nt > 0 ? p - y : 0.f;
+        float l = (y > 0.f) ? -y * (zi - mx - __logf(se)) : 0.f;
+        for (int o = 16; o; o >>= 1) l += __shfl_xor_sync(FULL, l, o);
+        if (lane == 0) city_loss[c] = nt > 0 ? l : 0.f;
+    }
+}
+
+// Backward over rows: dh2 = dz w3 [h2 > 0], dh1 = dh2 W2 [h1 > 0] (constant units get 0).
+// Also writes dz as a BF16 [R][16] matrix (column 0) for the dw3 reduction.
+__global__ void __launch_bounds__(128) mlp_backward_rows_kernel(MlpWeights w, const float* __restrict__ dz, int R,
+                                                                const bf16* __restrict__ h1,
+                                                                const bf16* __restrict__ h2, bf16* __restrict__ dh1,
+                                                                bf16* __restrict__ dh2, bf16* __restrict__ dzm) {
+    __shared__ MlpSmem sh;
+    load_weights(sh, w);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    for (int r0 = (blockIdx.x * 4 + warp) * 16; r0 < R; r0 += gridDim.x * 64) {
+        const int ra = r0 + g, rb = r0 + g + 8;
+        const float dza = ra < R ? dz[ra] : 0.f, dzb = rb < R ? dz[rb] : 0.f;
+        // dh2 in A-fragment layout: k-step s covers columns 16s..16s+15
+        uint32_t a[4][4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {  // columns 16s + 8hh + 2t, +1
+                const int col = 16 * s + 8 * hh + 2 * t;
+                float v[4];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const float ha = ra < R ? __bfloat162float(h2[(size_t)ra * MLP_H + col + e]) : 0.f;
+                    const float hb = rb < R ? __bfloat162float(h2[(size_t)rb * MLP_H + col + e]) : 0.f;
+                    const bool live = col + e != MLP_H - 1;
+                    v[e] = (live && ha > 0.f) ? dza * sh.w3[col + e] : 0.f;
+                    v[2 + e] = (live && hb > 0.f) ? dzb * sh.w3[col + e] : 0.f;
+                }
+                a[s][2 * hh] = pack_bf16(v[0], v[1]);
+                a[s][2 * hh + 1] = pack_bf16(v[2], v[3]);
+                if (ra < R) *reinterpret_cast<uint32_t*>(dh2 + (size_t)ra * MLP_H + col) = a[s][2 * hh];
+                if (rb < R) *reinterpret_cast<uint32_t*>(dh2 + (size_t)rb * MLP_H + col) = a[s][2 * hh + 1];
+            }
+        }
+        // dh1 = dh2 W2: B(k = h2 unit, n = h1 unit) = W2[k][n] = W2T[n][k]
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const uint32_t b[2] = {ld32(&sh.W2T[(8 * j + g) * MLP_H + 16 * s + 2 * t]),
+                                       ld32(&sh.W2T[(8 * j + g) * MLP_H + 16 * s + 8 + 2 * t])};
+                mma_bf16(d, a[s], b);
+            }
+            const int col = 8 * j + 2 * t;
+            float v[4];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const float ha = ra < R ? __bfloat162float(h1[(size_t)ra * MLP_H + col + e]) : 0.f;
+                const float hb = rb < R ? __bfloat162float(h1[(size_t)rb * MLP_H + col + e]) : 0.f;
+                const bool live = col + e != MLP_H - 1;
+                v[e] = (live && ha > 0.f) ? d[e] : 0.f;
+                v[2 + e] = (live && hb > 0.f) ? d[2 + e] : 0.f;
+            }
+            if (ra < R) *reinterpret_cast<uint32_t*>(dh1 + (size_t)ra * MLP_H + col) = pack_bf16(v[0], v[1]);
+            if (rb < R) *reinterpret_cast<uint32_t*>(dh1 + (size_t)rb * MLP_H + col) = pack_bf16(v[2], v[3]);
+        }
+        if (t == 0) {
+            if (ra < R) dzm[(size_t)ra * 16] = __float2bfloat16_rn(dza);
+            if (rb < R) dzm[(size_t)rb * 16] = __float2bfloat16_rn(dzb);
+        }
+    }
+}
+
+// Split-K partial products C_b = P^T Q over the rows of block b: P [R][MP], Q [R][NQ] (BF16),
+// MP in {16, 64}, NQ in {16, 64}.  Rows in 16-row steps; partial[b][MP][NQ] in FP32.
+// Each warp owns output tiles (16 rows of C) x (8 columns); fragments are assembled from
+// shared-memory copies of the row step.
+template <int MP, int NQ>
+__global__ void __launch_bounds__(128) mlp_wgrad_kernel(const bf16* __restrict__ P, const bf16* __restrict__ Q, int R,
+                                                        int rows_per_block, float* __restrict__ partial) {
+    constexpr int MT = MP / 16, NT = NQ / 8, TILES = MT * NT, TPW = (TILES + 3) / 4;
+    __shared__ bf16 Ps[16][MP];
+    __shared__ bf16 Qs[16][NQ];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    float acc[TPW][4];
+#pragma unroll
+    for (int i = 0; i < TPW; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+    const int rbeg = blockIdx.x * rows_per_block, rend = min(R, rbeg + rows_per_block);
+    for (int r0 = rbeg; r0 < rend; r0 += 16) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 16 * MP; i += blockDim.x) {
+            const int rr = i / MP, cc = i % MP;
+            Ps[rr][cc] = r0 + rr < rend ? P[(size_t)(r0 + rr) * MP + cc] : __float2bfloat16_rn(0.f);
+        }
+        for (int i = threadIdx.x; i < 16 * NQ; i += blockDim.x) {
+            const int rr = i / NQ, cc = i % NQ;
+            Qs[rr][cc] = r0 + rr < rend ? Q[(size_t)(r0 + rr) * NQ + cc] : __float2bfloat16_rn(0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < TPW; ++i) {
+            const int tile = warp * TPW + i;
+            if (tile >= TILES) break;
+            const int mt = tile / NT, nt = tile % NT;
+            // A = P^T (m = C row, k = data row): a0 (m g, k 2t..2t+1), a1 (m g+8), a2 (k +8), a3
+            const int m0 = 16 * mt;
+            uint32_t a[4];
+            a[0] = pack_bf16(__bfloat162float(Ps[2 * t][m0 + g]), __bfloat162float(Ps[2 * t + 1][m0 + g]));
+            a[1] = pack_bf16(__bfloat162float(Ps[2 * t][m0 + g + 8]), __bfloat162float(Ps[2 * t + 1][m0 + g + 8]));
+            a[2] = pack_bf16(__bfloat162float(Ps[2 * t + 8][m0 + g]), __bfloat162float(Ps[2 * t + 9][m0 + g]));
+            a[3] = pack_bf16(__bfloat162float(Ps[2 * t + 8][m0 + g + 8]), __bfloat162float(Ps[2 * t + 9][m0 + g + 8]));
+            // B = Q (k = data row, n = C column): b0 (k 2t..2t+1, n g), b1 (k +8)
+            const int n0 = 8 * nt;
+            uint32_t b[2];
+            b[0] = pack_bf16(__bfloat162float(Qs[2 * t][n0 + g]), __bfloat162float(Qs[2 * t + 1][n0 + g]));
+            b[1] = pack_bf16(__bfloat162float(Qs[2 * t + 8][n0 + g]), __bfloat162float(Qs[2 * t + 9][n0 + g]));
+            mma_bf16(acc[i], a, b);
+        }
+    }
+    float* out = partial + (size_t)blockIdx.x * MP * NQ;
+#pragma unroll
+    for (int i = 0; i < TPW; ++i) {
+        const int tile = warp * TPW + i;
+        if (tile >= TILES) break;
+        const int mt = tile / NT, nt = tile % NT;
+        const int m = 16 * mt + g, n = 8 * nt + 2 * t;
+        out[(size_t)m * NQ + n] = acc[i][0];
+        out[(size_t)m * NQ + n + 1] = acc[i][1];
+        out[(size_t)(m + 8) * NQ + n] = acc[i][2];
+        out[(size_t)(m + 8) * NQ + n + 1] = acc[i][3];
+    }
+}
+
+__global__ void mlp_scale_kernel(float* __restrict__ v, int count, float scale) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) v[e] *= scale;
+}
+
+// grad[e] = sum over blocks (in block order) of partial[b * stride + e] * scale, e < elems.
+__global__ void mlp_reduce_kernel(const float* __restrict__ partial, int blocks, int stride, int elems, float scale,
+                                  float* __restrict__ grad) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < elems; e += gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int b = 0; b < blocks; ++b) s += partial[(size_t)b * stride + e];
+        grad[e] = s * scale;
+    }
+}
+
+// Adam on FP32 master weights; BF16 copies refreshed.  mask: 1 = trainable entry.
+__global__ void mlp_adam_kernel(float* __restrict__ w, float* __restrict__ m1, float* __restrict__ m2,
+                                const float* __restrict__ grad, const uint8_t* __restrict__ mask, int elems, float lr,
+                                float b1, float b2, float eps, float c1, float c2, bf16* __restrict__ wb) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < elems; e += gridDim.x * blockDim.x) {
+        if (mask[e]) {
+            const float gr = grad[e];
+            const float a = b1 * m1[e] + (1.f - b1) * gr;
+            const float bsq = b2 * m2[e] + (1.f - b2) * gr * gr;
+            m1[e] = a;
+            m2[e] = bsq;
+            w[e] -= lr * (a / c1) / (sqrtf(bsq / c2) + eps);
+        }
+        wb[e] = __float2bfloat16_rn(w[e]);
+    }
+}
+
+// ---------------------------------------------------------------- features of candidate edges
+// Row (i, r) for candidate j = cand[i][r]:
+//   f0 = d_ij / dbar_i (dbar_i = mean candidate distance of i), f1 = r / (k - 1),
+//   f2 = (x_j - x_i) / dbar_i, f3 = (y_j - y_i) / dbar_i,
+//   f4 = deg_j / 32 where deg_j = distinct neighbours of j over the l_best tours of ants 0 .. D-1,
+//   f5 = 1 (bias input), f6..f15 = 0.
+__global__ void edge_features_kernel(const double* __restrict__ xy, const int* __restrict__ cand, int n, int k,
+                                     const int* __restrict__ deg, bf16* __restrict__ X) {
+    const int lane = threadIdx.x & 31;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5) {
+        const double xi = xy[2 * i], yi = xy[2 * i + 1];
+        double d = 0.0, dx = 0.0, dy = 0.0;
+        int j = 0;
+        if (lane < k) {
+            j = cand[(size_t)i * k + lane];
+            dx = xy[2 * j] - xi;
+            dy = xy[2 * j + 1] - yi;
+            d = sqrt(dx * dx + dy * dy);
+        }
+        float s = lane < k ? (float)d : 0.f;
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+        const float dbar = fmaxf(s / (float)k, 1e-30f);
+        if (lane < k) {
+            uint4* row = reinterpret_cast<uint4*>(X + ((size_t)i * k + lane) * MLP_IN);
+            const float f1 = k > 1 ? (float)lane / (float)(k - 1) : 0.f;
+            row[0] = make_uint4(pack_bf16((float)d / dbar, f1), pack_bf16((float)dx / dbar, (float)dy / dbar),
+                                pack_bf16((float)deg[j] * (1.f / 32.f), 1.f), 0u);
+            row[1] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+}
+
+// deg[j] = number of distinct cities among j's neighbours in the l_best tours of ants 0 .. D-1
+// (D <= 16: at most 32 entries, one per lane; equal entries found with __match_any_sync).
+__global__ void neighbour_degree_kernel(const int* __restrict__ nb, int n, int m, int D, int* __restrict__ deg) {
+    const int lane = threadIdx.x & 31;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n; j += (gridDim.x * blockDim.x) >> 5) {
+        const int x = lane < 2 * D ? nb[(size_t)j * m * 2 + lane] : -1 - lane;  // distinct dummies
+        const unsigned same = __match_any_sync(FULL, x);
+        const bool first = lane < 2 * D && (__ffs(same) - 1) == lane;
+        const int cnt = __popc(__ballot_sync(FULL, first));
+        if (lane == 0) deg[j] = cnt;
+    }
+}
+
+
+// best-tour labels: per city the bitmask of candidate ranks holding its two neighbours in the
+// l_best tour of the best ant (the tour of length C_gbest).
+__global__ void tour_labels_kernel(const uint8_t* __restrict__ nbrank, const int* __restrict__ gbest_ant, int n, int m,
+                                   int k, uint32_t* __restrict__ target) {
+    const int a = *gbest_ant;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t rs = nbrank[((size_t)i * m + a) * 2], rp = nbrank[((size_t)i * m + a) * 2 + 1];
+        target[i] = (rs < (uint32_t)k ? 1u << rs : 0u) | (rp < (uint32_t)k ? 1u << rp : 0u);
+    }
+}
+
+// Validate learned scores (finite and > 0), or convert them into the FP64 eta^beta table.
+__global__ void check_scores_kernel(const float* __restrict__ score, long long count, int* __restrict__ errflag) {
+    bool bad = false;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count; e += (long long)gridDim.x * blockDim.x)
+        bad |= !(score[e] > 0.f && score[e] <= FLT_MAX);
+    if (__any_sync(FULL, bad) && (threadIdx.x & 31) == 0) atomicOr(errflag, DEVERR_BAD_SCORE);
+}
+
+__global__ void scores_to_eta_kernel(const float* __restrict__ score, const double* __restrict__ xy,
+                                     const int* __restrict__ cand, int n, int k, double beta,
+                                     double* __restrict__ etab) {
+    const long long count = (long long)n * k;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count; e += (long long)gridDim.x * blockDim.x) {
+        if (score) {
+            etab[e] = (double)score[e];
+        } else {  // the plain heuristic, as the candidate-list builder computes it
+            const int i = (int)(e / k), j = cand[e];
+            etab[e] = eta_pow_from_d2(dist2(xy[2 * i], xy[2 * i + 1], xy[2 * j], xy[2 * j + 1]), beta);
+        }
+    }
+}
+
+__global__ void sum_kernel(const float* __restrict__ v, int count, float scale, float* __restrict__ out) {
+    __shared__ float part[32];
+    float s = 0.f;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) s += v[i];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        *out = t * scale;
+    }
+}
+
+// ---------------------------------------------------------------- the network handle
+#define MLP_NW (MLP_H * MLP_IN + MLP_H * MLP_H + MLP_H)
+#define MLP_RPB 256  // rows per block of the split-K weight gradients
+
+struct aco_mlp {
+    cudaStream_t stream;
+    long long max_rows;
+    int step;
+    float* w;       // FP32 master weights W1 | W2 | w3
+    float* m1;      // Adam moments
+    float* m2;
+    float* grad;
+    uint8_t* mask;  // trainable entries
+    bf16* wb;       // BF16 copies used by the kernels
+    float* z;       // max_rows
+    float* dz;      // max_rows
+    float* closs;   // max_rows (per city, cities <= rows)
+    bf16* h1;       // max_rows * 64
+    bf16* h2;
+    bf16* dh1;
+    bf16* dh2;
+    bf16* dzm;      // max_rows * 16
+    float* partial; // blocks * 4096
+    char err[256];
+};
+
+static MlpWeights weights_of(const aco_mlp* h) {
+    return MlpWeights{h->wb, h->wb + MLP_H * MLP_IN, h->wb + MLP_H * MLP_IN + MLP_H * MLP_H};
+}
+
+static void host_mask(uint8_t* mk) {
+    for (int u = 0; u < MLP_H; ++u)
+        for (int c = 0; c < MLP_IN; ++c) mk[u * MLP_IN + c] = (u < MLP_H - 1 && c < 6) ? 1 : 0;
+    for (int u = 0; u < MLP_H; ++u)
+        for (int c = 0; c < MLP_H; ++c) mk[MLP_H * MLP_IN + u * MLP_H + c] = u < MLP_H - 1 ? 1 : 0;
+    for (int c = 0; c < MLP_H; ++c) mk[MLP_H * MLP_IN + MLP_H * MLP_H + c] = 1;
+}
+
+static void free_mlp(aco_mlp* h) {
+    void* ptrs[] = {h->w, h->m1, h->m2, h->grad, h->mask, h->wb, h->z, h->dz, h->closs,
+                    h->h1, h->h2, h->dh1, h->dh2, h->dzm, h->partial};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+}
+
+static int blocks_for(long long rows, int per_block) {
+    long long b = (rows + per_block - 1) / per_block;
+    return (int)(b < 1 ? 1 : (b > 8192 ? 8192 : b));
+}
+
+static aco_status mlp_launch_ok(aco_mlp* h, const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return ACO_OK;
+    snprintf(h->err, sizeof(h->err), "%s: %s", what, cudaGetErrorString(e));
+    return ACO_ERR_CUDA;
+}
+
+extern "C" const char* aco_mlp_last_error(const aco_mlp* h) { return h ? h->err : ""; }
+
+extern "C" aco_status aco_mlp_create(const float* w_host, int64_t max_rows, void* stream, aco_mlp** out) {
+    if (!out || !w_host || max_rows < 16 || max_rows > (1LL << 30)) return ACO_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int e = 0; e < MLP_NW; ++e)
+        if (!isfinite(w_host[e])) return ACO_ERR_INVALID_ARG;
+    aco_mlp* h = new (std::nothrow) aco_mlp();
+    if (!h) return ACO_ERR_OOM;
+    memset(h, 0, sizeof(*h));
+    h->stream = (cudaStream_t)stream;
+    h->max_rows = max_rows;
+    const long long blocks = (max_rows + MLP_RPB - 1) / MLP_RPB;
+    bool ok = true;
+    ok &= cudaMalloc(&h->w, sizeof(float) * MLP_NW) == cudaSuccess;
+    ok &= cudaMalloc(&h->m1, sizeof(float) * MLP_NW) == cudaSuccess;
+    ok &= cudaMalloc(&h->m2, sizeof(float) * MLP_NW) == cudaSuccess;
+    ok &= cudaMalloc(&h->grad, sizeof(float) * MLP_NW) == cudaSuccess;
+    ok &= cudaMalloc(&h->mask, MLP_NW) == cudaSuccess;
+    ok &= cudaMalloc(&h->wb, sizeof(bf16) * MLP_NW) == cudaSuccess;
+    ok &= cudaMalloc(&h->z, sizeof(float) * max_rows) == cudaSuccess;
+    ok &= cudaMalloc(&h->dz, sizeof(float) * max_rows) == cudaSuccess;
+    ok &= cudaMalloc(&h->closs, sizeof(float) * max_rows) == cudaSuccess;
+    ok &= cudaMalloc(&h->h1, sizeof(bf16) * MLP_H * max_rows) == cudaSuccess;
+    ok &= cudaMalloc(&h->h2, sizeof(bf16) * MLP_H * max_rows) == cudaSuccess;
+    ok &= cudaMalloc(&h->dh1, sizeof(bf16) * MLP_H * max_rows) == cudaSuccess;
+    ok &= cudaMalloc(&h->dh2, sizeof(bf16) * MLP_H * max_rows) == cudaSuccess;
+    ok &= cudaMalloc(&h->dzm, sizeof(bf16) * 16 * max_rows) == cudaSuccess;
+    ok &= cudaMalloc(&h->partial, sizeof(float) * MLP_H * MLP_H * blocks) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_mlp(h);
+        delete h;
+        return ACO_ERR_OOM;
+    }
+    uint8_t mk[MLP_NW];
+    host_mask(mk);
+    float w0[MLP_NW];
+    for (int e = 0; e < MLP_NW; ++e) w0[e] = mk[e] ? w_host[e] : 0.f;
+    cudaMemcpyAsync(h->w, w0, sizeof(w0), cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(h->mask, mk, sizeof(mk), cudaMemcpyHostToDevice, h->stream);
+    cudaMemsetAsync(h->m1, 0, sizeof(float) * MLP_NW, h->stream);
+    cudaMemsetAsync(h->m2, 0, sizeof(float) * MLP_NW, h->stream);
+    cudaMemsetAsync(h->grad, 0, sizeof(float) * MLP_NW, h->stream);
+    // BF16 copies: an Adam step with zero learning rate leaves the masters and refreshes them
+    mlp_adam_kernel<<<blocks_for(MLP_NW, 256), 256, 0, h->stream>>>(h->w, h->m1, h->m2, h->grad, h->mask, MLP_NW, 0.f,
+                                                                    0.9f, 0.999f, 1e-8f, 1.f, 1.f, h->wb);
+    aco_status st = mlp_launch_ok(h, "create");
+    if (st == ACO_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) st = ACO_ERR_CUDA;
+    if (st != ACO_OK) {
+        free_mlp(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return ACO_OK;
+}
+
+extern "C" void aco_mlp_destroy(aco_mlp* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_mlp(h);
+    delete h;
+}
+
+extern "C" aco_status aco_mlp_get_weights(aco_mlp* h, float* w_host) {
+    if (!h || !w_host) return ACO_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpyAsync(w_host, h->w, sizeof(float) * MLP_NW, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        snprintf(h->err, sizeof(h->err), "get_weights: %s", cudaGetErrorString(e));
+        return ACO_ERR_CUDA;
+    }
+    return ACO_OK;
+}
+
+extern "C" aco_status aco_mlp_forward(aco_mlp* h, const uint16_t* X_dev, int64_t rows, float* z_dev,
+                                      float* score_dev) {
+    if (!h || !X_dev || rows < 0 || (!z_dev && !score_dev)) return ACO_ERR_INVALID_ARG;
+    if (rows == 0) return ACO_OK;
+    mlp_forward_kernel<<<blocks_for(rows, 64), 128, 0, h->stream>>>(weights_of(h), (const bf16*)X_dev, rows, z_dev,
+                                                                   score_dev, nullptr, nullptr);
+    return mlp_launch_ok(h, "mlp_forward_kernel");
+}
+
+// forward with stored activations, loss, backward: gradient of scale * (summed loss) into
+// h->grad; the loss into loss_dev[0] if given.
+static aco_status mlp_backward(aco_mlp* h, const bf16* X, const uint32_t* target, int cities, int k, float scale,
+                               float* loss_dev) {
+    const int rows = cities * k;
+    cudaStream_t s = h->stream;
+    const MlpWeights w = weights_of(h);
+    mlp_forward_kernel<<<blocks_for(rows, 64), 128, 0, s>>>(w, X, rows, h->z, nullptr, h->h1, h->h2);
+    mlp_loss_kernel<<<blocks_for(cities, 8), 256, 0, s>>>(h->z, target, cities, k, h->dz, h->closs);
+    if (loss_dev) sum_kernel<<<1, 1024, 0, s>>>(h->closs, cities, scale, loss_dev);
+    // the row gradient kernels take dz * scale: fold the scale into dz once
+    cudaMemsetAsync(h->dzm, 0, sizeof(bf16) * (size_t)rows * 16, s);
+    mlp_scale_kernel<<<blocks_for(rows, 256), 256, 0, s>>>(h->dz, rows, scale);
+    mlp_backward_rows_kernel<<<blocks_for(rows, 64), 128, 0, s>>>(w, h->dz, rows, h->h1, h->h2, h->dh1, h->dh2,
+                                                                   h->dzm);
+    const int blocks = (rows + MLP_RPB - 1) / MLP_RPB;
+    float* gW1 = h->grad;
+    float* gW2 = h->grad + MLP_H * MLP_IN;
+    float* gw3 = h->grad + MLP_H * MLP_IN + MLP_H * MLP_H;
+    mlp_wgrad_kernel<64, 64><<<blocks, 128, 0, s>>>(h->dh2, h->h1, rows, MLP_RPB, h->partial);  // dW2 = dh2^T h1
+    mlp_reduce_kernel<<<16, 256, 0, s>>>(h->partial, blocks, MLP_H * MLP_H, MLP_H * MLP_H, 1.f, gW2);
+    mlp_wgrad_kernel<64, 16><<<blocks, 128, 0, s>>>(h->dh1, X, rows, MLP_RPB, h->partial);      // dW1 = dh1^T x
+    mlp_reduce_kernel<<<4, 256, 0, s>>>(h->partial, blocks, MLP_H * MLP_IN, MLP_H * MLP_IN, 1.f, gW1);
+    mlp_wgrad_kernel<16, 64><<<blocks, 128, 0, s>>>(h->dzm, h->h2, rows, MLP_RPB, h->partial);  // dw3 = dz^T h2
+    mlp_reduce_kernel<<<1, 64, 0, s>>>(h->partial, blocks, 16 * MLP_H, MLP_H, 1.f, gw3);  // row 0 of dzm^T h2
+    return mlp_launch_ok(h, "mlp backward");
+}
+
+extern "C" aco_status aco_mlp_backward(aco_mlp* h, const uint16_t* X_dev, const uint32_t* target_dev, int32_t cities,
+                                       int32_t k, float scale, float* grad_dev, float* loss_dev) {
+    if (!h || !X_dev || !target_dev || cities < 1 || k < 1 || k > 32 || !isfinite(scale)) return ACO_ERR_INVALID_ARG;
+    if ((long long)cities * k > h->max_rows) return ACO_ERR_INVALID_ARG;
+    aco_status st = mlp_backward(h, (const bf16*)X_dev, target_dev, cities, k, scale, loss_dev);
+    if (st == ACO_OK && grad_dev)
+        cudaMemcpyAsync(grad_dev, h->grad, sizeof(float) * MLP_NW, cudaMemcpyDeviceToDevice, h->stream);
+    return st == ACO_OK ? mlp_launch_ok(h, "backward copy") : st;
+}
+
+static aco_status mlp_adam(aco_mlp* h, const float* grad, float lr) {
+    h->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)h->step), c2 = 1.f - powf(b2, (float)h->step);
+    mlp_adam_kernel<<<blocks_for(MLP_NW, 256), 256, 0, h->stream>>>(h->w, h->m1, h->m2, grad, h->mask, MLP_NW, lr, b1,
+                                                                    b2, 1e-8f, c1, c2, h->wb);
+    return mlp_launch_ok(h, "mlp_adam_kernel");
+}
+
+extern "C" aco_status aco_mlp_adam(aco_mlp* h, const float* grad_dev, float lr) {
+    if (!h || !(lr >= 0.f) || !isfinite(lr)) return ACO_ERR_INVALID_ARG;
+    return mlp_adam(h, grad_dev ? grad_dev : h->grad, lr);
+}
+
+extern "C" aco_status aco_mlp_train(aco_mlp* h, const uint16_t* X_dev, const uint32_t* target_dev, int32_t cities,
+                                    int32_t k, int32_t batch_cities, int32_t steps, float lr, float* loss_dev) {
+    if (!h || !X_dev || !target_dev || cities < 1 || k < 1 || k > 32 || batch_cities < 1 || steps < 0 ||
+        !(lr >= 0.f) || !isfinite(lr))
+        return ACO_ERR_INVALID_ARG;
+    if ((long long)batch_cities * k > h->max_rows) return ACO_ERR_INVALID_ARG;
+    const bf16* X = (const bf16*)X_dev;
+    const int nb = (cities + batch_cities - 1) / batch_cities;
+    for (int t = 0; t < steps; ++t) {
+        const int b = t % nb;
+        const int c0 = b * batch_cities;
+        const int cn = cities - c0 < batch_cities ? cities - c0 : batch_cities;
+        aco_status st = mlp_backward(h, X + (size_t)c0 * k * MLP_IN, target_dev + c0, cn, k, 1.f / (float)cn,
+                                     loss_dev ? loss_dev + t : nullptr);
+        if (st != ACO_OK) return st;
+        st = mlp_adam(h, h->grad, lr);
+        if (st != ACO_OK) return st;
+    }
+    return ACO_OK;
+}
+
+// ---------------------------------------------------------------- instance side
+extern "C" aco_status aco_edge_features(aco_instance* inst, int32_t degree_ants, uint16_t* X_dev) {
+    if (!inst || !X_dev) return ACO_ERR_INVALID_ARG;
+    if (inst->p.mode != ACO_MODE_LBEST_PARTIAL || !inst->cand_built || !inst->initialized)
+        return set_err(inst, ACO_ERR_STATE, "edge_features: needs candidate lists and l_best tours");
+    if (degree_ants < 1 || degree_ants > 16 || degree_ants > inst->p.m)
+        return set_err(inst, ACO_ERR_INVALID_ARG, "edge_features: degree_ants must be in 1 .. min(m, 16)");
+    const int n = inst->p.n, k = inst->p.k;
+    neighbour_degree_kernel<<<blocks_for(n, 8), 256, 0, inst->stream>>>(inst->nb, n, inst->p.m, degree_ants, inst->deg);
+    edge_features_kernel<<<blocks_for(n, 8), 256, 0, inst->stream>>>(inst->xy, inst->cand, n, k, inst->deg, (bf16*)X_dev);
+    return check_launch(inst, "edge_features_kernel");
+}
+
+extern "C" aco_status aco_tour_labels(aco_instance* inst, uint32_t* target_dev) {
+    if (!inst || !target_dev) return ACO_ERR_INVALID_ARG;
+    if (inst->p.mode != ACO_MODE_LBEST_PARTIAL || !inst->initialized)
+        return set_err(inst, ACO_ERR_STATE, "tour_labels: needs l_best tours");
+    if (inst->p.k > 32) return set_err(inst, ACO_ERR_INVALID_ARG, "tour_labels: k > 32");
+    tour_labels_kernel<<<blocks_for(inst->p.n, 256), 256, 0, inst->stream>>>(inst->nbrank, inst->gbest_ant, inst->p.n,
+                                                                            inst->p.m, inst->p.k, target_dev);
+    return check_launch(inst, "tour_labels_kernel");
+}
+
+extern "C" aco_status aco_set_edge_scores(aco_instance* inst, const float* score_dev) {
+    if (!inst) return ACO_ERR_INVALID_ARG;
+    if (inst->p.mode != ACO_MODE_LBEST_PARTIAL || !inst->cand_built)
+        return set_err(inst, ACO_ERR_STATE, "set_edge_scores: needs candidate lists");
+    if (inst->constructed) return set_err(inst, ACO_ERR_STATE, "set_edge_scores: tours constructed, update pending");
+    const long long count = (long long)inst->p.n * inst->p.k;
+    if (score_dev) {
+        check_scores_kernel<<<blocks_for(count, 256), 256, 0, inst->stream>>>(score_dev, count, inst->errflag);
+        aco_status st = check_launch(inst, "check_scores_kernel");
+        if (st == ACO_OK) st = sync_and_check(inst, "set_edge_scores");
+        if (st != ACO_OK) return st;
+    }
+    scores_to_eta_kernel<<<blocks_for(count, 256), 256, 0, inst->stream>>>(score_dev, inst->xy, inst->cand, inst->p.n,
+                                                                          inst->p.k, inst->p.beta, inst->etab);
+    aco_status st = check_launch(inst, "scores_to_eta_kernel");
+    if (st != ACO_OK) return st;
+    st = launch_reweight(inst);
+    if (st != ACO_OK) return st;
+    inst->scored = score_dev != nullptr;
+    return ACO_OK;
+}

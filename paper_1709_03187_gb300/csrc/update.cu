@@ -279,6 +279,9 @@ aco_status launch_lbest_init_weights(aco_instance* inst) {
     return launch_rebuild(inst, 0);
 }
 
+// Candidate-edge weights recomputed from the current eta^beta table (after the table changes).
+aco_status launch_reweight(aco_instance* inst) { return launch_rebuild(inst, inst->initialized ? 1 : 0); }
+
 aco_status launch_update_lbest(aco_instance* inst) {
     const aco_params& p = inst->p;
     CommitArgs C;
