@@ -45,7 +45,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="lbest200k", choices=sorted(aco_synth.WORKLOADS) + ["batch512"])
+    ap.add_argument("--workload", default="lbest200k",
+                    choices=sorted(aco_synth.WORKLOADS) + ["batch512", "learned20k"])
     ap.add_argument("--ants", type=int, default=0, help="override m (profiling of smaller cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -449,10 +450,107 @@ def run_batch(args):
     print(json.dumps(out))
 
 
+# ------------------------------------------------------------------ learned proposal
+def _colony_curve(xy, n, m, k, f, seed, iters, scorer=None, target=None):
+    """One colony run: candidate lists, initial tours, (scores,) iterations; C_gbest read after
+    every iteration.  Returns (elapsed ms at each iteration, C_gbest at each iteration, ms of
+    the scoring step)."""
+    import torch
+
+    from paper_1709_03187_gb300 import Colony
+
+    col = Colony(xy, mode=1, n=n, m=m, k=k, max_mod_frac=f, seed=seed)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(iters + 3)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    col.build_candidates()
+    col.iterate(0)
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record()
+    if scorer is not None:
+        scorer.score(col.handle, n, k, 16, beta=2.0)
+    s1.record()
+    best = [col.stats()["gbest"]]
+    ev[1].record()
+    for it in range(1, iters):
+        col.iterate(it)
+        best.append(col.stats()["gbest"])
+        ev[it + 1].record()
+        if target is not None and best[-1] <= target:
+            break
+    torch.cuda.synchronize()
+    ms = [ev[0].elapsed_time(ev[i + 1]) for i in range(len(best))]
+    col.close()
+    return ms, best, s0.elapsed_time(s1)
+
+
+def run_learned(args):
+    """Learned proposal against the plain heuristic at n = 20,000 (clustered, 100 clusters,
+    sigma = 0.01, k = 20, m = 512, f = 0.1).  Training: plain runs on 2,000 clustered instances of
+    n = 1,000 (5 clusters, sigma = 0.01: the evaluation's 200 cities per cluster), m = 32, k = 20,
+    f = 1, 40 iterations; labels from each instance's best tour; Adam over minibatches of 2,048
+    cities.  The plain arm runs 100 iterations; the learned arm runs until its C_gbest reaches the
+    plain arm's final C_gbest (at most 300 iterations).  Both arms read C_gbest after every
+    iteration and are timed with CUDA events from candidate lists to that iteration (each arm run
+    twice; the faster timing counts).  The learned score is exp(z)^beta with the instance's beta = 2."""
+    import torch
+
+    from paper_1709_03187_gb300 import EdgeScorer
+    from paper_1709_03187_gb300.learned import training_data
+
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    xys = [aco_synth.clustered(1000, 5, 0.01, 10_000 + i) for i in range(2000)]
+    t_gen = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record()
+    X, T, train_best = training_data(xys, m=32, k=20, iterations=40, max_mod_frac=1.0, seed=11)
+    e[1].record()
+    sc = EdgeScorer(aco_synth.mlp_weights(1), max_rows=2048 * 20)
+    loss = sc.train(X, T, 20, batch_cities=2048, steps=2000, lr=2e-3)
+    e[2].record()
+    torch.cuda.synchronize()
+    loss = loss.cpu().numpy()
+    n, m, k, f, iters = 20_000, 512, 20, 0.1, 100
+    rows = []
+    for s in (1, 2, 3):
+        xy = aco_synth.clustered(n, 100, 0.01, 20_000 + s)
+        # each arm twice (the runs are deterministic): the faster timing of each
+        runs_p = [_colony_curve(xy, n, m, k, f, s, iters) for _ in range(2)]
+        ms_p, best_p, _ = min(runs_p, key=lambda r: r[0][-1])
+        runs_l = [_colony_curve(xy, n, m, k, f, s, 3 * iters, scorer=sc, target=best_p[-1]) for _ in range(2)]
+        ms_l, best_l, ms_score = min(runs_l, key=lambda r: r[0][-1])
+        reached = best_l[-1] <= best_p[-1]
+        rows.append(dict(seed=s, plain_len=best_p[-1], plain_ms=ms_p[-1], plain_iters=iters,
+                         learned_iters=len(best_l) if reached else None, learned_ms=ms_l[-1] if reached else None,
+                         ratio=(ms_l[-1] / ms_p[-1]) if reached else None,
+                         score_ms=ms_score,
+                         len_at_iter_25=(best_p[24], best_l[24] if len(best_l) > 24 else None)))
+    ratios = [r["ratio"] for r in rows]
+    out = {"metric": "GPU wall-clock to reach the plain heuristic's mean tour length, learned / plain",
+           "value": round(float(np.mean(ratios)), 3) if all(r is not None for r in ratios) else None,
+           "unit": "ratio", "higher_is_better": False,
+           "workload": "learned20k: n=20,000 clustered (100 clusters, sigma=0.01), k=20, m=512, f=0.1, beta=2, plain "
+                       "100 iterations vs learned (score exp(z)^beta) until it reaches the plain final C_gbest; "
+                       "3 seeds",
+           "per_seed": rows,
+           "training": {"instances": 2000, "n": 1000, "plain_iterations": 40, "m": 32,
+                        "plain_ms": round(e[0].elapsed_time(e[1]), 1), "train_ms": round(e[1].elapsed_time(e[2]), 1),
+                        "steps": 2000, "batch_cities": 2048, "rows": int(X.shape[0]),
+                        "loss_first": float(loss[:20].mean()), "loss_last": float(loss[-20:].mean()),
+                        "train_instances_mean_gbest": float(np.mean(train_best)), "generate_s": round(t_gen, 1)}}
+    sc.close()
+    print(json.dumps(out))
+
+
 def main():
     args = parse_args()
     if args.workload == "batch512" and args.impl == "ours":
         run_batch(args)
+    elif args.workload == "learned20k" and args.impl == "ours":
+        run_learned(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -209,7 +209,8 @@ aco_status aco_batch_instance(aco_batch* b, int32_t i, aco_instance** out);
  * Network (weights as one FP32 vector of ACO_MLP_WEIGHTS entries: W1 [64][16], W2 [64][64],
  * w3 [64], row-major, used as BF16; products accumulate in FP32 on the tensor cores):
  *   h1 = relu(W1 x) with h1[63] = 1;  h2 = relu(W2 h1) with h2[63] = 1;  z = w3 . h2;
- *   score = exp(min(max(z, -60), 60)).
+ *   score = exp(min(max(beta z, -60), 60)): exp(z) is the learned counterpart of eta, raised to
+ *   the same exponent beta as eta in Eq. 1.
  * Training target: per city, the softmax of z over its k candidate edges against the
  * candidate ranks that are its neighbours in a best tour (a bitmask per city; cities without
  * such a rank are left out); cross-entropy loss, Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the
@@ -224,9 +225,10 @@ typedef struct aco_mlp aco_mlp; /* opaque: weights, optimiser state and training
 aco_status aco_mlp_create(const float* w_host, int64_t max_rows, void* stream, aco_mlp** out);
 /* The FP32 weights (ACO_MLP_WEIGHTS floats).  Synchronises. */
 aco_status aco_mlp_get_weights(aco_mlp* h, float* w_host);
-/* z_dev and/or score_dev (rows floats each; either may be NULL, not both) for rows of BF16
- * features X_dev (rows * 16 BF16 bit patterns).  No row limit.  Enqueued. */
-aco_status aco_mlp_forward(aco_mlp* h, const uint16_t* X_dev, int64_t rows, float* z_dev, float* score_dev);
+/* z_dev and/or score_dev = exp(beta z) (rows floats each; either may be NULL, not both) for rows of
+ * BF16 features X_dev (rows * 16 BF16 bit patterns).  No row limit.  Enqueued. */
+aco_status aco_mlp_forward(aco_mlp* h, const uint16_t* X_dev, int64_t rows, float* z_dev, float* score_dev,
+                           float beta);
 /* Gradient of scale * (summed loss over `cities` cities of k rows each, k <= 32) with respect to
  * the weights into grad_dev (ACO_MLP_WEIGHTS floats, may be NULL: then kept inside for
  * aco_mlp_adam) and the scaled loss into loss_dev[0] (may be NULL).  cities * k <= max_rows.

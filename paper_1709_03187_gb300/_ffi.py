@@ -79,7 +79,7 @@ def lib():
             "aco_batch_instance": (S, [V, I32, ctypes.POINTER(V)]),
             "aco_mlp_create": (S, [V, ctypes.c_int64, V, ctypes.POINTER(V)]),
             "aco_mlp_get_weights": (S, [V, V]),
-            "aco_mlp_forward": (S, [V, V, ctypes.c_int64, V, V]),
+            "aco_mlp_forward": (S, [V, V, ctypes.c_int64, V, V, ctypes.c_float]),
             "aco_mlp_backward": (S, [V, V, V, I32, I32, ctypes.c_float, V, V]),
             "aco_mlp_adam": (S, [V, V, ctypes.c_float]),
             "aco_mlp_train": (S, [V, V, V, I32, I32, I32, I32, ctypes.c_float, V]),
@@ -264,8 +264,9 @@ def aco_mlp_get_weights(h):
     return out
 
 
-def aco_mlp_forward(h, X_dev, rows: int, z_dev=None, score_dev=None):
-    _mcheck(lib().aco_mlp_forward(h, _ptr(X_dev), int(rows), _ptr(z_dev), _ptr(score_dev)), "aco_mlp_forward", h)
+def aco_mlp_forward(h, X_dev, rows: int, z_dev=None, score_dev=None, beta: float = 1.0):
+    _mcheck(lib().aco_mlp_forward(h, _ptr(X_dev), int(rows), _ptr(z_dev), _ptr(score_dev), beta), "aco_mlp_forward",
+            h)
 
 
 def aco_mlp_backward(h, X_dev, target_dev, cities: int, k: int, scale: float, grad_dev=None, loss_dev=None):

@@ -155,10 +155,10 @@ __device__ void forward16(const MlpSmem& sh, const bf16* __restrict__ X, long lo
     z_hi = zh;
 }
 
-// z and/or score = exp(z) (z clamped to [-60, 60]), optionally h1 and h2, for R rows; 4 warps
-// per block, 16 rows per warp per step.
+// z and/or score = exp(beta z) (beta z clamped to [-60, 60]), optionally h1 and h2, for R rows;
+// 4 warps per block, 16 rows per warp per step.
 __global__ void __launch_bounds__(128) mlp_forward_kernel(MlpWeights w, const bf16* __restrict__ X, long long R,
-                                                          float* __restrict__ z, float* __restrict__ score,
+                                                          float* __restrict__ z, float* __restrict__ score, float beta,
                                                           bf16* __restrict__ h1, bf16* __restrict__ h2) {
     __shared__ MlpSmem sh;
     load_weights(sh, w);
@@ -170,11 +170,11 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(MlpWeights w, const bf
         if (t == 0) {
             if (r0 + g < R) {
                 if (z) z[r0 + g] = zl;
-                if (score) score[r0 + g] = __expf(fminf(fmaxf(zl, -60.f), 60.f));
+                if (score) score[r0 + g] = __expf(fminf(fmaxf(beta * zl, -60.f), 60.f));
             }
             if (r0 + g + 8 < R) {
                 if (z) z[r0 + g + 8] = zh;
-                if (score) score[r0 + g + 8] = __expf(fminf(fmaxf(zh, -60.f), 60.f));
+                if (score) score[r0 + g + 8] = __expf(fminf(fmaxf(beta * zh, -60.f), 60.f));
             }
         }
     }
@@ -588,11 +588,11 @@ extern "C" aco_status aco_mlp_get_weights(aco_mlp* h, float* w_host) {
 }
 
 extern "C" aco_status aco_mlp_forward(aco_mlp* h, const uint16_t* X_dev, int64_t rows, float* z_dev,
-                                      float* score_dev) {
-    if (!h || !X_dev || rows < 0 || (!z_dev && !score_dev)) return ACO_ERR_INVALID_ARG;
+                                      float* score_dev, float beta) {
+    if (!h || !X_dev || rows < 0 || (!z_dev && !score_dev) || !isfinite(beta)) return ACO_ERR_INVALID_ARG;
     if (rows == 0) return ACO_OK;
     mlp_forward_kernel<<<blocks_for(rows, 64), 128, 0, h->stream>>>(weights_of(h), (const bf16*)X_dev, rows, z_dev,
-                                                                   score_dev, nullptr, nullptr);
+                                                                   score_dev, beta, nullptr, nullptr);
     return mlp_launch_ok(h, "mlp_forward_kernel");
 }
 
@@ -603,7 +603,7 @@ static aco_status mlp_backward(aco_mlp* h, const bf16* X, const uint32_t* target
     const int rows = cities * k;
     cudaStream_t s = h->stream;
     const MlpWeights w = weights_of(h);
-    mlp_forward_kernel<<<blocks_for(rows, 64), 128, 0, s>>>(w, X, rows, h->z, nullptr, h->h1, h->h2);
+    mlp_forward_kernel<<<blocks_for(rows, 64), 128, 0, s>>>(w, X, rows, h->z, nullptr, 1.f, h->h1, h->h2);
     mlp_loss_kernel<<<blocks_for(cities, 8), 256, 0, s>>>(h->z, target, cities, k, h->dz, h->closs);
     if (loss_dev) sum_kernel<<<1, 1024, 0, s>>>(h->closs, cities, scale, loss_dev);
     // the row gradient kernels take dz * scale: fold the scale into dz once

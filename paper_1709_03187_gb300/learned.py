@@ -1,7 +1,8 @@
 """EdgeScorer: the learned edge proposal (wrapper of aco_mlp_* and the instance-side calls).
 
-A 3-layer network over per-candidate-edge features scores every candidate edge; exp(z) replaces
-eta^beta of Eq. 1 on candidate edges, and the plain heuristic stays in place everywhere else.
+A 3-layer network over per-candidate-edge features scores every candidate edge; exp(z) is the
+learned counterpart of eta, and exp(z)^beta replaces eta^beta of Eq. 1 on candidate edges, while
+the plain heuristic stays in place everywhere else.
 Training uses the best tours that the plain method itself finds: the labels of a city are the
 candidate ranks of its two neighbours in the best l_best tour.  Features, forward pass, loss,
 backward pass and the optimiser all run in the library's kernels; this module only moves
@@ -44,11 +45,12 @@ class EdgeScorer:
         return _ffi.aco_mlp_get_weights(self._h)
 
     # -------------------------------------------------------------- network calls
-    def forward(self, X: torch.Tensor, z: bool = True, score: bool = False):
+    def forward(self, X: torch.Tensor, z: bool = True, score: bool = False, beta: float = 1.0):
+        """z and/or score = exp(beta z) per row."""
         rows = X.shape[0]
         zt = torch.empty(rows, dtype=torch.float32, device=X.device) if z else None
         st = torch.empty(rows, dtype=torch.float32, device=X.device) if score else None
-        _ffi.aco_mlp_forward(self._h, X, rows, zt, st)
+        _ffi.aco_mlp_forward(self._h, X, rows, zt, st, beta)
         return zt if not score else (st if not z else (zt, st))
 
     def backward(self, X: torch.Tensor, target: torch.Tensor, k: int, scale: float = 1.0):
@@ -82,11 +84,12 @@ class EdgeScorer:
         _ffi.aco_tour_labels(handle, T)
         return T
 
-    def score(self, handle, n: int, k: int, degree_ants: int = 16) -> torch.Tensor:
-        """Features of the instance's candidate edges, the network's scores, installed in place of
-        eta^beta.  Returns the scores (n * k float32)."""
+    def score(self, handle, n: int, k: int, degree_ants: int = 16, beta: float = 2.0) -> torch.Tensor:
+        """Features of the instance's candidate edges and the network's scores exp(z)^beta (beta:
+        the instance's Eq. 1 exponent of eta), installed in place of eta^beta.  Returns the scores
+        (n * k float32)."""
         X = self.features(handle, n, k, degree_ants)
-        s = self.forward(X, z=False, score=True)
+        s = self.forward(X, z=False, score=True, beta=beta)
         _ffi.aco_set_edge_scores(handle, s)
         return s
 

@@ -43,11 +43,13 @@ def test_forward_within_bf16_bound(rows):
     sc = EdgeScorer(w, max_rows=1 << 12)
     z, s = sc.forward(_to_dev_bf16(X), z=True, score=True)
     z, s = z.cpu().numpy().astype(np.float64), s.cpu().numpy().astype(np.float64)
+    s2 = sc.forward(_to_dev_bf16(X), z=False, score=True, beta=2.0).cpu().numpy().astype(np.float64)
     wo = _oracle_weights(w)
     zo = mlp.forward(wo, X)[0]
     bound = mlp.z_error_bound(wo, X)
     assert np.all(np.abs(z - zo) <= 1.05 * bound + 1e-6), np.max(np.abs(z - zo) - bound)
     assert np.all(np.abs(np.log(s) - np.clip(zo, -60, 60)) <= 1.05 * bound + 2e-6)
+    assert np.all(np.abs(np.log(s2) - np.clip(2 * zo, -60, 60)) <= 2 * 1.05 * bound + 4e-6)
     sc.close()
 
 
