@@ -49,7 +49,7 @@ static void free_all(aco_instance* inst) {
                     inst->nb, inst->nbrank, inst->clen, inst->cfix, inst->q, inst->gbest, inst->gbest_ant,
                     inst->seg, inst->antit, inst->accq, inst->tau, inst->etab_d, inst->W64d, inst->W32d,
                     inst->tours, inst->succ_d, inst->pred_d, inst->counters, inst->errflag, inst->xy32,
-                    inst->ulist, inst->uxy, inst->bel, inst->btx, inst->btq, inst->deg};
+                    inst->ulist, inst->uxy, inst->bel, inst->btx, inst->btq, inst->deg, inst->ghk, inst->ghq};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -140,6 +140,8 @@ extern "C" aco_status aco_create_instance(const double* xy_dev, const aco_params
         ok &= dalloc(&inst->bel, m * 2 * m, &total);
         ok &= dalloc(&inst->btx, m * 2 * m, &total);
         ok &= dalloc(&inst->btq, m * 2 * m, &total);
+        ok &= dalloc(&inst->ghk, m * 2 * m, &total);
+        ok &= dalloc(&inst->ghq, m * 2 * m, &total);
         long long fm = (long long)floor(p->max_mod_frac * (double)n);
         long long pmin = n - fm;
         if (pmin < 1) pmin = 1;
@@ -174,6 +176,8 @@ extern "C" aco_status aco_create_instance(const double* xy_dev, const aco_params
         if (inst->accq) cudaMemsetAsync(inst->accq, 0, sizeof(unsigned long long) * m * n, s);
         cudaMemsetAsync(inst->nb, 0xFF, sizeof(int32_t) * 2 * n * m, s);
         cudaMemsetAsync(inst->nbrank, 0xFF, 2 * n * m, s);
+        cudaMemsetAsync(inst->ghk, 0xFF, sizeof(int32_t) * 2 * m * m, s);
+        cudaMemsetAsync(inst->ghq, 0, sizeof(unsigned long long) * 2 * m * m, s);
     }
     // coordinates: finite, and bounding box * n small enough for the exact length grid
     double* hxy = (double*)malloc(sizeof(double) * 2 * n);

@@ -263,6 +263,8 @@ struct aco_instance {
     unsigned short* bel;       // m*2m per-ant list of non-candidate neighbour entries
     int32_t* btx;              // m*2m per-ant list of unvisited non-candidate neighbours
     unsigned long long* btq;   // m*2m and the weight of the ant of each such entry
+    int32_t* ghk;              // m*2m per-ant hash of boosted cities (kept all -1 between uses)
+    unsigned long long* ghq;   // m*2m their summed weights (kept 0 between uses)
     float2* xy32;          // n FP32 coordinates (distance screen of the exhausted-list rule)
     int32_t* ulist;        // m*ucap remaining discarded cities of each ant's partial rebuild
     float2* uxy;           // m*ucap their FP32 coordinates

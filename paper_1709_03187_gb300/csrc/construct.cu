@@ -59,6 +59,8 @@ struct LbestArgs {
     unsigned short* __restrict__ bel;
     int* __restrict__ btx;
     unsigned long long* __restrict__ btq;
+    int* __restrict__ ghk;                 // per-ant global hash of boosted cities (2m slots, -1 = empty)
+    unsigned long long* __restrict__ ghq;  // and their summed weights (0 when empty)
     int* __restrict__ ulist;
     float2* __restrict__ uxy;
     unsigned long long* __restrict__ counters;
@@ -151,10 +153,30 @@ __device__ __forceinline__ void top2_push(float w, int x, float& w1, int& x1, fl
 // of its entries.
 #define TOUCH_SM 96  // touched lists up to this length are aggregated in shared memory
 
+#define BHASH 128     // slots of the per-ant hash of boosted cities (distinct unvisited neighbours)
+#define BHASH_MAX 96  // more distinct cities than this: the listed path decides
+
 struct BoostSmem {
     int tx[TOUCH_SM];
     unsigned long long tq[TOUCH_SM];
+    unsigned long long hq[BHASH];  // summed integer pheromone of the city in each slot
+    int hkey[BHASH];               // city, -1 = empty (kept empty between exhausted steps)
+    int hcount;                    // distinct cities inserted
 };
+
+__device__ __forceinline__ unsigned bhash_slot(int x) { return ((unsigned)x * 2654435761u) >> 25; }
+
+// Empties the hash (four slots per lane).
+__device__ __forceinline__ void bhash_clear(BoostSmem& sh, int lane) {
+    __syncwarp();
+#pragma unroll
+    for (int s4 = 0; s4 < BHASH / 32; ++s4) {
+        sh.hkey[lane + 32 * s4] = -1;
+        sh.hq[lane + 32 * s4] = 0ull;
+    }
+    if (lane == 0) sh.hcount = 0;
+    __syncwarp();
+}
 
 // For 2m <= 2048 (m a multiple of 8) each lane holds 64 bytes of the rank row.
 struct RankRow {
@@ -317,27 +339,35 @@ __device__ void boosted_eval(const LbestArgs& A, int a, int cur, int nt, BoostSm
         __syncwarp();
         return;
     }
-    const bool in_smem = nt <= TOUCH_SM;
-    if (in_smem) {
-        for (int t = lane; t < nt; t += 32) {
-            sh.tx[t] = gx[t];
-            sh.tq[t] = gq[t];
-        }
-        __syncwarp();
-    }
-    const int* tx = in_smem ? sh.tx : gx;
-    const unsigned long long* tq = in_smem ? sh.tq : gq;
-    const float2 q32 = A.xy32[cur];
+    // equal cities merged by their summed weights in a hash: the shared-memory one (empty
+    // between uses) for up to BHASH_MAX entries, else the ant's global one (capacity 2m, which
+    // every list fits); each slot is evaluated once and emptied
+    const bool small = nt <= BHASH_MAX;
+    int* keys = small ? sh.hkey : A.ghk + (size_t)a * cap;
+    unsigned long long* qs = small ? sh.hq : A.ghq + (size_t)a * cap;
+    const int hcap = small ? BHASH : (int)cap;
     for (int t = lane; t < nt; t += 32) {
-        const int x = tx[t];
-        unsigned long long Qx = 0;
-        bool first = true;
-        for (int u = 0; u < nt; ++u)
-            if (tx[u] == x) {
-                Qx += tq[u];
-                first = first && u >= t;
+        const int x = gx[t];
+        const unsigned long long q = gq[t];
+        unsigned h = small ? bhash_slot(x) : (unsigned)(((unsigned long long)((unsigned)x * 2654435761u) * hcap) >> 32);
+        for (int pr = 0; pr < hcap; ++pr) {
+            const int old = atomicCAS(&keys[h], -1, x);
+            if (old == -1 || old == x) {
+                atomicAdd(&qs[h], q);
+                break;
             }
-        if (!first) continue;
+            h = h + 1 == (unsigned)hcap ? 0u : h + 1;
+        }
+    }
+    __syncwarp();
+    const float2 q32 = A.xy32[cur];
+    for (int s0 = 0; s0 < hcap; s0 += 32) {
+        const int slot = s0 + lane;
+        const int x = slot < hcap ? *reinterpret_cast<volatile int*>(&keys[slot]) : -1;
+        if (x < 0) continue;
+        const unsigned long long Qx = *reinterpret_cast<volatile unsigned long long*>(&qs[slot]);
+        keys[slot] = -1;
+        qs[slot] = 0ull;
         if (EXACT) {
             const double d2 = dist2(qx, qy, A.xy[2 * x], A.xy[2 * x + 1]);
             const double w = weight_of(A, tau0pow, Qx, d2);
@@ -351,6 +381,7 @@ __device__ void boosted_eval(const LbestArgs& A, int a, int cur, int nt, BoostSm
             top2_push(weight_f32(tauf, d2f, A.ia, A.ib), x, w1, x1, w2);
         }
     }
+    if (small && lane == 0) sh.hcount = 0;
     __syncwarp();
 }
 
@@ -627,13 +658,218 @@ __device__ int partial_choice_fast(const LbestArgs& A, int a, int cur, const uin
     return -1;
 }
 
+// Loads of one round (256 entries, 8 per lane) of the remaining-city list.
+__device__ __forceinline__ void load_remaining(const int* ul, const float2* uxy, int base, int ucount, int lane,
+                                               int (&id)[8], float2 (&p)[8]) {
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+        const int idx = base + 32 * h + lane;
+        id[h] = -1;
+        p[h] = make_float2(0.f, 0.f);
+        if (idx < ucount) {
+            id[h] = ul[idx];
+            p[h] = uxy[idx];
+        }
+    }
+}
+
+// Exhausted step of a partial rebuild, FP32-screened as partial_choice_fast, with the boosted
+// cities aggregated in a shared-memory hash:
+//  1. the non-candidate entries of the rank row of `cur` (held in registers) are listed in `el`
+//     (shared memory: the staging buffer, idle at an exhausted step), their neighbour ids and ant
+//     weights gathered eight per lane, and the unvisited cities inserted into the hash with the
+//     summed weights of their entries (shared-memory atomics on integers: the order of the
+//     insertions does not matter);
+//  2. the coordinates of the hashed cities are requested, and one pass over the remaining-city
+//     list (the next round's loads in flight) compacts it and keeps, per lane, the two nearest
+//     cities at tau0; a hashed city also counts there at tau0, which only underestimates it;
+//  3. the hashed cities are estimated with their tau.
+// Returns the city when the best estimate wins by more than the error bounds allow (the hash is
+// empty again); -1 when the estimates are too close (the hash is kept for hashed_exact); -2 when
+// the hash overflowed (emptied).
+__device__ int partial_choice_hashed(const LbestArgs& A, int a, int cur, const uint32_t* bits, int& ucount,
+                                     BoostSmem& sh, unsigned short* el, int lane, const RankRow& rr) {
+    int* ul = A.ulist + (size_t)a * A.ucap;
+    float2* uxy = A.uxy + (size_t)a * A.ucap;
+    const int* irow = A.nb + (size_t)cur * A.m * 2;
+    int id[8];
+    float2 p[8];
+    load_remaining(ul, uxy, 0, ucount, lane, id, p);  // in flight while the hash is built
+    const float2 q32 = A.xy32[cur];
+    // 1a. entry e of the rank row sits in lane (e % 512) / 16 at byte (e / 512) * 16 + e % 16;
+    //     bit 4 * word + byte of bm marks a non-candidate entry
+    unsigned long long bm = 0;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const uint32_t wv[4] = {rr.v[h].x, rr.v[h].y, rr.v[h].z, rr.v[h].w};
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const uint32_t m8 = __vcmpeq4(wv[g], 0xFFFFFFFFu) & 0x80808080u;
+            bm |= (unsigned long long)((m8 * 0x00204081u) >> 28) << (4 * (h * 4 + g));
+        }
+    }
+    int ne = 0;
+    int off = warp_offsets(__popcll(bm), ne, lane);
+    while (bm) {
+        const int b = __ffsll((long long)bm) - 1;
+        bm &= bm - 1;
+        const int word = b >> 2;
+        el[off++] = (unsigned short)((word >> 2) * 512 + lane * 16 + 4 * (word & 3) + (b & 3));
+    }
+    __syncwarp();
+    // 1b. gather and insert, 256 entries per round
+    bool over = false;
+    for (int t0 = 0; t0 < ne; t0 += 256) {
+        int x8[8];
+        unsigned long long q8[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const int t = t0 + 32 * h + lane;
+            const int e = t < ne ? (int)el[t] : -1;
+            x8[h] = e >= 0 ? __ldcs(irow + e) : -1;
+            q8[h] = e >= 0 ? __ldg(A.q + (e >> 1)) : 0ull;
+        }
+        bool unv[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) unv[h] = x8[h] >= 0 && !is_visited(bits, x8[h]);
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            if (!unv[h]) continue;
+            unsigned hs = bhash_slot(x8[h]);
+            bool done = false;
+            for (int pr = 0; pr < BHASH && !done; ++pr) {
+                const int old = atomicCAS(&sh.hkey[hs], -1, x8[h]);
+                if (old == -1 || old == x8[h]) {
+                    atomicAdd(&sh.hq[hs], q8[h]);
+                    if (old == -1 && atomicAdd(&sh.hcount, 1) >= BHASH_MAX) over = true;
+                    done = true;
+                }
+                hs = (hs + 1) & (BHASH - 1);
+            }
+            if (!done) over = true;
+        }
+    }
+    __syncwarp();
+    const bool overflow = __any_sync(FULL, over);
+    // 2. coordinates of the hashed cities (four slots per lane) requested before the scan
+    int hx[BHASH / 32];
+    float2 hp[BHASH / 32];
+#pragma unroll
+    for (int s4 = 0; s4 < BHASH / 32; ++s4) {
+        hx[s4] = sh.hkey[lane + 32 * s4];
+        hp[s4] = hx[s4] >= 0 ? A.xy32[hx[s4]] : make_float2(0.f, 0.f);
+    }
+    if (overflow) {
+        bhash_clear(sh, lane);
+        return -2;
+    }
+    float w1 = -1.f, w2 = -1.f, dmin = FLT_MAX;
+    int x1 = 0x7fffffff;
+    float d1 = FLT_MAX, d2s = FLT_MAX;  // the two nearest cities at tau0
+    int y1 = 0x7fffffff;
+    int cnt = 0;
+    const unsigned ltm = (1u << lane) - 1u;
+    for (int base = 0; base < ucount; base += 256) {
+        int idn[8];
+        float2 pn[8];
+        load_remaining(ul, uxy, base + 256, ucount, lane, idn, pn);
+        bool kp[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) kp[h] = id[h] >= 0 && !is_visited(bits, id[h]);
+        unsigned bl[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) bl[h] = __ballot_sync(FULL, kp[h]);
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const int pos = cnt + __popc(bl[h] & ltm);
+            cnt += __popc(bl[h]);
+            if (kp[h] && pos != base + 32 * h + lane) {
+                ul[pos] = id[h];
+                uxy[pos] = p[h];
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const float dx = __fsub_rn(p[h].x, q32.x), dy = __fsub_rn(p[h].y, q32.y);
+            const float v = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+            const bool lt1 = kp[h] && (v < d1 || (v == d1 && id[h] < y1));
+            const bool lt2 = kp[h] && v < d2s;
+            d2s = lt1 ? d1 : (lt2 ? v : d2s);
+            y1 = lt1 ? id[h] : y1;
+            d1 = lt1 ? v : d1;
+        }
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            id[h] = idn[h];
+            p[h] = pn[h];
+        }
+    }
+    ucount = cnt;
+    // 3. the hashed cities with their tau
+#pragma unroll
+    for (int s4 = 0; s4 < BHASH / 32; ++s4) {
+        const int x = hx[s4];
+        if (x < 0) continue;
+        const float dx = __fsub_rn(hp[s4].x, q32.x), dy = __fsub_rn(hp[s4].y, q32.y);
+        const float d2f = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+        const unsigned long long Q = sh.hq[lane + 32 * s4];
+        const float tauf = __fadd_rn(A.tau0f, __fmul_rn(__ull2float_rn(Q), 0x1.0p-32f));
+        dmin = fminf(dmin, d2f);
+        top2_push(weight_f32(tauf, d2f, A.ia, A.ib), x, w1, x1, w2);
+    }
+    if (d1 < FLT_MAX) {
+        dmin = fminf(dmin, d1);
+        top2_push(__fmul_rn(A.tau0powf, weight_f32(1.f, d1, 0, A.ib)), y1, w1, x1, w2);
+        if (d2s < FLT_MAX) w2 = fmaxf(w2, __fmul_rn(A.tau0powf, weight_f32(1.f, d2s, 0, A.ib)));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const float ow1 = __shfl_xor_sync(FULL, w1, o), ow2 = __shfl_xor_sync(FULL, w2, o);
+        const int ox1 = __shfl_xor_sync(FULL, x1, o);
+        dmin = fminf(dmin, __shfl_xor_sync(FULL, dmin, o));
+        if (ow1 > w1 || (ow1 == w1 && ox1 < x1)) {
+            w2 = fmaxf(w1, ow2);
+            w1 = ow1;
+            x1 = ox1;
+        } else {
+            w2 = fmaxf(w2, ow1);
+        }
+    }
+    if (!(dmin >= 1e-30f) || !(w1 > 0.f) || !(w1 <= FLT_MAX)) return -1;
+    const float eps_d = __fdiv_rn(__fmul_rn(1.1f, d2_bound(dmin, A.coord_r)), dmin);
+    const float E = __fmul_rn(1.25f, __fadd_rn(__fmul_rn(0.5f * (float)A.ib + 0.5f, eps_d),
+                                               __fmul_rn((float)(A.ib + A.ia + 4), 0x1.0p-22f)));
+    if (!(E < 0.25f)) return -1;
+    if (__fmul_rn(w1, 1.f - E) > __fmul_rn(w2, 1.f + E)) {
+        bhash_clear(sh, lane);
+        return x1;
+    }
+    return -1;
+}
+
+// Exact FP64 weights of the hashed cities (after partial_choice_hashed returned -1), then the
+// hash is emptied.
+__device__ void hashed_exact(const LbestArgs& A, BoostSmem& sh, int lane, double qx, double qy, double tau0pow,
+                             double& bw, int& bc) {
+#pragma unroll
+    for (int s4 = 0; s4 < BHASH / 32; ++s4) {
+        const int x = sh.hkey[lane + 32 * s4];
+        if (x < 0) continue;
+        const double d2 = dist2(qx, qy, A.xy[2 * x], A.xy[2 * x + 1]);
+        const double w = weight_of(A, tau0pow, sh.hq[lane + 32 * s4], d2);
+        if (better(w, x, bw, bc)) { bw = w; bc = x; }
+    }
+    bhash_clear(sh, lane);
+}
+
 // Exhausted-list rule.  Returns the chosen city (uniform across the warp).
 __device__ int exhausted_choice(const LbestArgs& A, int a, int cur, double u, bool partial, int& ucount,
-                                const uint32_t* bits, BoostSmem& sh, int lane) {
+                                const uint32_t* bits, BoostSmem& sh, unsigned short* el, int lane) {
     __syncwarp();  // the previous city's visited bit (set at the top of the step) is visible
     const double qx = A.xy[2 * cur], qy = A.xy[2 * cur + 1];
     const double tau0pow = powr(A.tau0, A.alpha);
-    int choice;
+    int choice = -1;
+    bool decided = false;
     if (A.fallback == 0) {
         double bw = -1.0;
         int bc = 0x7fffffff;
@@ -641,17 +877,27 @@ __device__ int exhausted_choice(const LbestArgs& A, int a, int cur, double u, bo
         RankRow rr;
         const bool pre = A.initialized && (A.m & 7) == 0 && A.m <= 1024;
         if (pre) load_rank_row(A, cur, lane, rr);
-        if (partial && A.ia >= 0 && A.ib >= 0) {
+        if (partial && A.ia >= 0 && A.ib >= 0 && pre && el) {
+            const int fast = partial_choice_hashed(A, a, cur, bits, ucount, sh, el, lane, rr);
+            if (fast >= 0) return fast;
+            if (fast == -1) {  // near tie: exact weights of the near-nearest and of the hashed cities
+                remaining_argmax(A, a, cur, bits, ucount, lane, qx, qy, tau0pow, bw, bc);
+                hashed_exact(A, sh, lane, qx, qy, tau0pow, bw, bc);
+                decided = true;
+            }
+        } else if (partial && A.ia >= 0 && A.ib >= 0) {
             const int fast = partial_choice_fast(A, a, cur, bits, ucount, sh, lane, pre ? &rr : nullptr);
             if (fast >= 0) return fast;
         }
-        if (partial) remaining_argmax(A, a, cur, bits, ucount, lane, qx, qy, tau0pow, bw, bc);
-        else nearest_unvisited(A, cur, bits, lane, qx, qy, tau0pow, bw, bc);
-        if (A.initialized) {
-            const int nt = collect_boosted(A, a, cur, bits, lane, pre ? &rr : nullptr);
-            float f1 = -1.f, f2 = -1.f, fd = FLT_MAX;
-            int fx = 0;
-            boosted_eval<true>(A, a, cur, nt, sh, lane, qx, qy, tau0pow, bw, bc, f1, fx, f2, fd);
+        if (!decided) {
+            if (partial) remaining_argmax(A, a, cur, bits, ucount, lane, qx, qy, tau0pow, bw, bc);
+            else nearest_unvisited(A, cur, bits, lane, qx, qy, tau0pow, bw, bc);
+            if (A.initialized) {
+                const int nt = collect_boosted(A, a, cur, bits, lane, pre ? &rr : nullptr);
+                float f1 = -1.f, f2 = -1.f, fd = FLT_MAX;
+                int fx = 0;
+                boosted_eval<true>(A, a, cur, nt, sh, lane, qx, qy, tau0pow, bw, bc, f1, fx, f2, fd);
+            }
         }
         warp_argmax(bw, bc);
         choice = bc;
@@ -719,6 +965,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) construct_lbest_kernel(const
     uint32_t* bits = reinterpret_cast<uint32_t*>(my_smem + bits_offset(A.k));
     const int n = A.n, k = A.k;
     const int W = (n + 31) >> 5;
+    bhash_clear(boost, lane);
     bool partial = false;
     if (A.initialized) {
         partial = true;
@@ -848,7 +1095,9 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) construct_lbest_kernel(const
             rowp = staged ? &stage[wb][pick][0] : A.candw + (size_t)j * k;
         } else {
             ++nfall;
-            j = exhausted_choice(A, a, cur, __shfl_sync(FULL, my_u, t & 31), partial, ucount, bits, boost, lane);
+            // no copies were issued this step (every candidate is visited): the staging buffer is free
+            j = exhausted_choice(A, a, cur, __shfl_sync(FULL, my_u, t & 31), partial, ucount, bits, boost,
+                                 staged ? reinterpret_cast<unsigned short*>(stage) : nullptr, lane);
             rowp = A.candw + (size_t)j * k;
         }
         wb ^= 1;
@@ -911,7 +1160,7 @@ void fill_lbest_args(const aco_instance* inst, int32_t iteration, LbestArgs& A) 
     A.cell_start = inst->cell_start; A.cell_city = inst->cell_city; A.cell_xy = inst->cell_xy; A.candw = inst->candw;
     A.W64 = inst->W64; A.lbest = inst->lbest; A.nb = inst->nb; A.nbrank = inst->nbrank;
     A.q = inst->q; A.cfix = inst->cfix;
-    A.seg = inst->seg; A.antit = inst->antit; A.accq = inst->accq; A.bel = inst->bel; A.btx = inst->btx; A.btq = inst->btq; A.ulist = inst->ulist; A.uxy = inst->uxy;
+    A.seg = inst->seg; A.antit = inst->antit; A.accq = inst->accq; A.bel = inst->bel; A.btx = inst->btx; A.btq = inst->btq; A.ghk = inst->ghk; A.ghq = inst->ghq; A.ulist = inst->ulist; A.uxy = inst->uxy;
     A.counters = inst->counters; A.errflag = inst->errflag;
 }
 
