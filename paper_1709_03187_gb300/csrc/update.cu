@@ -156,27 +156,85 @@ __global__ void __launch_bounds__(256) rebuild_kernel(const __grid_constant__ Re
     const int i0 = BATCH ? bm.y + w : blockIdx.x * warps + w;
     const int iend = BATCH ? bm.z : n;
     const int istep = BATCH ? warps : gridDim.x * warps;
+    // m <= 1024, m % 8 == 0: lane l always holds the ranks of ants hb * 256 + 8 l .. + 7
+    // (hb < 4), so their weights stay in registers for every city of the warp
+    const bool regq = use_ants && vec && m <= 1024;
+    unsigned long long qr[4][8];
+    if (regq) {
+#pragma unroll
+        for (int hb = 0; hb < 4; ++hb)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int a = hb * 256 + lane * 8 + j;
+                qr[hb][j] = a < m ? qs[a] : 0ull;
+            }
+    }
+    uint4 nxt[4];  // rank bytes of the warp's next city (fast path), requested one city ahead
+    if (regq && i0 < iend) {
+        const uint8_t* row = R.nbrank + (size_t)i0 * m * 2;
+#pragma unroll
+        for (int hb = 0; hb < 4; ++hb) {
+            const int a0 = hb * 256 + lane * 8;
+            nxt[hb] = a0 < m ? __ldcs(reinterpret_cast<const uint4*>(row + 2 * (size_t)a0)) : make_uint4(~0u, ~0u, ~0u, ~0u);
+        }
+    }
     for (int i = i0; i < iend; i += istep) {
         unsigned long long Q = 0;
         if (use_ants) {
             for (int r = 0; r < k; ++r) hist[r * 32 + lane] = 0ull;
             const uint8_t* row = R.nbrank + (size_t)i * m * 2;
-            if (vec) {
-                for (int base = 0; base < m; base += 256) {
-                    const int a0 = base + lane * 8;
-                    if (a0 < m) {
-                        const uint4 v = __ldcs(reinterpret_cast<const uint4*>(row + 2 * (size_t)a0));
-                        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+            if (regq) {
+                uint4 v[4];
+#pragma unroll
+                for (int hb = 0; hb < 4; ++hb) v[hb] = nxt[hb];
+                if (i + istep < iend) {
+                    const uint8_t* nrow = R.nbrank + (size_t)(i + istep) * m * 2;
+#pragma unroll
+                    for (int hb = 0; hb < 4; ++hb) {
+                        const int a0 = hb * 256 + lane * 8;
+                        nxt[hb] = a0 < m ? __ldcs(reinterpret_cast<const uint4*>(nrow + 2 * (size_t)a0))
+                                         : make_uint4(~0u, ~0u, ~0u, ~0u);
+                    }
+                }
+                unsigned long long* hl = hist + lane;
+#pragma unroll
+                for (int hb = 0; hb < 4; ++hb) {
+                    const uint32_t wv[4] = {v[hb].x, v[hb].y, v[hb].z, v[hb].w};
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const uint32_t r = (wv[h] >> (8 * b)) & 0xFFu;
+                            if (r < (uint32_t)k) atomicAdd(hl + r * 32, qr[hb][2 * h + (b >> 1)]);
+                        }
+                    }
+                }
+            } else if (vec) {
+                // the row's rank bytes, four 16-byte loads per lane in flight; each entry is one
+                // shared-memory reduction (no returned value, so the adds do not wait on each other)
+                for (int base = 0; base < m; base += 1024) {
+                    uint4 v[4];
+#pragma unroll
+                    for (int hb = 0; hb < 4; ++hb) {
+                        const int a0 = base + hb * 256 + lane * 8;
+                        v[hb] = a0 < m ? __ldcs(reinterpret_cast<const uint4*>(row + 2 * (size_t)a0))
+                                       : make_uint4(~0u, ~0u, ~0u, ~0u);
+                    }
+#pragma unroll
+                    for (int hb = 0; hb < 4; ++hb) {
+                        const int a0 = base + hb * 256 + lane * 8;
+                        const uint32_t wv[4] = {v[hb].x, v[hb].y, v[hb].z, v[hb].w};
 #pragma unroll
                         for (int h = 0; h < 4; ++h) {
 #pragma unroll
                             for (int g = 0; g < 2; ++g) {
-                                const int a = a0 + 2 * h + g;
                                 const uint32_t pair = wv[h] >> (16 * g);
                                 const uint32_t rs = pair & 0xFFu, rp = (pair >> 8) & 0xFFu;
-                                const unsigned long long qa = qs[a];
-                                if (rs < (uint32_t)k) hist[rs * 32 + lane] += qa;
-                                if (rp < (uint32_t)k) hist[rp * 32 + lane] += qa;
+                                if (rs < (uint32_t)k || rp < (uint32_t)k) {
+                                    const unsigned long long qa = qs[a0 + 2 * h + g];
+                                    if (rs < (uint32_t)k) atomicAdd(&hist[rs * 32 + lane], qa);
+                                    if (rp < (uint32_t)k) atomicAdd(&hist[rp * 32 + lane], qa);
+                                }
                             }
                         }
                     }
@@ -185,8 +243,8 @@ __global__ void __launch_bounds__(256) rebuild_kernel(const __grid_constant__ Re
                 for (int a = lane; a < m; a += 32) {
                     const uint32_t rs = row[2 * a], rp = row[2 * a + 1];
                     const unsigned long long qa = qs[a];
-                    if (rs < (uint32_t)k) hist[rs * 32 + lane] += qa;
-                    if (rp < (uint32_t)k) hist[rp * 32 + lane] += qa;
+                    if (rs < (uint32_t)k) atomicAdd(&hist[rs * 32 + lane], qa);
+                    if (rp < (uint32_t)k) atomicAdd(&hist[rp * 32 + lane], qa);
                 }
             }
             __syncwarp();
