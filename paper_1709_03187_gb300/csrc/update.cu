@@ -205,13 +205,12 @@ __global__ void __launch_bounds__(256) rebuild_kernel(const __grid_constant__ Re
 #pragma unroll
                         for (int b = 0; b < 4; ++b) {
                             const uint32_t r = (wv[h] >> (8 * b)) & 0xFFu;
-                            if (r < (uint32_t)k) atomicAdd(hl + r * 32, qr[hb][2 * h + (b >> 1)]);
+                            if (r < (uint32_t)k) hl[r * 32] += qr[hb][2 * h + (b >> 1)];
                         }
                     }
                 }
             } else if (vec) {
-                // the row's rank bytes, four 16-byte loads per lane in flight; each entry is one
-                // shared-memory reduction (no returned value, so the adds do not wait on each other)
+                // the row's rank bytes, four 16-byte loads per lane in flight
                 for (int base = 0; base < m; base += 1024) {
                     uint4 v[4];
 #pragma unroll
@@ -232,8 +231,8 @@ __global__ void __launch_bounds__(256) rebuild_kernel(const __grid_constant__ Re
                                 const uint32_t rs = pair & 0xFFu, rp = (pair >> 8) & 0xFFu;
                                 if (rs < (uint32_t)k || rp < (uint32_t)k) {
                                     const unsigned long long qa = qs[a0 + 2 * h + g];
-                                    if (rs < (uint32_t)k) atomicAdd(&hist[rs * 32 + lane], qa);
-                                    if (rp < (uint32_t)k) atomicAdd(&hist[rp * 32 + lane], qa);
+                                    if (rs < (uint32_t)k) hist[rs * 32 + lane] += qa;
+                                    if (rp < (uint32_t)k) hist[rp * 32 + lane] += qa;
                                 }
                             }
                         }
@@ -243,15 +242,19 @@ __global__ void __launch_bounds__(256) rebuild_kernel(const __grid_constant__ Re
                 for (int a = lane; a < m; a += 32) {
                     const uint32_t rs = row[2 * a], rp = row[2 * a + 1];
                     const unsigned long long qa = qs[a];
-                    if (rs < (uint32_t)k) atomicAdd(&hist[rs * 32 + lane], qa);
-                    if (rp < (uint32_t)k) atomicAdd(&hist[rp * 32 + lane], qa);
+                    if (rs < (uint32_t)k) hist[rs * 32 + lane] += qa;
+                    if (rp < (uint32_t)k) hist[rp * 32 + lane] += qa;
                 }
             }
             __syncwarp();
             if (lane < k) {
+                // lane r sums the 32 columns of rank r starting at column r (conflict-free banks),
+                // in four independent integer chains
                 const unsigned long long* h = hist + lane * 32;
-#pragma unroll 8
-                for (int l = 0; l < 32; ++l) Q += h[l];
+                unsigned long long q4[4] = {0ull, 0ull, 0ull, 0ull};
+#pragma unroll
+                for (int l = 0; l < 32; ++l) q4[l & 3] += h[(l + lane) & 31];
+                Q = (q4[0] + q4[1]) + (q4[2] + q4[3]);
             }
             __syncwarp();
         }
