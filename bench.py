@@ -58,6 +58,25 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def replica_seed(seed: int, rank: int) -> int:
+    """Rank r runs its own colony, seeded seed + r: replicas, with no exchange between ranks."""
+    return int(seed) + int(rank)
+
+
+def aggregate_over_ranks(t_step: float, units: float, world: int, device="cpu"):
+    """Whole-job figures: the slowest rank's timed seconds and the units all ranks processed."""
+    if world == 1:
+        return float(t_step), float(units)
+    import torch
+    import torch.distributed as dist
+
+    tt = torch.tensor([float(t_step)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    uu = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(uu.item())
+
+
 def read_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -158,7 +177,7 @@ def run_ours(args):
     params = dict(wl["params"])
     if args.ants:
         params["m"] = args.ants
-    params["seed"] = int(params["seed"]) + rank
+    params["seed"] = replica_seed(params["seed"], rank)
     n, m, k = params["n"], params["m"], params["k"]
     xy = aco_synth.make(args.workload)
     stream = torch.cuda.Stream()
@@ -202,14 +221,7 @@ def run_ours(args):
     t_upd = sum(b.elapsed_time(c) for _, b, c in evs) / 1e3
     t_step = t_con + t_upd
     decisions = st_after["decisions"] - st_before["decisions"]
-    if world > 1:
-        tt = torch.tensor([t_step], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dd = torch.tensor([decisions], dtype=torch.float64, device="cuda")
-        dist.all_reduce(dd, op=dist.ReduceOp.SUM)
-        t_max, dec_all = float(tt.item()), float(dd.item())
-    else:
-        t_max, dec_all = t_step, float(decisions)
+    t_max, dec_all = aggregate_over_ranks(t_step, decisions, world, "cuda")
     value = dec_all / t_max
     its = args.steps * world / t_max
 

@@ -59,7 +59,13 @@ typedef struct aco_params {
     uint64_t seed;        /* Philox4x32-10 key                                               */
     int32_t fallback;     /* exhausted list: 0 = argmax tau^a eta^b over unvisited (ties to the
                              lowest index), 1 = Eq. 1 over all unvisited                    */
-    int32_t reserved;     /* must be 0                                                       */
+    int32_t selection;    /* decision rule on the candidate list (LBEST only; DENSE needs 0):
+                             0 = the Eq. 1 random proportional wheel;
+                             1 = Independent Roulette (Section 3): argmax over unvisited
+                             candidates with positive weight of tau^a eta^b * u_r, ties to the
+                             lowest rank, u_r = (x + 1/2) 2^-32 from word r % 4 of the Philox
+                             draw with counter (8 t + r / 4, ant, iteration, 4) at decision t;
+                             no such candidate: the exhausted-list rule (fallback)           */
 } aco_params;
 
 /* Counters accumulated since creation (aco_get_stats). */

@@ -32,7 +32,7 @@ class Params(ctypes.Structure):
         ("mode", ctypes.c_int32), ("n", ctypes.c_int32), ("m", ctypes.c_int32), ("k", ctypes.c_int32),
         ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("rho", ctypes.c_double),
         ("tau0", ctypes.c_double), ("max_mod_frac", ctypes.c_double), ("p_partial", ctypes.c_double),
-        ("seed", ctypes.c_uint64), ("fallback", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("seed", ctypes.c_uint64), ("fallback", ctypes.c_int32), ("selection", ctypes.c_int32),
     ]
 
 
@@ -95,6 +95,8 @@ def lib():
             "or_knn_sweep": (ctypes.c_int, [ctypes.c_int, f64p, ctypes.c_int, i32p]),
             "or_create_with_cand": (P, [ctypes.POINTER(Params), f64p, i32p]),
             "or_set_edge_scores": (None, [P, ctypes.c_void_p]),
+            "or_ir_pick": (ctypes.c_int, [f64p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                          ctypes.c_uint32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -117,6 +119,12 @@ def u53(x0: int, x1: int) -> float:
 
 def bounded(x: int, r: int) -> int:
     return lib().or_bounded(x, r)
+
+
+def ir_pick(w, seed: int, t: int, ant: int, iteration: int) -> int:
+    """Independent Roulette over one candidate row of weights (rank order): the rank picked, or -1."""
+    w = np.ascontiguousarray(w, np.float64)
+    return int(lib().or_ir_pick(w, w.size, seed, t, ant, iteration))
 
 
 def powr(x: float, e: float) -> float:
@@ -176,10 +184,10 @@ class Oracle:
 
     def __init__(self, xy: np.ndarray, *, mode: int, n: int, m: int, k: int = 0, alpha: float = 1.0,
                  beta: float = 2.0, rho: float = 0.5, tau0: float = 1.0, max_mod_frac: float = 1.0,
-                 p_partial: float = 1.0, seed: int = 1, fallback: int = 0, cand=None):
+                 p_partial: float = 1.0, seed: int = 1, fallback: int = 0, selection: int = 0, cand=None):
         self.xy = np.ascontiguousarray(xy, np.float64)
         assert self.xy.shape == (n, 2)
-        self.p = Params(mode, n, m, k, alpha, beta, rho, tau0, max_mod_frac, p_partial, seed, fallback, 0)
+        self.p = Params(mode, n, m, k, alpha, beta, rho, tau0, max_mod_frac, p_partial, seed, fallback, selection)
         self.n, self.m, self.k, self.mode = n, m, k, mode
         if cand is not None:
             self._h = lib().or_create_with_cand(ctypes.byref(self.p), self.xy, np.ascontiguousarray(cand, np.int32))

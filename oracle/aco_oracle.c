@@ -40,7 +40,8 @@
  *     iteration); commits happen after every ant has built its tour.
  *   Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key = seed
  *     (low, high word), counter = (index, ant, iteration, purpose); purpose 0 = wheel draw of
- *     decision `index`, 1 = start city / start position, 2 = preserved count, 3 = partial coin.
+ *     decision `index`, 1 = start city / start position, 2 = preserved count, 3 = partial coin,
+ *     4 = Independent Roulette draws of decision t (counter index 8 t + r / 4 for rank r).
  *     u = ((x0 << 32 | x1) >> 11) * 2^-53; an integer in [0, r) is (x0 * r) >> 32.
  *   Integer exponents a, b in [0, 64] use repeated multiplication x*x*...*x (left to right);
  *   other exponents call pow().
@@ -169,7 +170,7 @@ typedef struct {
     double max_mod_frac, p_partial;
     uint64_t seed;
     int32_t fallback; /* 0 = argmax over unvisited, 1 = Eq. 1 wheel over unvisited */
-    int32_t reserved;
+    int32_t selection; /* 0 = Eq. 1 wheel, 1 = Independent Roulette (candidate lists) */
 } or_params;
 
 typedef struct {
@@ -327,6 +328,24 @@ static int wheel(const double* w, int cnt, double u) {
 }
 
 /* One decision of ant `ant` at city i (candidate mode). */
+/* Independent Roulette (Section 3): each candidate draws its own uniform and the largest
+ * weight x uniform wins.  Among ranks with w[r] > 0, argmax of w[r] * u_r, ties to the lowest
+ * rank; u_r = (x + 1/2) 2^-32 with x word r % 4 of the draw (8 t + r / 4, ant, iteration, 4).
+ * Returns -1 when no weight is positive (the caller then applies the exhausted-list rule). */
+int or_ir_pick(const double* w, int k, uint64_t seed, uint32_t t, uint32_t ant, uint32_t iteration) {
+    int best = -1;
+    double bp = 0.0;
+    for (int r = 0; r < k; ++r) {
+        if (!(w[r] > 0.0)) continue;
+        uint32_t x[4];
+        draw(seed, 8u * t + (uint32_t)(r / 4), ant, iteration, 4, x);
+        double u = ((double)x[r % 4] + 0.5) * 0x1.0p-32;
+        double prod = w[r] * u;
+        if (prod > bp) { bp = prod; best = r; }
+    }
+    return best;
+}
+
 static int decide_cand(or_state* st, int ant, int i, uint32_t t, uint32_t iteration) {
     const or_params* p = &st->p;
     int n = p->n, k = p->k;
@@ -342,7 +361,7 @@ static int decide_cand(or_state* st, int ant, int i, uint32_t t, uint32_t iterat
         double tau = tau_from_Q(st, st->Q[(size_t)i * k + r]);
         w[r] = or_powr(tau, p->alpha) * st->etab[(size_t)i * k + r];
     }
-    int r = wheel(w, k, u);
+    int r = p->selection == 1 ? or_ir_pick(w, k, p->seed, t, (uint32_t)ant, iteration) : wheel(w, k, u);
     if (r >= 0) return row[r];
     /* every candidate visited */
     st->fallbacks++;

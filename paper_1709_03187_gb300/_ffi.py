@@ -29,7 +29,7 @@ class Params(ctypes.Structure):
         ("mode", ctypes.c_int32), ("n", ctypes.c_int32), ("m", ctypes.c_int32), ("k", ctypes.c_int32),
         ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("rho", ctypes.c_double), ("tau0", ctypes.c_double),
         ("max_mod_frac", ctypes.c_double), ("p_partial", ctypes.c_double), ("seed", ctypes.c_uint64),
-        ("fallback", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("fallback", ctypes.c_int32), ("selection", ctypes.c_int32),
     ]
 
 

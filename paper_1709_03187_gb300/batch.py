@@ -16,13 +16,13 @@ class Batch:
 
     def __init__(self, xys, *, m: int, k: int, alpha: float = 1.0, beta: float = 2.0, tau0: float = 1.0,
                  max_mod_frac: float = 1.0, p_partial: float = 1.0, seed: int = 1, fallback: int = 0,
-                 stream: torch.cuda.Stream | None = None):
+                 selection: int = 0, stream: torch.cuda.Stream | None = None):
         self.ns = np.array([x.shape[0] for x in xys], np.int32)
         self.ms = np.minimum(self.ns, m)
         self.count = len(xys)
         self.xy = torch.from_numpy(np.ascontiguousarray(np.concatenate(xys, 0), np.float64)).cuda()
         self.params = make_params(1, int(self.ns.max()), m, k, alpha, beta, 0.0, tau0, max_mod_frac, p_partial, seed,
-                                  fallback)
+                                  fallback, selection)
         self.stream = stream
         self._h = _ffi.aco_batch_create(self.xy, self.ns, self.params, stream)
 

@@ -9,8 +9,8 @@ from ._ffi import ACO_MODE_DENSE, ACO_MODE_LBEST_PARTIAL, Params
 
 def make_params(mode: int, n: int, m: int, k: int = 0, alpha: float = 1.0, beta: float = 2.0, rho: float = 0.1,
                 tau0: float = 1.0, max_mod_frac: float = 1.0, p_partial: float = 1.0, seed: int = 1,
-                fallback: int = 0) -> Params:
-    return Params(mode, n, m, k, alpha, beta, rho, tau0, max_mod_frac, p_partial, seed, fallback, 0)
+                fallback: int = 0, selection: int = 0) -> Params:
+    return Params(mode, n, m, k, alpha, beta, rho, tau0, max_mod_frac, p_partial, seed, fallback, selection)
 
 
 class Colony:
@@ -21,11 +21,13 @@ class Colony:
 
     def __init__(self, xy, *, mode: int, n: int, m: int, k: int = 0, alpha: float = 1.0, beta: float = 2.0,
                  rho: float = 0.1, tau0: float = 1.0, max_mod_frac: float = 1.0, p_partial: float = 1.0,
-                 seed: int = 1, fallback: int = 0, stream: torch.cuda.Stream | None = None, device=None):
+                 seed: int = 1, fallback: int = 0, selection: int = 0, stream: torch.cuda.Stream | None = None,
+                 device=None):
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.xy = torch.as_tensor(xy, dtype=torch.float64).to(self.device).contiguous()
         assert self.xy.shape == (n, 2)
-        self.params = make_params(mode, n, m, k, alpha, beta, rho, tau0, max_mod_frac, p_partial, seed, fallback)
+        self.params = make_params(mode, n, m, k, alpha, beta, rho, tau0, max_mod_frac, p_partial, seed, fallback,
+                                  selection)
         self.n, self.m, self.k, self.mode = n, m, k, mode
         self.stream = stream
         self._h = None

@@ -75,7 +75,9 @@ static bool params_ok(const aco_params* p, char* why, size_t wn) {
         return snprintf(why, wn, "max_mod_frac in (0,1]"), false;
     if (!(p->p_partial >= 0 && p->p_partial <= 1)) return snprintf(why, wn, "p_partial in [0,1]"), false;
     if (p->fallback != 0 && p->fallback != 1) return snprintf(why, wn, "fallback must be 0 or 1"), false;
-    if (p->reserved != 0) return snprintf(why, wn, "reserved must be 0"), false;
+    if (p->selection != 0 && p->selection != 1) return snprintf(why, wn, "selection must be 0 or 1"), false;
+    if (p->mode == ACO_MODE_DENSE && p->selection != 0)
+        return snprintf(why, wn, "Independent Roulette needs candidate lists (LBEST mode)"), false;
     if (p->mode == ACO_MODE_DENSE && p->n > 8192) return snprintf(why, wn, "DENSE mode supports n <= 8192"), false;
     // the visited bitset of one ant lives in shared memory (<= 200 KB, beside ~6 KB of buffers)
     if ((long long)(p->n + 31) / 32 * 4 > 200 * 1024) return snprintf(why, wn, "n too large for the visited bitset"), false;

@@ -22,7 +22,7 @@
 typedef unsigned __int128 u128;
 
 // ------------------------------------------------------------------ random numbers
-enum : uint32_t { PURPOSE_WHEEL = 0, PURPOSE_START = 1, PURPOSE_KEEP = 2, PURPOSE_COIN = 3 };
+enum : uint32_t { PURPOSE_WHEEL = 0, PURPOSE_START = 1, PURPOSE_KEEP = 2, PURPOSE_COIN = 3, PURPOSE_IR = 4 };
 
 struct Draw4 { uint32_t x0, x1, x2, x3; };
 
