@@ -286,7 +286,8 @@ def run_ours(args):
 def run_e2e(args, xy, params, stream):
     """The same metric through the public API from host buffers: pinned coordinates copied in,
     candidate lists, initial tours and `steps` iterations, C_gbest read back every step and the
-    best tour read back at the end.  Decisions of the whole solve / wall time."""
+    best tour read back at the end.  Decisions of the `steps` iterations / wall time of the whole
+    solve (set-up time counted, set-up decisions not)."""
     import torch
 
     from paper_1709_03187_gb300 import Colony
@@ -300,9 +301,13 @@ def run_e2e(args, xy, params, stream):
     col = Colony(dev, stream=stream, **params)
     col.build_candidates()
     gb = []
+    dec0 = 0
     for it in range(args.steps + 1):
         col.iterate(it)
-        gb.append(col.stats()["gbest"])  # device -> host read of the step's result (8 B)
+        s_it = col.stats()  # device -> host read of the step's result (C_gbest, 8 B)
+        gb.append(s_it["gbest"])
+        if it == 0:
+            dec0 = s_it["decisions"]  # the initial tours are set-up, not steps of the metric
     st = col.stats()
     lb, cl, _ = col.state()
     best = lb[st["gbest_ant"]].cpu()
@@ -310,11 +315,12 @@ def run_e2e(args, xy, params, stream):
     wall = time.perf_counter() - t0
     col.close()
     del best
-    return {"value": round(st["decisions"] / wall, 1), "unit": "decisions/s",
+    return {"value": round((st["decisions"] - dec0) / wall, 1), "unit": "decisions/s",
             "h2d_bytes_per_step": round(host.numel() * 8 / (args.steps + 1), 1),
             "d2h_bytes_per_step": round(8 + 4 * params["n"] / (args.steps + 1), 1),
             "wall_s": round(wall, 3), "iterations": args.steps + 1,
-            "note": "includes instance creation, candidate lists and the initial tours"}
+            "note": "wall time includes instance creation, candidate lists and the initial tours; decisions "
+                    "are those of the timed iterations only"}
 
 
 def cpu_baseline_from_state(col, xy, params, iteration, sample):

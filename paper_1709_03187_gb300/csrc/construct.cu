@@ -35,6 +35,7 @@ struct LbestArgs {
     double alpha, beta, tau0, f, p_partial;
     unsigned long long seed;
     int fallback, iteration, initialized;
+    int selection;  // 0 = Eq. 1 wheel, 1 = Independent Roulette
     int ucap;       // capacity of the per-ant remaining-city list
     float coord_r;  // max |coordinate| (FP32 screen error bound)
     int ia, ib;     // alpha, beta as small integers (0..16) for the FP32 screen, else -1
@@ -1059,7 +1060,31 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) construct_lbest_kernel(const
         if (staged) cp_async_commit();
         const unsigned fmask = __ballot_sync(FULL, feas);
         int pick = -1;
-        if (fmask) {
+        if (fmask && A.selection == 1) {
+            // Independent Roulette: the candidate's exact weight times its own uniform; the
+            // largest positive product wins, ties to the lowest rank
+            double prod = 0.0;
+            if (feas) {
+                const double w64 = A.W64[(size_t)cur * k + lane];
+                if (w64 > 0.0) {
+                    const Draw4 d = aco_draw(A.seed, 8u * (uint32_t)t + (uint32_t)(lane >> 2), a, iteration, PURPOSE_IR);
+                    const uint32_t xr = (lane & 3) == 0 ? d.x0 : (lane & 3) == 1 ? d.x1 : (lane & 3) == 2 ? d.x2 : d.x3;
+                    prod = __dmul_rn(w64, __dmul_rn(__dadd_rn(__uint2double_rn(xr), 0.5), 0x1.0p-32));
+                }
+            }
+            double bp = prod;
+            int bl = prod > 0.0 ? lane : 32;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const double ob = __shfl_xor_sync(FULL, bp, o);
+                const int ol = __shfl_xor_sync(FULL, bl, o);
+                if (ob > bp || (ob == bp && ol < bl)) {
+                    bp = ob;
+                    bl = ol;
+                }
+            }
+            pick = bl < 32 ? bl : -1;
+        } else if (fmask) {
             float S = feas ? w : 0.f;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -1149,6 +1174,7 @@ void fill_lbest_args(const aco_instance* inst, int32_t iteration, LbestArgs& A) 
     A.n = p.n; A.m = p.m; A.k = p.k;
     A.alpha = p.alpha; A.beta = p.beta; A.tau0 = p.tau0; A.f = p.max_mod_frac; A.p_partial = p.p_partial;
     A.seed = p.seed; A.fallback = p.fallback; A.iteration = iteration; A.initialized = inst->initialized ? 1 : 0;
+    A.selection = p.selection;
     A.ucap = inst->ucap; A.coord_r = inst->coord_r;
     const bool ia_ok = p.alpha >= 0 && p.alpha <= 16 && floor(p.alpha) == p.alpha;
     const bool ib_ok = p.beta >= 0 && p.beta <= 16 && floor(p.beta) == p.beta;
