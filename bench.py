@@ -46,7 +46,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="lbest200k",
-                    choices=sorted(aco_synth.WORKLOADS) + ["batch512", "learned20k"])
+                    choices=sorted(aco_synth.WORKLOADS) + ["batch512", "learned20k", "schedule20k"])
     ap.add_argument("--ants", type=int, default=0, help="override m (profiling of smaller cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -563,8 +563,54 @@ def run_learned(args):
     print(json.dumps(out))
 
 
+# ------------------------------------------------------------------ modification schedule
+def run_schedule(args):
+    """The paper's proposed growing modification limit (Section 7) against a fixed one at
+    n = 20,000 (the learned20k instances), m = 512, k = 20: 100 iterations with f = 0.1 fixed,
+    and 100 iterations with f growing linearly from 0.01 to 0.1 over the first 50.  Per seed: the
+    CUDA-event time of the iterations and the final C_gbest."""
+    import torch
+
+    from paper_1709_03187_gb300 import Colony, linear_f_schedule
+
+    torch.cuda.set_device(0)
+    n, m, k, iters = 20_000, 512, 20, 100
+    rows = []
+    for s in (1, 2, 3):
+        xy = aco_synth.clustered(n, 100, 0.01, 20_000 + s)
+        res = {}
+        for name, sched in (("fixed", lambda t: 0.1), ("growing", linear_f_schedule(0.01, 0.1, 50))):
+            col = Colony(xy, mode=1, n=n, m=m, k=k, max_mod_frac=0.1, seed=s)
+            col.build_candidates()
+            col.iterate(0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for it in range(1, iters):
+                col.set_max_mod_frac(sched(it))
+                col.iterate(it)
+            e1.record()
+            torch.cuda.synchronize()
+            res[name] = (e0.elapsed_time(e1), col.stats()["gbest"])
+            col.close()
+        rows.append({"seed": s, "fixed_ms": round(res["fixed"][0], 1), "fixed_gbest": res["fixed"][1],
+                     "growing_ms": round(res["growing"][0], 1), "growing_gbest": res["growing"][1]})
+    out = {"metric": "C_gbest after 100 iterations and GPU time, growing vs fixed modification limit",
+           "workload": "schedule20k: n=20,000 clustered (100 clusters, sigma=0.01), k=20, m=512; f=0.1 fixed vs "
+                       "f from 0.01 to 0.1 over 50 iterations; 3 seeds",
+           "per_seed": rows,
+           "mean_fixed_gbest": float(np.mean([r["fixed_gbest"] for r in rows])),
+           "mean_growing_gbest": float(np.mean([r["growing_gbest"] for r in rows])),
+           "mean_fixed_ms": float(np.mean([r["fixed_ms"] for r in rows])),
+           "mean_growing_ms": float(np.mean([r["growing_ms"] for r in rows]))}
+    print(json.dumps(out))
+
+
 def main():
     args = parse_args()
+    if args.workload == "schedule20k" and args.impl == "ours":
+        run_schedule(args)
+        return
     if args.workload == "batch512" and args.impl == "ours":
         run_batch(args)
     elif args.workload == "learned20k" and args.impl == "ours":

@@ -148,6 +148,14 @@ aco_status aco_get_stats(aco_instance* inst, aco_stats* out_host);
 aco_status aco_step_probs(aco_instance* inst, int32_t city, const uint32_t* visited_bits_dev,
                           float* probs_out_dev, int32_t* exhausted_out_dev);
 
+/* Run-time schedule of the PartialACO parameters (Section 3.1; a growing f is the schedule the
+ * paper proposes as future work in Section 7): from the next aco_construct_tours on, at most
+ * floor(f n) cities are rebuilt, and an ant rebuilds partially with probability p_partial.
+ * 0 < f <= the max_mod_frac given at creation (the per-ant lists are sized for it), 0 <= p_partial
+ * <= 1; LBEST mode; not between construct and update (ACO_ERR_STATE).  Host-side only. */
+aco_status aco_set_max_mod_frac(aco_instance* inst, double f);
+aco_status aco_set_p_partial(aco_instance* inst, double p_partial);
+
 /* ------------------------------------------------------------------ batched colonies
  * Many independent instances of uneven size solved together: the same method and parameters
  * per instance (Section 3, Algorithm 1), with all of a batch's colonies advanced by single

@@ -95,6 +95,8 @@ def lib():
             "or_knn_sweep": (ctypes.c_int, [ctypes.c_int, f64p, ctypes.c_int, i32p]),
             "or_create_with_cand": (P, [ctypes.POINTER(Params), f64p, i32p]),
             "or_set_edge_scores": (None, [P, ctypes.c_void_p]),
+            "or_set_max_mod_frac": (None, [P, ctypes.c_double]),
+            "or_set_p_partial": (None, [P, ctypes.c_double]),
             "or_ir_pick": (ctypes.c_int, [f64p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                           ctypes.c_uint32]),
         }
@@ -291,6 +293,12 @@ class Oracle:
 
     def set_lbest(self, lbest: np.ndarray, clen: np.ndarray):
         lib().or_set_lbest(self._h, np.ascontiguousarray(lbest, np.int32), np.ascontiguousarray(clen, np.float64))
+
+    def set_max_mod_frac(self, f: float):
+        lib().or_set_max_mod_frac(self._h, f)
+
+    def set_p_partial(self, p: float):
+        lib().or_set_p_partial(self._h, p)
 
     def set_edge_scores(self, score):
         """Learned proposal: score[i, r] replaces eta^beta on candidate edge (i, cand[i, r]); None

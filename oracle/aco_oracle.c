@@ -545,6 +545,10 @@ void or_get_seg(const or_state* st, int32_t* s_out, int32_t* M_out) {
 void or_get_tau(const or_state* st, double* out) {
     memcpy(out, st->tau, sizeof(double) * (size_t)st->p.n * st->p.n);
 }
+/* Schedule of the PartialACO parameters between iterations (Section 3.1; Section 7's growing f). */
+void or_set_max_mod_frac(or_state* st, double f) { st->p.max_mod_frac = f; }
+void or_set_p_partial(or_state* st, double p) { st->p.p_partial = p; }
+
 void or_set_tau(or_state* st, const double* tau) {
     memcpy(st->tau, tau, sizeof(double) * (size_t)st->p.n * st->p.n);
 }

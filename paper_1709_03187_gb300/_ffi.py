@@ -88,6 +88,8 @@ def lib():
             "aco_edge_features": (S, [V, I32, V]),
             "aco_tour_labels": (S, [V, V]),
             "aco_set_edge_scores": (S, [V, V]),
+            "aco_set_max_mod_frac": (S, [V, ctypes.c_double]),
+            "aco_set_p_partial": (S, [V, ctypes.c_double]),
             "aco_status_string": (ctypes.c_char_p, [S]),
             "aco_last_error": (ctypes.c_char_p, [V]),
         }
@@ -299,3 +301,11 @@ def aco_tour_labels(h, target_dev):
 
 def aco_set_edge_scores(h, score_dev=None):
     _check(lib().aco_set_edge_scores(h, _ptr(score_dev)), "aco_set_edge_scores", h)
+
+
+def aco_set_max_mod_frac(h, f: float):
+    _check(lib().aco_set_max_mod_frac(h, f), "aco_set_max_mod_frac", h)
+
+
+def aco_set_p_partial(h, p_partial: float):
+    _check(lib().aco_set_p_partial(h, p_partial), "aco_set_p_partial", h)

@@ -13,6 +13,13 @@ def make_params(mode: int, n: int, m: int, k: int = 0, alpha: float = 1.0, beta:
     return Params(mode, n, m, k, alpha, beta, rho, tau0, max_mod_frac, p_partial, seed, fallback, selection)
 
 
+def linear_f_schedule(f0: float, f1: float, ramp: int):
+    """The growing modification limit of Section 7's proposal: f(t) = f0 + (f1 - f0) min(1, t / ramp)."""
+    def f(t: int) -> float:
+        return f0 + (f1 - f0) * min(1.0, t / ramp) if ramp > 0 else f1
+    return f
+
+
 class Colony:
     """One ACO colony on the current CUDA device.
 
@@ -62,6 +69,12 @@ class Colony:
 
     def update(self):
         _ffi.aco_update_pheromone(self._h)
+
+    def set_max_mod_frac(self, f: float):
+        _ffi.aco_set_max_mod_frac(self._h, f)
+
+    def set_p_partial(self, p_partial: float):
+        _ffi.aco_set_p_partial(self._h, p_partial)
 
     def iterate(self, iteration: int):
         _ffi.aco_construct_tours(self._h, iteration, None, None)

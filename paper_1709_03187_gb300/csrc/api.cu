@@ -149,6 +149,7 @@ extern "C" aco_status aco_create_instance(const double* xy_dev, const aco_params
         if (pmin < 1) pmin = 1;
         if (pmin > n - 1) pmin = n - 1;
         inst->ucap = (int32_t)(n - pmin);
+        inst->f_cap = p->max_mod_frac;
         ok &= dalloc(&inst->ulist, m * inst->ucap, &total);
         ok &= dalloc(&inst->uxy, m * inst->ucap, &total);
         ok &= dalloc(&inst->xy32, n, &total);
@@ -381,4 +382,23 @@ extern "C" aco_status aco_step_probs(aco_instance* inst, int32_t city, const uin
     if (city < 0 || city >= inst->p.n) return set_err(inst, ACO_ERR_INVALID_ARG, "city out of range");
     if (!inst->cand_built) return set_err(inst, ACO_ERR_STATE, "step_probs before build_candidates");
     return launch_step_probs(inst, city, visited_bits_dev, probs_out_dev, exhausted_out_dev);
+}
+
+extern "C" aco_status aco_set_max_mod_frac(aco_instance* inst, double f) {
+    if (!inst) return ACO_ERR_INVALID_ARG;
+    if (inst->p.mode != ACO_MODE_LBEST_PARTIAL) return set_err(inst, ACO_ERR_STATE, "set_max_mod_frac: LBEST mode only");
+    if (inst->constructed) return set_err(inst, ACO_ERR_STATE, "set_max_mod_frac: tours constructed, update pending");
+    if (!(f > 0.0 && f <= inst->f_cap))
+        return set_err(inst, ACO_ERR_INVALID_ARG, "set_max_mod_frac: f must be in (0, f at creation = %g]", inst->f_cap);
+    inst->p.max_mod_frac = f;
+    return ACO_OK;
+}
+
+extern "C" aco_status aco_set_p_partial(aco_instance* inst, double p_partial) {
+    if (!inst) return ACO_ERR_INVALID_ARG;
+    if (inst->p.mode != ACO_MODE_LBEST_PARTIAL) return set_err(inst, ACO_ERR_STATE, "set_p_partial: LBEST mode only");
+    if (inst->constructed) return set_err(inst, ACO_ERR_STATE, "set_p_partial: tours constructed, update pending");
+    if (!(p_partial >= 0.0 && p_partial <= 1.0)) return set_err(inst, ACO_ERR_INVALID_ARG, "set_p_partial: p in [0, 1]");
+    inst->p.p_partial = p_partial;
+    return ACO_OK;
 }

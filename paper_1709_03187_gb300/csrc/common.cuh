@@ -269,6 +269,7 @@ struct aco_instance {
     int32_t* ulist;        // m*ucap remaining discarded cities of each ant's partial rebuild
     float2* uxy;           // m*ucap their FP32 coordinates
     int32_t ucap;          // largest rebuilt count, n - max(1, n - floor(f n))
+    double f_cap;          // f at creation: the largest f the per-ant lists are sized for
     float coord_r;         // max |coordinate| (rounded up)
     int32_t* deg;          // n degree-in-best-tours scratch of the edge features
     bool scored;           // candidate edges carry learned scores instead of eta^beta

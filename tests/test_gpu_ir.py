@@ -49,3 +49,38 @@ def test_ir_differs_from_the_wheel_and_is_rejected_in_dense_mode():
     assert not np.array_equal(tours[0], tours[1])
     with pytest.raises(AcoError):
         Colony(aco_synth.uniform(50, 1), mode=0, n=50, m=4, selection=1)
+
+
+def test_f_schedule_and_p_partial_match_oracle():
+    """F3: the modification limit grows between iterations (and p_partial changes) exactly as
+    in the oracle."""
+    require_gpu()
+    from paper_1709_03187_gb300 import AcoError, Colony, linear_f_schedule
+
+    n, m, k = 900, 16, 12
+    xy = aco_synth.clustered(n, 9, 0.02, 21)
+    kw = dict(mode=1, n=n, m=m, k=k, max_mod_frac=0.4, seed=8)
+    col = Colony(xy, **kw)
+    cand = col.build_candidates(return_lists=True).cpu().numpy()
+    ref = oracle.Oracle(xy, cand=cand, **kw)
+    sched = linear_f_schedule(0.01, 0.4, 5)
+    for it in range(8):
+        col.set_max_mod_frac(sched(it))
+        ref.set_max_mod_frac(sched(it))
+        if it == 6:
+            col.set_p_partial(0.5)
+            ref.set_p_partial(0.5)
+        col.iterate(it)
+        ref.iterate(it)
+        lb, cl, _ = col.state()
+        assert np.array_equal(lb.cpu().numpy(), ref.lbest), f"iteration {it}"
+        assert np.array_equal(cl.cpu().numpy(), ref.clen)
+    with pytest.raises(AcoError) as e:
+        col.set_max_mod_frac(0.41)  # above the creation value
+    assert e.value.status == 1
+    col.construct(8)
+    with pytest.raises(AcoError) as e:
+        col.set_max_mod_frac(0.1)  # between construct and update
+    assert e.value.status == 4
+    col.update()
+    col.close()

@@ -54,3 +54,31 @@ def test_ir_colony_finds_the_optimum_of_small_instances():
         assert col.clen.min() <= best * (1 + 1e-12)
         for t in col.lbest:
             assert sorted(t) == list(range(8))
+
+
+def test_oracle_f_schedule_bounds_and_reduction():
+    """F3: a growing f rebuilds at most floor(f(t) n) cities at iteration t; a constant schedule
+    equals the fixed-f run."""
+    from paper_1709_03187_gb300.colony import linear_f_schedule
+
+    xy = aco_synth.clustered(400, 6, 0.03, 3)
+    sched = linear_f_schedule(0.02, 0.3, 6)
+    col = oracle.Oracle(xy, mode=1, n=400, m=10, k=8, max_mod_frac=0.3, seed=4)
+    fixed = oracle.Oracle(xy, mode=1, n=400, m=10, k=8, max_mod_frac=0.3, seed=4)
+    same = oracle.Oracle(xy, mode=1, n=400, m=10, k=8, max_mod_frac=0.3, seed=4)
+    for it in range(8):
+        col.set_max_mod_frac(sched(it))
+        same.set_max_mod_frac(0.3)
+        col.iterate(it)
+        fixed.iterate(it)
+        same.iterate(it)
+        if it > 0:
+            _, M = col.segments()
+            assert np.all(M <= math.floor(sched(it) * 400))
+    assert np.array_equal(same.lbest, fixed.lbest)
+    assert not np.array_equal(col.lbest, fixed.lbest)
+    # p_partial = 0: every ant builds a full tour
+    col.set_p_partial(0.0)
+    col.iterate(8)
+    s, M = col.segments()
+    assert np.all(s < 0)
