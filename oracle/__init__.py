@@ -96,6 +96,9 @@ def lib():
             "or_create_with_cand": (P, [ctypes.POINTER(Params), f64p, i32p]),
             "or_set_edge_scores": (None, [P, ctypes.c_void_p]),
             "or_set_max_mod_frac": (None, [P, ctypes.c_double]),
+            "or_set_local_search": (None, [P, ctypes.c_double, ctypes.c_int]),
+            "or_ls_moves": (ctypes.c_int64, [P]),
+            "or_two_opt_windowed": (ctypes.c_int, [ctypes.c_int, f64p, i32p, ctypes.c_int, ctypes.c_int]),
             "or_set_p_partial": (None, [P, ctypes.c_double]),
             "or_ir_pick": (ctypes.c_int, [f64p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                           ctypes.c_uint32]),
@@ -127,6 +130,13 @@ def ir_pick(w, seed: int, t: int, ant: int, iteration: int) -> int:
     """Independent Roulette over one candidate row of weights (rank order): the rank picked, or -1."""
     w = np.ascontiguousarray(w, np.float64)
     return int(lib().or_ir_pick(w, w.size, seed, t, ant, iteration))
+
+
+def two_opt_windowed(xy: np.ndarray, tour: np.ndarray, window: int, max_passes: int = 16):
+    """Windowed 2-opt of one tour (returns (improved tour, moves))."""
+    t = np.ascontiguousarray(tour, np.int32).copy()
+    mv = lib().or_two_opt_windowed(t.size, np.ascontiguousarray(xy, np.float64), t, window, max_passes)
+    return t, int(mv)
 
 
 def powr(x: float, e: float) -> float:
@@ -293,6 +303,13 @@ class Oracle:
 
     def set_lbest(self, lbest: np.ndarray, clen: np.ndarray):
         lib().or_set_lbest(self._h, np.ascontiguousarray(lbest, np.int32), np.ascontiguousarray(clen, np.float64))
+
+    def set_local_search(self, p: float, window: int = 500):
+        lib().or_set_local_search(self._h, p, window)
+
+    @property
+    def ls_moves(self) -> int:
+        return int(lib().or_ls_moves(self._h))
 
     def set_max_mod_frac(self, f: float):
         lib().or_set_max_mod_frac(self._h, f)

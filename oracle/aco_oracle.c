@@ -53,6 +53,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#define OR_LS_MAX_ANTS 8     /* ants improved by local search per iteration, at most */
+#define OR_LS_MAX_PASSES 16  /* windowed 2-opt passes, at most */
+
 /* ------------------------------------------------------------------ Philox4x32-10 (SC'11) */
 #define PH_M0 0xD2511F53u
 #define PH_M1 0xCD9E8D57u
@@ -195,6 +198,10 @@ typedef struct {
     int32_t* built;   /* m: 1 if ant was constructed this iteration */
     int32_t* seg_s;   /* m: start position s (partial) or -1 (full) */
     int32_t* seg_M;   /* m: rebuilt city count */
+    /* local search (Section 3.2 / Section 5): probability per ant and iteration, window */
+    double ls_p;
+    int32_t ls_window;
+    int64_t ls_moves;
     /* counters */
     int64_t decisions, fallbacks, scans;
     /* scratch */
@@ -462,6 +469,47 @@ static void build_partial(or_state* st, int a, uint32_t iteration) {
     st->seg_M[a] = M;
 }
 
+/* Windowed 2-opt (Section 3.2: 2-opt on a constructed tour; Section 5: only edges within W tour
+ * positions of each other).  A move (i, j), 2 <= j - i <= W, replaces edges (T[i], T[i+1]) and
+ * (T[j], T[j+1]) by (T[i], T[j]) and (T[i+1], T[j+1]), reversing T[i+1..j]; its FP64 gain is
+ * (d(a,b) + d(c,d)) - (d(a,c) + d(b,d)) and it is taken when the gain is > 0.  Passes split the
+ * positions into blocks at 0, off, off + 2W, off + 4W, ..., n (off = 0 on even passes, W on odd
+ * ones); within a block every position i (ascending) scans j = i + 2 .. min(i + W, end - 2)
+ * ascending, applies each improving move at once and carries on with the next j.  Moves never
+ * cross a block edge, so blocks are independent.  It stops after two passes in a row without a
+ * move, or after max_passes.  Returns the number of moves. */
+int or_two_opt_windowed(int n, const double* xy, int32_t* T, int W, int max_passes) {
+    if (n < 4 || W < 2) return 0;
+    int moves = 0, quiet = 0;
+    for (int pass = 0; pass < max_passes && quiet < 2; ++pass) {
+        const int off = (pass & 1) ? W : 0;
+        int improved = 0;
+        int b0 = 0;
+        while (b0 < n) {
+            int b1 = (b0 < off) ? off : b0 + 2 * W;
+            if (b1 > n) b1 = n;
+            for (int i = b0; i + 3 < b1; ++i) {
+                int jmax = i + W < b1 - 2 ? i + W : b1 - 2;
+                for (int j = i + 2; j <= jmax; ++j) {
+                    int a = T[i], b = T[i + 1], c = T[j], d = T[j + 1];
+                    double g = (or_edge_len(xy, a, b) + or_edge_len(xy, c, d)) -
+                               (or_edge_len(xy, a, c) + or_edge_len(xy, b, d));
+                    if (g > 0.0) {
+                        for (int l = i + 1, r = j; l < r; ++l, --r) {
+                            int t = T[l]; T[l] = T[r]; T[r] = t;
+                        }
+                        ++moves;
+                        improved = 1;
+                    }
+                }
+            }
+            b0 = b1;
+        }
+        quiet = improved ? 0 : quiet + 1;
+    }
+    return moves;
+}
+
 /* Tour construction for every ant (ants == NULL) or for the listed ants only.  rebuild = 0
  * reuses the pheromone computed by the previous call (same l_best population). */
 void or_construct_ex(or_state* st, int iteration, const int32_t* ants, int count, int rebuild) {
@@ -469,6 +517,7 @@ void or_construct_ex(or_state* st, int iteration, const int32_t* ants, int count
     if (st->p.mode == 1 && rebuild) lbest_pheromone(st);
     if (!ants) count = m;
     memset(st->built, 0, sizeof(int32_t) * (size_t)m);
+    int ls_count = 0;
     for (int c = 0; c < count; ++c) {
         int a = ants ? ants[c] : c;
         int partial = 0;
@@ -482,6 +531,17 @@ void or_construct_ex(or_state* st, int iteration, const int32_t* ants, int count
         }
         if (partial) build_partial(st, a, (uint32_t)iteration);
         else build_full(st, a, (uint32_t)iteration);
+        if (st->p.mode == 1 && st->ls_p > 0.0 && ls_count < OR_LS_MAX_ANTS) {
+            uint32_t x[4];
+            draw(st->p.seed, 0, (uint32_t)a, (uint32_t)iteration, 5, x);
+            if (or_u53(x[0], x[1]) < st->ls_p) {
+                ++ls_count;
+                st->ls_moves += or_two_opt_windowed(st->p.n, st->xy, st->newtour + (size_t)a * st->p.n,
+                                                    st->ls_window, OR_LS_MAX_PASSES);
+                st->seg_s[a] = -1;  /* committed as a whole tour */
+                st->seg_M[a] = st->p.n - 1;
+            }
+        }
         st->newlen[a] = or_tour_length(st->p.n, st->xy, st->newtour + (size_t)a * st->p.n);
         st->built[a] = 1;
     }
@@ -547,6 +607,10 @@ void or_get_tau(const or_state* st, double* out) {
 }
 /* Schedule of the PartialACO parameters between iterations (Section 3.1; Section 7's growing f). */
 void or_set_max_mod_frac(or_state* st, double f) { st->p.max_mod_frac = f; }
+/* Local search after construction: each ant (index order, at most OR_LS_MAX_ANTS per
+ * iteration) whose draw (0, ant, iteration, 5) gives u < p applies the windowed 2-opt. */
+void or_set_local_search(or_state* st, double p, int window) { st->ls_p = p; st->ls_window = window; }
+int64_t or_ls_moves(const or_state* st) { return st->ls_moves; }
 void or_set_p_partial(or_state* st, double p) { st->p.p_partial = p; }
 
 void or_set_tau(or_state* st, const double* tau) {
