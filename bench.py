@@ -46,7 +46,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="lbest200k",
-                    choices=sorted(aco_synth.WORKLOADS) + ["batch512", "learned20k", "schedule20k"])
+                    choices=sorted(aco_synth.WORKLOADS) + ["batch512", "learned20k", "schedule20k", "ls200k"])
     ap.add_argument("--ants", type=int, default=0, help="override m (profiling of smaller cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -606,8 +606,48 @@ def run_schedule(args):
     print(json.dumps(out))
 
 
+# ------------------------------------------------------------------ local search
+def run_ls(args):
+    """Windowed 2-opt (Section 3.2, Section 5's setting: probability 0.001 per tour, window 500) on
+    the 200,000-city workload (m = 1024, k = 16, f = 0.01), 50 iterations after the initial tours,
+    with and without local search: CUDA-event time per iteration, 2-opt moves, final C_gbest."""
+    import torch
+
+    from paper_1709_03187_gb300 import Colony
+
+    torch.cuda.set_device(0)
+    wl = aco_synth.WORKLOADS["lbest200k"]
+    params = dict(wl["params"])
+    xy = aco_synth.make("lbest200k")
+    res = {}
+    for name, p_ls in (("plain", 0.0), ("local_search", 0.001)):
+        col = Colony(xy, **params)
+        col.build_candidates()
+        col.iterate(0)
+        col.set_local_search(p_ls, 500)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for it in range(1, 51):
+            col.iterate(it)
+        e1.record()
+        torch.cuda.synchronize()
+        st = col.stats()
+        res[name] = {"ms_per_iteration": round(e0.elapsed_time(e1) / 50, 4), "gbest": st["gbest"],
+                     "ls_moves": int(st["ls_moves"])}
+        col.close()
+    out = {"metric": "ms per iteration and C_gbest after 50 iterations, windowed 2-opt (p=0.001, W=500) vs none",
+           "workload": "ls200k: n=200,000 clustered (200 clusters, sigma=0.005), k=16, m=1024, f=0.01",
+           "plain": res["plain"], "local_search": res["local_search"],
+           "time_ratio": round(res["local_search"]["ms_per_iteration"] / res["plain"]["ms_per_iteration"], 3)}
+    print(json.dumps(out))
+
+
 def main():
     args = parse_args()
+    if args.workload == "ls200k" and args.impl == "ours":
+        run_ls(args)
+        return
     if args.workload == "schedule20k" and args.impl == "ours":
         run_schedule(args)
         return

@@ -79,6 +79,7 @@ typedef struct aco_stats {
     double gbest;            /* length of the best tour so far (C_gbest), +inf if none       */
     int32_t gbest_ant;       /* ant holding it (lowest index among equals), -1 if none       */
     int32_t iterations;      /* completed construct + update pairs                           */
+    uint64_t ls_moves;       /* 2-opt moves made by the local search                         */
 } aco_stats;
 
 typedef struct aco_instance aco_instance; /* opaque: owns all device state of one colony */
@@ -155,6 +156,18 @@ aco_status aco_step_probs(aco_instance* inst, int32_t city, const uint32_t* visi
  * <= 1; LBEST mode; not between construct and update (ACO_ERR_STATE).  Host-side only. */
 aco_status aco_set_max_mod_frac(aco_instance* inst, double f);
 aco_status aco_set_p_partial(aco_instance* inst, double p_partial);
+
+/* Local search on constructed tours (Section 3.2: 2-opt applied to a tour with a given
+ * probability, 0.001 in the paper; Section 5: only edges within `window` tour positions, 500 in
+ * the paper).  From the next aco_construct_tours on, each ant (index order, at most 8 per
+ * iteration) whose Philox draw (0, ant, iteration, 5) gives u < p applies windowed 2-opt to its new
+ * tour: passes over position blocks 0, off, off + 2W, ..., n (off alternating 0 and W), each block
+ * scanned first-improvement (i ascending, j = i + 2 .. i + W ascending) with FP64 gains
+ * (d(a,b) + d(c,d)) - (d(a,c) + d(b,d)) > 0, until two passes in a row make no move (at most 16).
+ * The tour is then committed as a whole if strictly shorter than l_best.  p in [0, 1] (0 = off,
+ * the default), 2 <= window <= 4096.  LBEST mode, single colony; not between construct and
+ * update.  The first call with p > 0 allocates the working tours (8 n int32). */
+aco_status aco_set_local_search(aco_instance* inst, double p, int32_t window);
 
 /* ------------------------------------------------------------------ batched colonies
  * Many independent instances of uneven size solved together: the same method and parameters

@@ -38,6 +38,7 @@ class Stats(ctypes.Structure):
         ("decisions", ctypes.c_uint64), ("fallbacks", ctypes.c_uint64), ("exact_resolves", ctypes.c_uint64),
         ("improved", ctypes.c_uint64), ("partial_ants", ctypes.c_uint64), ("full_ants", ctypes.c_uint64),
         ("gbest", ctypes.c_double), ("gbest_ant", ctypes.c_int32), ("iterations", ctypes.c_int32),
+        ("ls_moves", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:
@@ -90,6 +91,7 @@ def lib():
             "aco_set_edge_scores": (S, [V, V]),
             "aco_set_max_mod_frac": (S, [V, ctypes.c_double]),
             "aco_set_p_partial": (S, [V, ctypes.c_double]),
+            "aco_set_local_search": (S, [V, ctypes.c_double, I32]),
             "aco_status_string": (ctypes.c_char_p, [S]),
             "aco_last_error": (ctypes.c_char_p, [V]),
         }
@@ -309,3 +311,7 @@ def aco_set_max_mod_frac(h, f: float):
 
 def aco_set_p_partial(h, p_partial: float):
     _check(lib().aco_set_p_partial(h, p_partial), "aco_set_p_partial", h)
+
+
+def aco_set_local_search(h, p: float, window: int = 500):
+    _check(lib().aco_set_local_search(h, p, window), "aco_set_local_search", h)

@@ -26,6 +26,7 @@ UNITS = [
     ("noalloc.cu", []),
     ("batch.cu", []),
     ("mlp.cu", []),
+    ("localsearch.cu", []),
 ]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

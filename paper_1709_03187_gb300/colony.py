@@ -73,6 +73,9 @@ class Colony:
     def set_max_mod_frac(self, f: float):
         _ffi.aco_set_max_mod_frac(self._h, f)
 
+    def set_local_search(self, p: float, window: int = 500):
+        _ffi.aco_set_local_search(self._h, p, window)
+
     def set_p_partial(self, p_partial: float):
         _ffi.aco_set_p_partial(self._h, p_partial)
 

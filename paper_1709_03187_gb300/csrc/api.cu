@@ -49,7 +49,8 @@ static void free_all(aco_instance* inst) {
                     inst->nb, inst->nbrank, inst->clen, inst->cfix, inst->q, inst->gbest, inst->gbest_ant,
                     inst->seg, inst->antit, inst->accq, inst->tau, inst->etab_d, inst->W64d, inst->W32d,
                     inst->tours, inst->succ_d, inst->pred_d, inst->counters, inst->errflag, inst->xy32,
-                    inst->ulist, inst->uxy, inst->bel, inst->btx, inst->btq, inst->deg, inst->ghk, inst->ghq};
+                    inst->ulist, inst->uxy, inst->bel, inst->btx, inst->btq, inst->deg, inst->ghk, inst->ghq,
+                    inst->ls_buf, inst->ls_sel, inst->ls_imp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -150,6 +151,7 @@ extern "C" aco_status aco_create_instance(const double* xy_dev, const aco_params
         if (pmin > n - 1) pmin = n - 1;
         inst->ucap = (int32_t)(n - pmin);
         inst->f_cap = p->max_mod_frac;
+        inst->ls_window = 500;
         ok &= dalloc(&inst->ulist, m * inst->ucap, &total);
         ok &= dalloc(&inst->uxy, m * inst->ucap, &total);
         ok &= dalloc(&inst->xy32, n, &total);
@@ -288,6 +290,10 @@ extern "C" aco_status aco_construct_tours(aco_instance* inst, int32_t iteration,
     aco_status st = inst->p.mode == ACO_MODE_LBEST_PARTIAL ? launch_construct_lbest(inst, iteration)
                                                            : launch_construct_dense(inst, iteration);
     if (st != ACO_OK) return st;
+    if (inst->p.mode == ACO_MODE_LBEST_PARTIAL && inst->ls_p > 0.0) {
+        st = launch_local_search(inst, iteration);
+        if (st != ACO_OK) return st;
+    }
     if (tours_out_dev || len_out_dev) {
         st = launch_write_new_tours(inst, tours_out_dev, len_out_dev);
         if (st != ACO_OK) return st;
@@ -364,6 +370,7 @@ extern "C" aco_status aco_get_stats(aco_instance* inst, aco_stats* out_host) {
     out_host->improved = c[CNT_IMPROVED];
     out_host->partial_ants = c[CNT_PARTIAL];
     out_host->full_ants = c[CNT_FULL];
+    out_host->ls_moves = c[CNT_LS_MOVES];
     out_host->gbest = INFINITY;
     out_host->gbest_ant = -1;
     if (inst->initialized) {

@@ -22,7 +22,10 @@
 typedef unsigned __int128 u128;
 
 // ------------------------------------------------------------------ random numbers
-enum : uint32_t { PURPOSE_WHEEL = 0, PURPOSE_START = 1, PURPOSE_KEEP = 2, PURPOSE_COIN = 3, PURPOSE_IR = 4 };
+enum : uint32_t { PURPOSE_WHEEL = 0, PURPOSE_START = 1, PURPOSE_KEEP = 2, PURPOSE_COIN = 3, PURPOSE_IR = 4, PURPOSE_LS = 5 };
+
+#define ACO_LS_MAX_ANTS 8     // ants improved by local search per iteration, at most
+#define ACO_LS_MAX_PASSES 16  // windowed 2-opt passes, at most
 
 struct Draw4 { uint32_t x0, x1, x2, x3; };
 
@@ -178,7 +181,7 @@ struct CandW {
     float w;
 };
 
-enum : int { CNT_DECISIONS = 0, CNT_FALLBACKS, CNT_RESOLVES, CNT_IMPROVED, CNT_PARTIAL, CNT_FULL, CNT_N };
+enum : int { CNT_DECISIONS = 0, CNT_FALLBACKS, CNT_RESOLVES, CNT_IMPROVED, CNT_PARTIAL, CNT_FULL, CNT_LS_MOVES, CNT_N };
 
 // ------------------------------------------------------------------ update kernel arguments
 struct CommitArgs {
@@ -270,6 +273,11 @@ struct aco_instance {
     float2* uxy;           // m*ucap their FP32 coordinates
     int32_t ucap;          // largest rebuilt count, n - max(1, n - floor(f n))
     double f_cap;          // f at creation: the largest f the per-ant lists are sized for
+    double ls_p;           // local search: probability per ant and iteration (0 = off)
+    int32_t ls_window;     // and its window W (tour positions)
+    int32_t* ls_buf;       // ACO_LS_MAX_ANTS * n working tours (allocated when first enabled)
+    int32_t* ls_sel;       // selected ants + count
+    int32_t* ls_imp;       // per selected ant and pass: a move was made
     float coord_r;         // max |coordinate| (rounded up)
     int32_t* deg;          // n degree-in-best-tours scratch of the edge features
     bool scored;           // candidate edges carry learned scores instead of eta^beta
@@ -293,6 +301,7 @@ aco_status set_err(aco_instance* inst, aco_status s, const char* fmt, ...);
 aco_status check_launch(aco_instance* inst, const char* what);
 aco_status sync_and_check(aco_instance* inst, const char* what);
 aco_status launch_reweight(aco_instance* inst);
+aco_status launch_local_search(aco_instance* inst, int32_t iteration);
 
 // kernels launched from the API (defined in the .cu files)
 aco_status launch_build_grid_and_knn(aco_instance* inst);
