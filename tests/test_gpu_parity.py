@@ -67,6 +67,8 @@ def test_tour_lengths_bit_exact(n, count):
     got = col.tour_lengths(torch.from_numpy(tours)).cpu().numpy()
     want = oracle.tour_lengths(xy, tours)
     assert np.array_equal(got, want)
+    empty = col.tour_lengths(torch.from_numpy(tours[:0]))  # no tours: nothing to do
+    assert empty.numel() == 0
 
 
 # ------------------------------------------------------------------ dense mode (Section 2)
@@ -119,6 +121,9 @@ def test_dense_probabilities_within_1e5():
     (3, 4, 2, 1.0, 6, 1.0, 0),
     (33, 5, 32, 0.5, 8, 1.0, 0),
     (1000, 64, 16, 0.01, 10, 1.0, 0),
+    (40, 1, 6, 0.5, 8, 1.0, 0),      # a single ant
+    (60, 6, 1, 0.5, 6, 1.0, 0),      # one candidate: nearly every step is an exhausted step
+    (90, 5, 2, 1.0, 6, 0.5, 1),      # two candidates, the Eq. 1 wheel over all unvisited
 ])
 def test_partialaco_iterations_bit_exact(n, m, k, f, iters, p_partial, fallback):
     xy = aco_synth.clustered(n, max(1, n // 50), 0.02, n + m)
