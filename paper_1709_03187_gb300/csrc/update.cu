@@ -30,14 +30,43 @@ __device__ __forceinline__ uint8_t rank_of(const int* __restrict__ cand, int k, 
     return 0xFF;
 }
 
+// Candidate ranks of `succ` and `pred` in the list of `c` (0xFF = not a candidate).  For k a
+// multiple of 4 the row is read with 16-byte loads in one round and compared in registers.
+__device__ __forceinline__ void ranks_of(const int* __restrict__ cand, int k, int c, int succ, int pred, uint8_t& rs,
+                                         uint8_t& rp) {
+    rs = rp = 0xFF;
+    if ((k & 3) == 0 && k <= 32) {
+        const int4* row = reinterpret_cast<const int4*>(cand + (size_t)c * k);
+        int4 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (4 * q < k) v[q] = __ldg(row + q);
+#pragma unroll
+        for (int q = 7; q >= 0; --q) {  // descending, so the lowest matching rank is kept
+            if (4 * q >= k) continue;
+            const int e[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+            for (int h = 3; h >= 0; --h) {
+                if (e[h] == succ) rs = (uint8_t)(4 * q + h);
+                if (e[h] == pred) rp = (uint8_t)(4 * q + h);
+            }
+        }
+        return;
+    }
+    rs = rank_of(cand, k, c, succ);
+    rp = rank_of(cand, k, c, pred);
+}
+
 __device__ __forceinline__ void set_neighbours(int* __restrict__ nb, uint8_t* __restrict__ nbrank,
                                                const int* __restrict__ cand, int m, int k, int a, int c, int succ,
                                                int pred) {
     const size_t e = ((size_t)c * m + a) * 2;
     nb[e] = succ;
     nb[e + 1] = pred;
-    nbrank[e] = rank_of(cand, k, c, succ);
-    nbrank[e + 1] = rank_of(cand, k, c, pred);
+    uint8_t rs, rp;
+    ranks_of(cand, k, c, succ, pred, rs, rp);
+    nbrank[e] = rs;
+    nbrank[e + 1] = rp;
 }
 
 // One warp per ant.  Batched colonies: block b is ant slot b, naming (instance, ant).
@@ -170,6 +199,8 @@ __global__ void __launch_bounds__(256) rebuild_kernel(const __grid_constant__ Re
             }
     }
     uint4 nxt[4];  // rank bytes of the warp's next city (fast path), requested one city ahead
+    double enxt = 0.0;  // and its eta^beta entry of this lane's rank
+    if (regq && i0 < iend && lane < k) enxt = R.etab[(size_t)i0 * k + lane];
     if (regq && i0 < iend) {
         const uint8_t* row = R.nbrank + (size_t)i0 * m * 2;
 #pragma unroll
@@ -180,6 +211,7 @@ __global__ void __launch_bounds__(256) rebuild_kernel(const __grid_constant__ Re
     }
     for (int i = i0; i < iend; i += istep) {
         unsigned long long Q = 0;
+        double ecur = -1.0;  // eta^beta of (i, lane) when prefetched, else read below
         if (use_ants) {
             for (int r = 0; r < k; ++r) hist[r * 32 + lane] = 0ull;
             const uint8_t* row = R.nbrank + (size_t)i * m * 2;
@@ -187,6 +219,8 @@ __global__ void __launch_bounds__(256) rebuild_kernel(const __grid_constant__ Re
                 uint4 v[4];
 #pragma unroll
                 for (int hb = 0; hb < 4; ++hb) v[hb] = nxt[hb];
+                ecur = enxt;
+                if (i + istep < iend && lane < k) enxt = R.etab[(size_t)(i + istep) * k + lane];
                 if (i + istep < iend) {
                     const uint8_t* nrow = R.nbrank + (size_t)(i + istep) * m * 2;
 #pragma unroll
@@ -263,7 +297,7 @@ __global__ void __launch_bounds__(256) rebuild_kernel(const __grid_constant__ Re
         if (lane < k) {
             const size_t e = (size_t)i * k + lane;
             const double tau = __dadd_rn(tau0, __dmul_rn(__ull2double_rn(Q), 0x1.0p-32));
-            const double wv = __dmul_rn(powr(tau, alpha), R.etab[e]);
+            const double wv = __dmul_rn(powr(tau, alpha), regq ? ecur : R.etab[e]);
             w32 = __double2float_rn(wv);
             if (!isfinite(wv)) atomicOr(R.errflag, DEVERR_NONFINITE);
             flag = !(w32 >= FLT_MIN && w32 <= FLT_MAX);
