@@ -50,7 +50,7 @@ static void free_all(aco_instance* inst) {
                     inst->seg, inst->antit, inst->accq, inst->tau, inst->etab_d, inst->W64d, inst->W32d,
                     inst->tours, inst->succ_d, inst->pred_d, inst->counters, inst->errflag, inst->xy32,
                     inst->ulist, inst->uxy, inst->bel, inst->btx, inst->btq, inst->deg, inst->ghk, inst->ghq,
-                    inst->ls_buf, inst->ls_sel, inst->ls_imp};
+                    inst->ls_buf, inst->ls_sel, inst->ls_imp, inst->fcnt, inst->ccnt, inst->csize};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -77,6 +77,9 @@ static bool params_ok(const aco_params* p, char* why, size_t wn) {
     if (!(p->p_partial >= 0 && p->p_partial <= 1)) return snprintf(why, wn, "p_partial in [0,1]"), false;
     if (p->fallback != 0 && p->fallback != 1) return snprintf(why, wn, "fallback must be 0 or 1"), false;
     if (p->selection != 0 && p->selection != 1) return snprintf(why, wn, "selection must be 0 or 1"), false;
+    // eta^0 = 1 makes every candidate list arbitrary and the exhausted-list rule a lowest-index scan
+    if (p->mode == ACO_MODE_LBEST_PARTIAL && !(p->beta > 0))
+        return snprintf(why, wn, "beta must be > 0 with candidate lists"), false;
     if (p->mode == ACO_MODE_DENSE && p->selection != 0)
         return snprintf(why, wn, "Independent Roulette needs candidate lists (LBEST mode)"), false;
     if (p->mode == ACO_MODE_DENSE && p->n > 8192) return snprintf(why, wn, "DENSE mode supports n <= 8192"), false;
@@ -230,6 +233,23 @@ extern "C" aco_status aco_create_instance(const double* xy_dev, const aco_params
     g.margin = 1e-6 * h + 1e-14 * mag;
     inst->grid = g;
     cudaMemcpy(inst->grid_dev, &g, sizeof(g), cudaMemcpyHostToDevice);
+    if (p->mode == ACO_MODE_LBEST_PARTIAL) {
+        // per-ant unvisited counts per cell and per coarse block (full constructions)
+        inst->ncells = gx * gy;
+        inst->cgx = (gx + ACO_CBLK - 1) / ACO_CBLK;
+        inst->cgy = (gy + ACO_CBLK - 1) / ACO_CBLK;
+        inst->ncoarse = inst->cgx * inst->cgy;
+        bool ok2 = dalloc(&inst->fcnt, m * inst->ncells, &total);
+        ok2 &= dalloc(&inst->ccnt, m * inst->ncoarse, &total);
+        ok2 &= dalloc(&inst->csize, inst->ncoarse, &total);
+        if (!ok2) {
+            cudaGetLastError();
+            snprintf(g_create_err, sizeof(g_create_err), "device allocation of %.1f MB failed", total / 1e6);
+            free_all(inst);
+            delete inst;
+            return ACO_ERR_OOM;
+        }
+    }
     inst->last_iteration = -1;
     *out = inst;
     return ACO_OK;
@@ -264,6 +284,8 @@ extern "C" aco_status aco_build_candidates(aco_instance* inst, int32_t* cand_out
     aco_status st = launch_build_grid_and_knn(inst);
     if (st != ACO_OK) return st;
     if (inst->p.mode == ACO_MODE_LBEST_PARTIAL) {
+        st = launch_coarse_sizes(inst);
+        if (st != ACO_OK) return st;
         st = launch_lbest_init_weights(inst);
         if (st != ACO_OK) return st;
         if (cand_out_dev)

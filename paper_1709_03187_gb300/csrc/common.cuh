@@ -24,6 +24,7 @@ typedef unsigned __int128 u128;
 // ------------------------------------------------------------------ random numbers
 enum : uint32_t { PURPOSE_WHEEL = 0, PURPOSE_START = 1, PURPOSE_KEEP = 2, PURPOSE_COIN = 3, PURPOSE_IR = 4, PURPOSE_LS = 5 };
 
+#define ACO_CBLK 8            // grid cells per edge of a coarse block (nearest-unvisited search)
 #define ACO_LS_MAX_ANTS 8     // ants improved by local search per iteration, at most
 #define ACO_LS_MAX_PASSES 16  // windowed 2-opt passes, at most
 
@@ -280,6 +281,10 @@ struct aco_instance {
     int32_t* ls_imp;       // per selected ant and pass: a move was made
     float coord_r;         // max |coordinate| (rounded up)
     int32_t* deg;          // n degree-in-best-tours scratch of the edge features
+    int32_t* fcnt;         // m*ncells unvisited cities per grid cell during a full construction
+    int32_t* ccnt;         // m*ncoarse and per block of ACO_CBLK x ACO_CBLK cells
+    int32_t* csize;        // ncoarse cities per block
+    int32_t ncells, ncoarse, cgx, cgy;
     bool scored;           // candidate edges carry learned scores instead of eta^beta
 
     // dense mode
@@ -305,6 +310,7 @@ aco_status launch_local_search(aco_instance* inst, int32_t iteration);
 
 // kernels launched from the API (defined in the .cu files)
 aco_status launch_build_grid_and_knn(aco_instance* inst);
+aco_status launch_coarse_sizes(aco_instance* inst);
 aco_status launch_dense_init(aco_instance* inst);
 aco_status launch_lbest_init_weights(aco_instance* inst);
 aco_status launch_construct_lbest(aco_instance* inst, int32_t iteration);

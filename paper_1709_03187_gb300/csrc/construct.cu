@@ -60,6 +60,10 @@ struct LbestArgs {
     unsigned short* __restrict__ bel;
     int* __restrict__ btx;
     unsigned long long* __restrict__ btq;
+    int* __restrict__ fcnt;                // per-ant unvisited cities per grid cell (full constructions)
+    int* __restrict__ ccnt;                // and per coarse block of ACO_CBLK x ACO_CBLK cells
+    const int* __restrict__ csize;         // cities per coarse block
+    int ncells, ncoarse, cgx, cgy;
     int* __restrict__ ghk;                 // per-ant global hash of boosted cities (2m slots, -1 = empty)
     unsigned long long* __restrict__ ghq;  // and their summed weights (0 when empty)
     int* __restrict__ ulist;
@@ -151,15 +155,11 @@ __device__ __forceinline__ void top2_push(float w, int x, float& w1, int& x1, fl
 // their neighbour ids together and lists the unvisited ones with the weight of the ant each entry
 // belongs to.  The lists are per-ant global scratch of capacity 2m (every entry fits) and are
 // filled with warp-aggregated offsets.  The integer pheromone of a city is the sum of the weights
-// of its entries.
-#define TOUCH_SM 96  // touched lists up to this length are aggregated in shared memory
-
+// of its entries; equal cities are merged in a hash (shared memory for short lists).
 #define BHASH 128     // slots of the per-ant hash of boosted cities (distinct unvisited neighbours)
 #define BHASH_MAX 96  // more distinct cities than this: the listed path decides
 
 struct BoostSmem {
-    int tx[TOUCH_SM];
-    unsigned long long tq[TOUCH_SM];
     unsigned long long hq[BHASH];  // summed integer pheromone of the city in each slot
     int hkey[BHASH];               // city, -1 = empty (kept empty between exhausted steps)
     int hcount;                    // distinct cities inserted
@@ -466,48 +466,246 @@ __device__ void remaining_argmax(const LbestArgs& A, int a, int cur, const uint3
     }
 }
 
-// Full construction: nearest unvisited city by a ring search over the grid (weight at tau0).
-__device__ void nearest_unvisited(const LbestArgs& A, int cur, const uint32_t* bits, int lane, double qx, double qy,
-                                  double tau0pow, double& bw, int& bc) {
+// Cell (x, y) of the `idx`-th cell on the Chebyshev ring r around (cx, cy) of a gx x gy grid;
+// false outside the grid.
+__device__ __forceinline__ bool ring_xy(int cx, int cy, int r, int idx, int gx, int gy, int& x, int& y) {
+    if (r == 0) { x = cx; y = cy; }
+    else if (idx < 2 * r + 1) { x = cx - r + idx; y = cy - r; }
+    else if (idx < 4 * r + 2) { x = cx - r + (idx - 2 * r - 1); y = cy + r; }
+    else if (idx < 6 * r + 1) { x = cx - r; y = cy - r + 1 + (idx - 4 * r - 2); }
+    else { x = cx + r; y = cy - r + 1 + (idx - 6 * r - 1); }
+    return x >= 0 && y >= 0 && x < gx && y < gy;
+}
+
+// Lower bound on the distance from (qx, qy) to any point outside the grid cells [x0, x1] x [y0, y1];
+// -1 when the block covers the whole grid.
+__device__ __forceinline__ double block_lower_bound(const GridDesc& g, double qx, double qy, int x0, int x1, int y0,
+                                                    int y1) {
+    double lb = 1e300;
+    bool open = false;
+    if (x0 > 0) { lb = fmin(lb, qx - (g.xmin + (double)x0 * g.h)); open = true; }
+    if (x1 < g.gx - 1) { lb = fmin(lb, (g.xmin + (double)(x1 + 1) * g.h) - qx); open = true; }
+    if (y0 > 0) { lb = fmin(lb, qy - (g.ymin + (double)y0 * g.h)); open = true; }
+    if (y1 < g.gy - 1) { lb = fmin(lb, (g.ymin + (double)(y1 + 1) * g.h) - qy); open = true; }
+    if (!open) return -1.0;
+    lb -= g.margin;
+    return lb < 0.0 ? 0.0 : lb;
+}
+
+// Unvisited cities of grid cell c at tau0: exact weights of the cities that can reach the lane's
+// nearest (nd: the lane's smallest squared distance so far).
+__device__ __forceinline__ void scan_cell(const LbestArgs& A, int c, const uint32_t* bits, double qx, double qy,
+                                          double tau0pow, double& nd, double& bw, int& bc) {
+    for (int pb = A.cell_start[c], pe = A.cell_start[c + 1]; pb < pe; ++pb) {
+        const int x = A.cell_city[pb];
+        if (is_visited(bits, x)) continue;
+        const double d2 = dist2(qx, qy, A.cell_xy[2 * pb], A.cell_xy[2 * pb + 1]);
+        if (!(d2 <= __dmul_rn(nd, 1.0 + 0x1.0p-40))) continue;  // cannot reach the best weight
+        const double w = __dmul_rn(tau0pow, eta_pow_from_d2(d2, A.beta));
+        if (better(w, x, bw, bc)) { bw = w; bc = x; }
+        nd = fmin(nd, d2);
+    }
+}
+
+__device__ __forceinline__ bool ring_done(const GridDesc& g, double nd, double lb) {
+    double wd = nd;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) wd = fmin(wd, __shfl_xor_sync(FULL, wd, o));
+    if (lb < 0.0) return true;
+    return wd < DBL_MAX && __dmul_rn(lb, lb) > __dmul_rn(wd, 1.0 + 0x1.0p-40);
+}
+
+// Full construction: nearest unvisited city (weight at tau0), every contender's weight exact.  The
+// ant's per-cell and per-block counts of unvisited cities let the search skip empty cells: rings
+// of cells 0..3 around the current city first, then rings of coarse blocks, each stopping as
+// soon as nothing outside the searched square can be nearer than the nearest found.
+__device__ void nearest_unvisited_exact(const LbestArgs& A, int a, int cur, const uint32_t* bits, int lane, double qx,
+                                        double qy, double tau0pow, double& bw, int& bc) {
     const GridDesc g = *A.grid;
+    const int* fc = A.fcnt + (size_t)a * A.ncells;
+    const int* cc = A.ccnt + (size_t)a * A.ncoarse;
     const int cell = A.city_cell[cur];
     const int cx = cell % g.gx, cy = cell / g.gx;
     double nd = DBL_MAX;
-    for (int r = 0;; ++r) {
+    for (int r = 0; r <= 3; ++r) {
         const int ncell = r == 0 ? 1 : 8 * r;
         for (int c0 = 0; c0 < ncell; c0 += 32) {
-            int pb = 0, pe = 0;
-            if (c0 + lane < ncell) {
-                int x, y;
-                const int idx = c0 + lane;
-                if (r == 0) { x = cx; y = cy; }
-                else if (idx < 2 * r + 1) { x = cx - r + idx; y = cy - r; }
-                else if (idx < 4 * r + 2) { x = cx - r + (idx - 2 * r - 1); y = cy + r; }
-                else if (idx < 6 * r + 1) { x = cx - r; y = cy - r + 1 + (idx - 4 * r - 2); }
-                else { x = cx + r; y = cy - r + 1 + (idx - 6 * r - 1); }
-                if (x >= 0 && y >= 0 && x < g.gx && y < g.gy) {
-                    const int c = y * g.gx + x;
-                    pb = A.cell_start[c];
-                    pe = A.cell_start[c + 1];
-                }
-            }
-            for (; pb < pe; ++pb) {
-                const int x = A.cell_city[pb];
-                if (is_visited(bits, x)) continue;
-                const double d2 = dist2(qx, qy, A.cell_xy[2 * pb], A.cell_xy[2 * pb + 1]);
-                if (!(d2 <= __dmul_rn(nd, 1.0 + 0x1.0p-40))) continue;  // cannot reach the best weight
-                const double w = __dmul_rn(tau0pow, eta_pow_from_d2(d2, A.beta));
-                if (better(w, x, bw, bc)) { bw = w; bc = x; }
-                nd = fmin(nd, d2);
+            int x, y;
+            if (c0 + lane < ncell && ring_xy(cx, cy, r, c0 + lane, g.gx, g.gy, x, y)) {
+                const int c = y * g.gx + x;
+                if (__ldcg(fc + c) > 0) scan_cell(A, c, bits, qx, qy, tau0pow, nd, bw, bc);
             }
         }
-        double wd = nd;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) wd = fmin(wd, __shfl_xor_sync(FULL, wd, o));
-        const double lb = ring_lower_bound(g, qx, qy, cx, cy, r);
-        if (lb < 0.0) break;
-        if (wd < DBL_MAX && __dmul_rn(lb, lb) > __dmul_rn(wd, 1.0 + 0x1.0p-40)) break;
+        if (ring_done(g, nd, ring_lower_bound(g, qx, qy, cx, cy, r))) return;
     }
+    const int CX = cx / ACO_CBLK, CY = cy / ACO_CBLK;
+    for (int rho = 0;; ++rho) {
+        const int nc = rho == 0 ? 1 : 8 * rho;
+        for (int c0 = 0; c0 < nc; c0 += 32) {
+            int X, Y, C = -1;
+            if (c0 + lane < nc && ring_xy(CX, CY, rho, c0 + lane, A.cgx, A.cgy, X, Y)) C = Y * A.cgx + X;
+            unsigned ne = __ballot_sync(FULL, C >= 0 && __ldcg(cc + C) > 0);
+            while (ne) {  // the warp scans each non-empty block: its cells, two per lane
+                const int src = __ffs(ne) - 1;
+                ne &= ne - 1;
+                const int Cs = __shfl_sync(FULL, C, src);
+                const int X0 = (Cs % A.cgx) * ACO_CBLK, Y0 = (Cs / A.cgx) * ACO_CBLK;
+                for (int f = lane; f < ACO_CBLK * ACO_CBLK; f += 32) {
+                    const int fx = X0 + f % ACO_CBLK, fy = Y0 + f / ACO_CBLK;
+                    if (fx < g.gx && fy < g.gy && __ldcg(fc + fy * g.gx + fx) > 0)
+                        scan_cell(A, fy * g.gx + fx, bits, qx, qy, tau0pow, nd, bw, bc);
+                }
+            }
+        }
+        const double lb = block_lower_bound(g, qx, qy, (CX - rho) * ACO_CBLK, (CX + rho + 1) * ACO_CBLK - 1,
+                                            (CY - rho) * ACO_CBLK, (CY + rho + 1) * ACO_CBLK - 1);
+        if (ring_done(g, nd, lb)) return;
+    }
+}
+
+// Per lane: the two smallest squared distances seen and the city of the smallest (lowest index
+// among equals).
+struct Near2 {
+    double d1, d2;
+    int c1;
+};
+
+__device__ __forceinline__ void near_push(Near2& s, double d, int x) {
+    if (x == s.c1) return;  // the same city seen again (block rings overlap the cell rings)
+    if (d < s.d1 || (d == s.d1 && x < s.c1)) {
+        s.d2 = s.d1;
+        s.d1 = d;
+        s.c1 = x;
+    } else if (d < s.d2) {
+        s.d2 = d;
+    }
+}
+
+// The unvisited cities of the lane's cell (c >= 0 with unvisited cities, else -1), spread over
+// the warp: an inclusive scan of the cell sizes, then every lane takes one city slot at a time
+// and finds its cell by a binary search over the scan (shuffles).
+__device__ __forceinline__ void scan_cells_flat(const LbestArgs& A, int c, const uint32_t* bits, double qx, double qy,
+                                                int lane, Near2& s) {
+    int pb = 0, nc = 0;
+    if (c >= 0) {
+        pb = A.cell_start[c];
+        nc = A.cell_start[c + 1] - pb;
+    }
+    int incl = nc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int T = __shfl_sync(FULL, incl, 31);
+    for (int s0 = 0; s0 < T; s0 += 32) {
+        const int slot = s0 + lane;
+        int lo = 0, hi = 31;
+#pragma unroll
+        for (int it = 0; it < 5; ++it) {
+            const int mid = (lo + hi) >> 1;
+            const int v = __shfl_sync(FULL, incl, mid);
+            if (v > slot) hi = mid;
+            else lo = mid + 1;
+        }
+        const int excl = __shfl_sync(FULL, incl - nc, lo);
+        const int base = __shfl_sync(FULL, pb, lo);
+        if (slot < T) {
+            const int p = base + (slot - excl);
+            const int x = A.cell_city[p];
+            if (!is_visited(bits, x)) near_push(s, dist2(qx, qy, A.cell_xy[2 * p], A.cell_xy[2 * p + 1]), x);
+        }
+    }
+}
+
+__device__ __forceinline__ double warp_min_d(double v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = fmin(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+
+// Full construction: nearest unvisited city (weight at tau0) by squared distances alone.  The
+// weight only falls as the distance grows, so the city of smallest d^2 wins unless another city
+// lies within 2^-40 of it (a possible tie of the rounded weights): then the exact search decides.
+__device__ void nearest_unvisited(const LbestArgs& A, int a, int cur, const uint32_t* bits, int lane, double qx,
+                                  double qy, double tau0pow, double& bw, int& bc) {
+    const GridDesc g = *A.grid;
+    const int* fc = A.fcnt + (size_t)a * A.ncells;
+    const int* cc = A.ccnt + (size_t)a * A.ncoarse;
+    const int cell = A.city_cell[cur];
+    const int cx = cell % g.gx, cy = cell / g.gx;
+    Near2 s{DBL_MAX, DBL_MAX, 0x7fffffff};
+    bool done = false;
+    for (int r = 0; r <= 3 && !done; ++r) {
+        const int ncell = r == 0 ? 1 : 8 * r;
+        for (int c0 = 0; c0 < ncell; c0 += 32) {
+            int x, y, c = -1;
+            if (c0 + lane < ncell && ring_xy(cx, cy, r, c0 + lane, g.gx, g.gy, x, y) && __ldcg(fc + y * g.gx + x) > 0)
+                c = y * g.gx + x;
+            scan_cells_flat(A, c, bits, qx, qy, lane, s);
+        }
+        const double lb = ring_lower_bound(g, qx, qy, cx, cy, r);
+        const double wd = warp_min_d(s.d1);
+        done = lb < 0.0 || (wd < DBL_MAX && __dmul_rn(lb, lb) > __dmul_rn(wd, 1.0 + 0x1.0p-40));
+    }
+    const int CX = cx / ACO_CBLK, CY = cy / ACO_CBLK;
+    for (int rho = 0; !done; ++rho) {
+        const int nc = rho == 0 ? 1 : 8 * rho;
+        for (int c0 = 0; c0 < nc; c0 += 32) {
+            int X, Y, C = -1;
+            if (c0 + lane < nc && ring_xy(CX, CY, rho, c0 + lane, A.cgx, A.cgy, X, Y)) C = Y * A.cgx + X;
+            unsigned ne = __ballot_sync(FULL, C >= 0 && __ldcg(cc + C) > 0);
+            while (ne) {  // each non-empty block: its cells, two per lane
+                const int src = __ffs(ne) - 1;
+                ne &= ne - 1;
+                const int Cs = __shfl_sync(FULL, C, src);
+                const int X0 = (Cs % A.cgx) * ACO_CBLK, Y0 = (Cs / A.cgx) * ACO_CBLK;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int f = lane + 32 * h;
+                    const int fx = X0 + f % ACO_CBLK, fy = Y0 + f / ACO_CBLK;
+                    int c = -1;
+                    if (fx < g.gx && fy < g.gy && __ldcg(fc + fy * g.gx + fx) > 0) c = fy * g.gx + fx;
+                    scan_cells_flat(A, c, bits, qx, qy, lane, s);
+                }
+            }
+        }
+        const double lb = block_lower_bound(g, qx, qy, (CX - rho) * ACO_CBLK, (CX + rho + 1) * ACO_CBLK - 1,
+                                            (CY - rho) * ACO_CBLK, (CY + rho + 1) * ACO_CBLK - 1);
+        const double wd = warp_min_d(s.d1);
+        done = lb < 0.0 || (wd < DBL_MAX && __dmul_rn(lb, lb) > __dmul_rn(wd, 1.0 + 0x1.0p-40));
+    }
+    const double D = warp_min_d(s.d1);
+    const double thr = __dmul_rn(D, 1.0 + 0x1.0p-40);
+    if (__any_sync(FULL, s.d2 <= thr)) {  // two cities within the tie margin on one lane
+        nearest_unvisited_exact(A, a, cur, bits, lane, qx, qy, tau0pow, bw, bc);
+        return;
+    }
+    if (s.d1 <= thr) {
+        const double w = __dmul_rn(tau0pow, eta_pow_from_d2(s.d1, A.beta));
+        if (better(w, s.c1, bw, bc)) { bw = w; bc = s.c1; }
+    }
+}
+
+// The counts of a full construction: every cell's city count, then each chosen city removed
+// (deferred: the cities chosen since the last exhausted step, read back from the tour).
+__device__ void counts_init(const LbestArgs& A, int a, int lane) {
+    int* fc = A.fcnt + (size_t)a * A.ncells;
+    int* cc = A.ccnt + (size_t)a * A.ncoarse;
+    for (int c = lane; c < A.ncells; c += 32) fc[c] = A.cell_start[c + 1] - A.cell_start[c];
+    for (int c = lane; c < A.ncoarse; c += 32) cc[c] = A.csize[c];
+}
+
+__device__ void counts_remove(const LbestArgs& A, int a, const int* seg, int from, int to, int lane) {
+    const GridDesc& g = *A.grid;
+    int* fc = A.fcnt + (size_t)a * A.ncells;
+    int* cc = A.ccnt + (size_t)a * A.ncoarse;
+    for (int p = from + lane; p < to; p += 32) {
+        const int c = A.city_cell[seg[p]];
+        atomicSub(fc + c, 1);
+        atomicSub(cc + ((c / g.gx) / ACO_CBLK) * A.cgx + (c % g.gx) / ACO_CBLK, 1);
+    }
+    __syncwarp();
 }
 
 // Eq. 1 wheel over every unvisited city in index order (fallback = 1), FP64, sequential order.
@@ -892,7 +1090,7 @@ __device__ int exhausted_choice(const LbestArgs& A, int a, int cur, double u, bo
         }
         if (!decided) {
             if (partial) remaining_argmax(A, a, cur, bits, ucount, lane, qx, qy, tau0pow, bw, bc);
-            else nearest_unvisited(A, cur, bits, lane, qx, qy, tau0pow, bw, bc);
+            else nearest_unvisited(A, a, cur, bits, lane, qx, qy, tau0pow, bw, bc);
             if (A.initialized) {
                 const int nt = collect_boosted(A, a, cur, bits, lane, pre ? &rr : nullptr);
                 float f1 = -1.f, f2 = -1.f, fd = FLT_MAX;
@@ -1010,6 +1208,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) construct_lbest_kernel(const
         const Draw4 d1 = aco_draw(A.seed, 0, a, iteration, PURPOSE_START);
         start = (int)below(d1.x0, (uint32_t)n);
         for (int w = lane; w < W; w += 32) bits[w] = 0u;
+        if (A.fallback == 0) counts_init(A, a, lane);
         __syncwarp();
         if (lane == 0) {
             bits[start >> 5] = 1u << (start & 31);
@@ -1030,6 +1229,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) construct_lbest_kernel(const
     const CandW* rowp = A.candw + (size_t)cur * k;  // current row (global or a staged copy)
     int wb = 0;                                      // staging buffer written this step
     int pend = -1;                                   // chosen city whose visited bit is set next step
+    int counted = 0;  // full construction: tour positions already removed from the unvisited counts
     for (int t = 0; t < steps; ++t) {
         if ((t & 31) == 0) {
             const Draw4 d = aco_draw(A.seed, (uint32_t)(t + lane), a, iteration, PURPOSE_WHEEL);
@@ -1120,6 +1320,10 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) construct_lbest_kernel(const
             rowp = staged ? &stage[wb][pick][0] : A.candw + (size_t)j * k;
         } else {
             ++nfall;
+            if (!partial && A.fallback == 0) {  // the cities chosen so far leave the unvisited counts
+                counts_remove(A, a, seg, counted, t + 1, lane);
+                counted = t + 1;
+            }
             // no copies were issued this step (every candidate is visited): the staging buffer is free
             j = exhausted_choice(A, a, cur, __shfl_sync(FULL, my_u, t & 31), partial, ucount, bits, boost,
                                  staged ? reinterpret_cast<unsigned short*>(stage) : nullptr, lane);
@@ -1186,7 +1390,9 @@ void fill_lbest_args(const aco_instance* inst, int32_t iteration, LbestArgs& A) 
     A.cell_start = inst->cell_start; A.cell_city = inst->cell_city; A.cell_xy = inst->cell_xy; A.candw = inst->candw;
     A.W64 = inst->W64; A.lbest = inst->lbest; A.nb = inst->nb; A.nbrank = inst->nbrank;
     A.q = inst->q; A.cfix = inst->cfix;
-    A.seg = inst->seg; A.antit = inst->antit; A.accq = inst->accq; A.bel = inst->bel; A.btx = inst->btx; A.btq = inst->btq; A.ghk = inst->ghk; A.ghq = inst->ghq; A.ulist = inst->ulist; A.uxy = inst->uxy;
+    A.seg = inst->seg; A.antit = inst->antit; A.accq = inst->accq; A.bel = inst->bel; A.btx = inst->btx; A.btq = inst->btq; A.ghk = inst->ghk; A.ghq = inst->ghq; A.ulist = inst->ulist;
+    A.fcnt = inst->fcnt; A.ccnt = inst->ccnt; A.csize = inst->csize; A.ncells = inst->ncells;
+    A.ncoarse = inst->ncoarse; A.cgx = inst->cgx; A.cgy = inst->cgy; A.uxy = inst->uxy;
     A.counters = inst->counters; A.errflag = inst->errflag;
 }
 

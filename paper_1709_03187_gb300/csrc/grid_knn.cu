@@ -299,3 +299,22 @@ cudaError_t launch_knn_on_scratch(const double* xy, int n, int k, int32_t* cand,
                                               nullptr, nullptr, errflag);
     return cudaGetLastError();
 }
+
+// Cities per coarse block of ACO_CBLK x ACO_CBLK grid cells (the nearest-unvisited search of full
+// constructions skips empty blocks).
+__global__ void coarse_size_kernel(const int* __restrict__ cell_start, int gx, int gy, int cgx, int ncoarse,
+                                   int* __restrict__ csize) {
+    for (int C = blockIdx.x * blockDim.x + threadIdx.x; C < ncoarse; C += gridDim.x * blockDim.x) {
+        const int X0 = (C % cgx) * ACO_CBLK, Y0 = (C / cgx) * ACO_CBLK;
+        int sum = 0;
+        for (int y = Y0; y < Y0 + ACO_CBLK && y < gy; ++y)
+            for (int x = X0; x < X0 + ACO_CBLK && x < gx; ++x) sum += cell_start[y * gx + x + 1] - cell_start[y * gx + x];
+        csize[C] = sum;
+    }
+}
+
+aco_status launch_coarse_sizes(aco_instance* inst) {
+    coarse_size_kernel<<<ceil_div(inst->ncoarse, 256), 256, 0, inst->stream>>>(
+        inst->cell_start, inst->grid.gx, inst->grid.gy, inst->cgx, inst->ncoarse, inst->csize);
+    return check_launch(inst, "coarse_size_kernel");
+}
