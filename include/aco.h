@@ -50,7 +50,7 @@ typedef struct aco_params {
     int32_t m;            /* ants, >= 1                                                      */
     int32_t k;            /* candidate-list length, 1..min(32, n-1) (ignored in DENSE)       */
     double alpha;         /* pheromone exponent of Eq. 1                                     */
-    double beta;          /* heuristic exponent of Eq. 1 (eta = 1/d)                         */
+    double beta;          /* heuristic exponent of Eq. 1 (eta = 1/d); > 0 with candidate lists */
     double rho;           /* evaporation rate of Eq. 2 (DENSE only; the Section 3 form has
                              no evaporation matrix)                                          */
     double tau0;          /* initial / base pheromone, > 0                                   */
