@@ -102,7 +102,7 @@ aco_status aco_build_candidates(aco_instance* inst, int32_t* cand_out_dev);
 
 /* Tour construction for every ant (Section 2, Eq. 1; Algorithm 1).
  * DENSE: each ant starts at a random city and applies Eq. 1 over all unvisited cities.
- * LBEST: the first call builds full initial tours (Algorithm 1, lines 1-3; tau = tau0).  Later
+ * LBEST: the first call builds full initial tours (Algorithm 1, before its iterations; tau = tau0).  Later
  * calls rebuild, per ant, a random contiguous part of at most floor(f n) cities of l_best
  * (with probability p_partial; otherwise a full tour), using Eq. 1 over the unvisited
  * candidates and the exhausted-list rule.  `iteration` keys the Philox draws (callers pass
@@ -114,7 +114,7 @@ aco_status aco_construct_tours(aco_instance* inst, int32_t iteration, int32_t* t
 /* Pheromone update after aco_construct_tours.
  * DENSE: Eq. 2 (tau <- (1 - rho) tau on every edge) then Eq. 3-5 (tau_ij += sum_k 1/C^k over
  * the tours containing edge (i,j), both directions).
- * LBEST: Algorithm 1 line 10 (an ant's l_best is replaced by its new tour when strictly
+ * LBEST: Algorithm 1 (an ant's l_best is replaced by its new tour when strictly
  * shorter), C_gbest = min C_lbest, then the Section 3 pheromone of every candidate edge,
  * tau_ij = tau0 + sum_a (C_gbest / C_a) [ (i,j) in l_best_a ] -- edges of replaced tours drop
  * out (evaporation) and edges of new l_best tours enter (deposit). */

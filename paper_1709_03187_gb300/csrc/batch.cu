@@ -229,7 +229,7 @@ extern "C" aco_status aco_batch_run(aco_batch* b, int32_t first_iteration, int32
     if (!b || iterations < 0 || first_iteration < 0) return ACO_ERR_INVALID_ARG;
     if (!b->built) return berr(b, ACO_ERR_STATE, "run before build_candidates");
     if (iterations == 0) return ACO_OK;
-    if (!b->initialized) {  // initial tours (Algorithm 1, lines 1-3): every ant builds a full tour
+    if (!b->initialized) {  // initial tours (Algorithm 1, before its iterations): every ant builds a full tour
         aco_status st = upload_args(b, first_iteration);
         if (st != ACO_OK) return st;
         if (enqueue_iteration(b, b->config) != cudaSuccess) return berr(b, ACO_ERR_CUDA, "initial iteration failed");

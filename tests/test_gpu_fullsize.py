@@ -3,7 +3,7 @@
 The oracle cannot run the whole colony at this size in seconds, so it checks sampled outputs it
 can compute one by one:
   * candidate lists of sampled cities by brute force (bit-exact);
-  * initial tours (Algorithm 1, lines 1-3) of sampled ants, built by the oracle from scratch with
+  * initial tours (Algorithm 1, before its iterations) of sampled ants, built by the oracle from scratch with
     its own candidate lists (bit-exact tours and lengths);
   * PartialACO iterations of sampled ants replayed by the oracle from the colony's state before
     the iteration (teacher forcing: the pre-iteration l_best population is read from the device
@@ -51,7 +51,7 @@ def test_fullsize_iterations(colony200k):
     col, xy, p, cand, ocand = colony200k
     n, m, k, f = p["n"], p["m"], p["k"], p["max_mod_frac"]
     rng = np.random.default_rng(1)
-    # initial tours (Algorithm 1, lines 1-3)
+    # initial tours (Algorithm 1, before its iterations)
     tours, lens = col.construct(0, return_tours=True, return_lengths=True)
     T0 = tours.cpu().numpy()
     L0 = lens.cpu().numpy()

@@ -1,4 +1,4 @@
-"""What the trained network gains over the plain heuristic (the plain method is the judge).
+"""What the trained network gains over the plain heuristic (the plain method is the yardstick).
 
 The network is trained on the GPU from plain runs on small clustered instances (labels: the
 candidate ranks of each city's neighbours in the best tour), then scores the candidate edges of
