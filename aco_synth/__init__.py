@@ -21,8 +21,8 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["uniform", "clustered", "mixed", "make", "batch_sizes", "permutations", "bf16_values", "mlp_weights",
-           "edge_scores", "WORKLOADS"]
+__all__ = ["uniform", "clustered", "mixed", "make", "batch_sizes", "permutations", "snake_tours", "bf16_values",
+           "mlp_weights", "edge_scores", "WORKLOADS"]
 
 
 def _dedupe(xy: np.ndarray, rng: np.random.Generator, redraw) -> np.ndarray:
@@ -104,6 +104,30 @@ def permutations(count: int, n: int, seed: int) -> np.ndarray:
     """`count` independent uniformly random tours of n cities, int32 [count][n]."""
     rng = np.random.default_rng(seed)
     return np.stack([rng.permutation(n) for _ in range(count)]).astype(np.int32)
+
+
+def snake_tours(xy: np.ndarray, count: int, seed: int, grid: int = 512, reversals: int = 64,
+                max_len: int = 2000) -> np.ndarray:
+    """`count` spatially coherent random tours, int32 [count][n]: the cities in the order of a
+    boustrophedon sweep over a grid x grid binning of the bounding box (by x within a bin), then
+    per tour a random rotation and `reversals` reversals of random segments of 2..max_len
+    positions.  (A population of tours that look like a colony's, without running one.)"""
+    rng = np.random.default_rng(seed)
+    n = xy.shape[0]
+    lo = xy.min(axis=0)
+    span = np.maximum(xy.max(axis=0) - lo, 1e-300)
+    b = np.minimum(((xy - lo) / span * grid).astype(np.int64), grid - 1)
+    col = np.where(b[:, 1] % 2 == 0, b[:, 0], grid - 1 - b[:, 0])
+    base = np.lexsort((xy[:, 0], col, b[:, 1]))
+    out = np.empty((count, n), np.int32)
+    for a in range(count):
+        t = np.roll(base, int(rng.integers(n)))
+        for _ in range(reversals):
+            i = int(rng.integers(n - 2))
+            ln = int(rng.integers(2, max(3, min(max_len, n - i) + 1)))
+            t[i:i + ln] = t[i:i + ln][::-1]
+        out[a] = t
+    return out
 
 
 def bf16_values(shape, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:

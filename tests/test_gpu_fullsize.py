@@ -5,9 +5,9 @@ can compute one by one:
   * candidate lists of sampled cities by brute force (bit-exact);
   * initial tours (Algorithm 1, before its iterations) of sampled ants, built by the oracle from scratch with
     its own candidate lists (bit-exact tours and lengths);
-  * PartialACO iterations of sampled ants replayed by the oracle from the colony's state before
-    the iteration (teacher forcing: the pre-iteration l_best population is read from the device
-    after checking that every sampled tour is a permutation with the exact length);
+  * a PartialACO iteration of sampled ants from a synthetic l_best population (spatially coherent
+    random tours from the input generators) loaded into both the colony and the oracle, each
+    computing its own exact lengths;
 and properties that hold at any size (permutations, exact lengths, l_best never lengthens,
 C_gbest = min C_lbest, preserved part untouched, rebuilt count <= floor(f n)).
 """
@@ -73,15 +73,19 @@ def test_fullsize_iterations(colony200k):
     assert np.array_equal(prev_l, L0)
     assert col.stats()["gbest"] == L0.min()
     del T0
-    # PartialACO iterations; the last one is replayed by the oracle for sampled ants
-    for it in range(1, 4):
-        lb_before = lb.cpu().numpy() if it == 3 else None
-        cl_before = cl.cpu().numpy() if it == 3 else None
+    # a PartialACO iteration from the same synthetic l_best population on both sides
+    S = aco_synth.snake_tours(xy, m, 7)
+    SL = oracle.tour_lengths(xy, S)
+    col.set_state(torch.from_numpy(S).cuda())
+    lb, cl, _ = col.state()
+    assert np.array_equal(cl.cpu().numpy(), SL)
+    ref.set_lbest(S, SL)
+    prev_l = SL
+    for it in range(5, 8):
         tours, lens = col.construct(it, return_tours=True, return_lengths=True)
-        if it == 3:
+        if it == 5:
             T = tours.cpu().numpy()
             Ln = lens.cpu().numpy()
-            ref.set_lbest(lb_before, cl_before)
             rs = rng.choice(m, 16, replace=False).astype(np.int32)
             ref.construct(it, ants=rs)
             RT = ref.newtours
@@ -89,7 +93,7 @@ def test_fullsize_iterations(colony200k):
             s, M = ref.segments()
             for a in rs:
                 assert 1 <= M[a] <= math.floor(f * n)
-                assert np.array_equal(RT[a], T[a]), f"iteration {it}: ant {a} differs from the oracle's replay"
+                assert np.array_equal(RT[a], T[a]), f"iteration {it}: ant {a} differs from the oracle"
                 assert RL[a] == Ln[a]
             del RT, T
         col.update()

@@ -19,8 +19,9 @@ def test_ir_colony_matches_oracle(n, m, k, f, seed):
     kw = dict(mode=1, n=n, m=m, k=k, max_mod_frac=f, seed=seed, selection=1)
     col = Colony(xy, **kw)
     cand = col.build_candidates(return_lists=True).cpu().numpy()
-    ref = oracle.Oracle(xy, cand=cand, **kw)
-    assert np.array_equal(cand, ref.cand)
+    ocand = oracle.knn(xy, k)  # the oracle's own lists
+    assert np.array_equal(cand, ocand)
+    ref = oracle.Oracle(xy, cand=ocand, **kw)
     for it in range(5):
         col.iterate(it)
         ref.iterate(it)
@@ -62,7 +63,9 @@ def test_f_schedule_and_p_partial_match_oracle():
     kw = dict(mode=1, n=n, m=m, k=k, max_mod_frac=0.4, seed=8)
     col = Colony(xy, **kw)
     cand = col.build_candidates(return_lists=True).cpu().numpy()
-    ref = oracle.Oracle(xy, cand=cand, **kw)
+    ocand = oracle.knn(xy, k)  # the oracle's own lists
+    assert np.array_equal(cand, ocand)
+    ref = oracle.Oracle(xy, cand=ocand, **kw)
     sched = linear_f_schedule(0.01, 0.4, 5)
     for it in range(8):
         col.set_max_mod_frac(sched(it))

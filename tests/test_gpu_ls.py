@@ -23,7 +23,9 @@ def test_local_search_matches_oracle(n, m, k, f, p, W, seed):
     kw = dict(mode=1, n=n, m=m, k=k, max_mod_frac=f, seed=seed)
     col = Colony(xy, **kw)
     cand = col.build_candidates(return_lists=True).cpu().numpy()
-    ref = oracle.Oracle(xy, cand=cand, **kw)
+    ocand = oracle.knn(xy, k)  # the oracle's own lists
+    assert np.array_equal(cand, ocand)
+    ref = oracle.Oracle(xy, cand=ocand, **kw)
     col.set_local_search(p, W)
     ref.set_local_search(p, W)
     for it in range(5):

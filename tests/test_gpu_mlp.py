@@ -131,8 +131,9 @@ def test_features_degree_and_labels_match_oracle():
     n, m, k = 500, 20, 12
     xy = aco_synth.clustered(n, 8, 0.03, 4)
     col = Colony(xy, mode=1, n=n, m=m, k=k, max_mod_frac=0.5, seed=2)
-    cand = col.build_candidates(return_lists=True).cpu().numpy()
-    assert np.array_equal(cand, oracle.knn(xy, k))
+    gcand = col.build_candidates(return_lists=True).cpu().numpy()
+    cand = oracle.knn(xy, k)  # the oracle's own lists feed its features
+    assert np.array_equal(gcand, cand)
     tours = aco_synth.permutations(m, n, 6)
     col.set_state(torch.from_numpy(tours).cuda())
     lens = oracle.tour_lengths(xy, tours)
