@@ -1254,7 +1254,9 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) construct_lbest_kernel(const
             if (feas && staged) {
                 const CandW* src = A.candw + (size_t)c * k;
                 CandW* dst = &stage[wb][lane][0];
-                for (int q = 0; q < k; q += 2) cp_async16(dst + q, src + q, keep_pol);
+#pragma unroll
+                for (int q = 0; q < STAGE_K; q += 2)
+                    if (q < k) cp_async16(dst + q, src + q, keep_pol);
             }
         }
         if (staged) cp_async_commit();
