@@ -872,6 +872,105 @@ __device__ __forceinline__ void load_remaining(const int* ul, const float2* uxy,
     }
 }
 
+// One pass over the remaining-city list (round 0 already loaded into id/p; the next round's loads
+// in flight while a round is processed): visited cities drop out (the list is compacted in
+// place) and the warp keeps, per lane, the two nearest cities at tau0 (d1 with city y1, d2s).
+__device__ __forceinline__ void scan_remaining(int* ul, float2* uxy, int& ucount, int lane, float2 q32,
+                                               const uint32_t* bits, int (&id)[8], float2 (&p)[8], float& d1,
+                                               float& d2s, int& y1) {
+    d1 = FLT_MAX;
+    d2s = FLT_MAX;
+    y1 = 0x7fffffff;
+    int cnt = 0;
+    const unsigned ltm = (1u << lane) - 1u;
+    for (int base = 0; base < ucount; base += 256) {
+        int idn[8];
+        float2 pn[8];
+        load_remaining(ul, uxy, base + 256, ucount, lane, idn, pn);
+        bool kp[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) kp[h] = id[h] >= 0 && !is_visited(bits, id[h]);
+        unsigned bl[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) bl[h] = __ballot_sync(FULL, kp[h]);
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const int pos = cnt + __popc(bl[h] & ltm);
+            cnt += __popc(bl[h]);
+            if (kp[h] && pos != base + 32 * h + lane) {
+                ul[pos] = id[h];
+                uxy[pos] = p[h];
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const float dx = __fsub_rn(p[h].x, q32.x), dy = __fsub_rn(p[h].y, q32.y);
+            const float v = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+            const bool lt1 = kp[h] && (v < d1 || (v == d1 && id[h] < y1));
+            const bool lt2 = kp[h] && v < d2s;
+            d2s = lt1 ? d1 : (lt2 ? v : d2s);
+            y1 = lt1 ? id[h] : y1;
+            d1 = lt1 ? v : d1;
+        }
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            id[h] = idn[h];
+            p[h] = pn[h];
+        }
+    }
+    ucount = cnt;
+}
+
+// FP32 estimates of the hashed cities (slots lane + 32 s, coordinates in hp) with their tau and of
+// the nearest remaining cities at tau0; the best estimate is returned when it wins by more than
+// the error bounds allow (the hash is emptied), else -1 (the hash is kept for hashed_exact).
+__device__ __forceinline__ int hashed_decision(const LbestArgs& A, BoostSmem& sh, int lane, float2 q32,
+                                               const int (&hx)[BHASH / 32], const float2 (&hp)[BHASH / 32],
+                                               float d1, float d2s, int y1) {
+    float w1 = -1.f, w2 = -1.f, dmin = FLT_MAX;
+    int x1 = 0x7fffffff;
+    // 3. the hashed cities with their tau
+#pragma unroll
+    for (int s4 = 0; s4 < BHASH / 32; ++s4) {
+        const int x = hx[s4];
+        if (x < 0) continue;
+        const float dx = __fsub_rn(hp[s4].x, q32.x), dy = __fsub_rn(hp[s4].y, q32.y);
+        const float d2f = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+        const unsigned long long Q = sh.hq[lane + 32 * s4];
+        const float tauf = __fadd_rn(A.tau0f, __fmul_rn(__ull2float_rn(Q), 0x1.0p-32f));
+        dmin = fminf(dmin, d2f);
+        top2_push(weight_f32(tauf, d2f, A.ia, A.ib), x, w1, x1, w2);
+    }
+    if (d1 < FLT_MAX) {
+        dmin = fminf(dmin, d1);
+        top2_push(__fmul_rn(A.tau0powf, weight_f32(1.f, d1, 0, A.ib)), y1, w1, x1, w2);
+        if (d2s < FLT_MAX) w2 = fmaxf(w2, __fmul_rn(A.tau0powf, weight_f32(1.f, d2s, 0, A.ib)));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const float ow1 = __shfl_xor_sync(FULL, w1, o), ow2 = __shfl_xor_sync(FULL, w2, o);
+        const int ox1 = __shfl_xor_sync(FULL, x1, o);
+        dmin = fminf(dmin, __shfl_xor_sync(FULL, dmin, o));
+        if (ow1 > w1 || (ow1 == w1 && ox1 < x1)) {
+            w2 = fmaxf(w1, ow2);
+            w1 = ow1;
+            x1 = ox1;
+        } else {
+            w2 = fmaxf(w2, ow1);
+        }
+    }
+    if (!(dmin >= 1e-30f) || !(w1 > 0.f) || !(w1 <= FLT_MAX)) return -1;
+    const float eps_d = __fdiv_rn(__fmul_rn(1.1f, d2_bound(dmin, A.coord_r)), dmin);
+    const float E = __fmul_rn(1.25f, __fadd_rn(__fmul_rn(0.5f * (float)A.ib + 0.5f, eps_d),
+                                               __fmul_rn((float)(A.ib + A.ia + 4), 0x1.0p-22f)));
+    if (!(E < 0.25f)) return -1;
+    if (__fmul_rn(w1, 1.f - E) > __fmul_rn(w2, 1.f + E)) {
+        bhash_clear(sh, lane);
+        return x1;
+    }
+    return -1;
+}
+
 // Exhausted step of a partial rebuild, FP32-screened as partial_choice_fast, with the boosted
 // cities aggregated in a shared-memory hash:
 //  1. the non-candidate entries of the rank row of `cur` (held in registers) are listed in `el`
@@ -962,88 +1061,10 @@ __device__ int partial_choice_hashed(const LbestArgs& A, int a, int cur, const u
         bhash_clear(sh, lane);
         return -2;
     }
-    float w1 = -1.f, w2 = -1.f, dmin = FLT_MAX;
-    int x1 = 0x7fffffff;
-    float d1 = FLT_MAX, d2s = FLT_MAX;  // the two nearest cities at tau0
-    int y1 = 0x7fffffff;
-    int cnt = 0;
-    const unsigned ltm = (1u << lane) - 1u;
-    for (int base = 0; base < ucount; base += 256) {
-        int idn[8];
-        float2 pn[8];
-        load_remaining(ul, uxy, base + 256, ucount, lane, idn, pn);
-        bool kp[8];
-#pragma unroll
-        for (int h = 0; h < 8; ++h) kp[h] = id[h] >= 0 && !is_visited(bits, id[h]);
-        unsigned bl[8];
-#pragma unroll
-        for (int h = 0; h < 8; ++h) bl[h] = __ballot_sync(FULL, kp[h]);
-#pragma unroll
-        for (int h = 0; h < 8; ++h) {
-            const int pos = cnt + __popc(bl[h] & ltm);
-            cnt += __popc(bl[h]);
-            if (kp[h] && pos != base + 32 * h + lane) {
-                ul[pos] = id[h];
-                uxy[pos] = p[h];
-            }
-        }
-#pragma unroll
-        for (int h = 0; h < 8; ++h) {
-            const float dx = __fsub_rn(p[h].x, q32.x), dy = __fsub_rn(p[h].y, q32.y);
-            const float v = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-            const bool lt1 = kp[h] && (v < d1 || (v == d1 && id[h] < y1));
-            const bool lt2 = kp[h] && v < d2s;
-            d2s = lt1 ? d1 : (lt2 ? v : d2s);
-            y1 = lt1 ? id[h] : y1;
-            d1 = lt1 ? v : d1;
-        }
-#pragma unroll
-        for (int h = 0; h < 8; ++h) {
-            id[h] = idn[h];
-            p[h] = pn[h];
-        }
-    }
-    ucount = cnt;
-    // 3. the hashed cities with their tau
-#pragma unroll
-    for (int s4 = 0; s4 < BHASH / 32; ++s4) {
-        const int x = hx[s4];
-        if (x < 0) continue;
-        const float dx = __fsub_rn(hp[s4].x, q32.x), dy = __fsub_rn(hp[s4].y, q32.y);
-        const float d2f = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-        const unsigned long long Q = sh.hq[lane + 32 * s4];
-        const float tauf = __fadd_rn(A.tau0f, __fmul_rn(__ull2float_rn(Q), 0x1.0p-32f));
-        dmin = fminf(dmin, d2f);
-        top2_push(weight_f32(tauf, d2f, A.ia, A.ib), x, w1, x1, w2);
-    }
-    if (d1 < FLT_MAX) {
-        dmin = fminf(dmin, d1);
-        top2_push(__fmul_rn(A.tau0powf, weight_f32(1.f, d1, 0, A.ib)), y1, w1, x1, w2);
-        if (d2s < FLT_MAX) w2 = fmaxf(w2, __fmul_rn(A.tau0powf, weight_f32(1.f, d2s, 0, A.ib)));
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        const float ow1 = __shfl_xor_sync(FULL, w1, o), ow2 = __shfl_xor_sync(FULL, w2, o);
-        const int ox1 = __shfl_xor_sync(FULL, x1, o);
-        dmin = fminf(dmin, __shfl_xor_sync(FULL, dmin, o));
-        if (ow1 > w1 || (ow1 == w1 && ox1 < x1)) {
-            w2 = fmaxf(w1, ow2);
-            w1 = ow1;
-            x1 = ox1;
-        } else {
-            w2 = fmaxf(w2, ow1);
-        }
-    }
-    if (!(dmin >= 1e-30f) || !(w1 > 0.f) || !(w1 <= FLT_MAX)) return -1;
-    const float eps_d = __fdiv_rn(__fmul_rn(1.1f, d2_bound(dmin, A.coord_r)), dmin);
-    const float E = __fmul_rn(1.25f, __fadd_rn(__fmul_rn(0.5f * (float)A.ib + 0.5f, eps_d),
-                                               __fmul_rn((float)(A.ib + A.ia + 4), 0x1.0p-22f)));
-    if (!(E < 0.25f)) return -1;
-    if (__fmul_rn(w1, 1.f - E) > __fmul_rn(w2, 1.f + E)) {
-        bhash_clear(sh, lane);
-        return x1;
-    }
-    return -1;
+    float d1, d2s;
+    int y1;
+    scan_remaining(ul, uxy, ucount, lane, q32, bits, id, p, d1, d2s, y1);
+    return hashed_decision(A, sh, lane, q32, hx, hp, d1, d2s, y1);
 }
 
 // Exact FP64 weights of the hashed cities (after partial_choice_hashed returned -1), then the

@@ -18,7 +18,7 @@ import pytest
 
 import aco_synth
 import oracle
-from tests.gpu_common import require_gpu
+from tests.gpu_common import exact_tour_lengths, require_gpu
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -59,7 +59,7 @@ def test_fullsize_iterations(colony200k):
     sample = rng.choice(m, 12, replace=False)
     for a in sample:
         assert np.array_equal(np.sort(T0[a]), np.arange(n))
-    assert np.array_equal(L0[sample], oracle.tour_lengths(xy, T0[sample]))
+    assert np.array_equal(L0[sample], exact_tour_lengths(xy, T0[sample]))
     ref = oracle.Oracle(xy, cand=ocand, **p)
     built = sample[:2].astype(np.int32)
     ref.construct(0, ants=built)
@@ -106,4 +106,4 @@ def test_fullsize_iterations(colony200k):
     chk = rng.choice(m, 16, replace=False)
     for a in chk:
         assert np.array_equal(np.sort(L[a]), np.arange(n))
-    assert np.array_equal(prev_l[chk], oracle.tour_lengths(xy, L[chk]))
+    assert np.array_equal(prev_l[chk], exact_tour_lengths(xy, L[chk]))
