@@ -46,7 +46,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="lbest200k",
-                    choices=sorted(aco_synth.WORKLOADS) + ["batch512", "learned20k", "schedule20k", "ls200k"])
+                    choices=sorted(aco_synth.WORKLOADS) + ["batch512", "learned20k", "schedule20k", "ls200k",
+                                                           "async200k"])
     ap.add_argument("--ants", type=int, default=0, help="override m (profiling of smaller cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -643,8 +644,56 @@ def run_ls(args):
     print(json.dumps(out))
 
 
+# ------------------------------------------------------------------ asynchronous sharing
+def run_async(args):
+    """Asynchronous l_best sharing (improved partial rebuilds commit inside the construction launch,
+    as in the paper's asynchronous CPU colony) against the synchronous iteration on the 200,000-city
+    workload (m = 1024, k = 16, f = 0.01): 100 iterations after the same initial tours, CUDA-event
+    time per iteration, decisions per second and the final C_gbest.  The asynchronous runs are not
+    reproducible, so three are taken."""
+    import torch
+
+    from paper_1709_03187_gb300 import Colony
+
+    torch.cuda.set_device(0)
+    params = dict(aco_synth.WORKLOADS["lbest200k"]["params"])
+    xy = aco_synth.make("lbest200k")
+    iters = 100
+    res = {}
+    for name, on, runs in (("synchronous", False, 1), ("asynchronous", True, 3)):
+        out = []
+        for _ in range(runs):
+            col = Colony(xy, **params)
+            col.build_candidates()
+            col.iterate(0)
+            col.set_async_share(on)
+            st0 = col.stats()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for it in range(1, iters + 1):
+                col.iterate(it)
+            e1.record()
+            torch.cuda.synchronize()
+            st = col.stats()
+            ms = e0.elapsed_time(e1)
+            out.append({"ms_per_iteration": round(ms / iters, 4),
+                        "decisions_per_s": round((st["decisions"] - st0["decisions"]) / (ms / 1e3), 1),
+                        "improved_per_iteration": round((st["improved"] - st0["improved"]) / iters, 1),
+                        "gbest": st["gbest"]})
+            col.close()
+        res[name] = out
+    out = {"metric": "ms per iteration, decisions/s and C_gbest after 100 iterations, asynchronous vs synchronous l_best sharing",
+           "workload": "async200k: n=200,000 clustered (200 clusters, sigma=0.005), k=16, m=1024, f=0.01",
+           "synchronous": res["synchronous"][0], "asynchronous": res["asynchronous"]}
+    print(json.dumps(out))
+
+
 def main():
     args = parse_args()
+    if args.workload == "async200k" and args.impl == "ours":
+        run_async(args)
+        return
     if args.workload == "ls200k" and args.impl == "ours":
         run_ls(args)
         return

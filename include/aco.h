@@ -169,6 +169,22 @@ aco_status aco_set_p_partial(aco_instance* inst, double p_partial);
  * update.  The first call with p > 0 allocates the working tours (8 n int32). */
 aco_status aco_set_local_search(aco_instance* inst, double p, int32_t window);
 
+/* Asynchronous l_best sharing (Section 3: the paper's CPU colony runs its ants asynchronously, so
+ * an ant's improved l_best, and the pheromone it implies, reach ants that are still building).
+ * on = 1: from the next aco_construct_tours on, an ant whose partial rebuild is strictly shorter
+ * than its l_best commits it inside the construction launch: the rebuilt l_best positions, the
+ * neighbour entries of the cities they touch, the integer pheromone of those entries' candidate
+ * edges (the ant keeps its deposit weight q_a of the iteration start) and the Eq. 1 weights of
+ * the touched cities' candidate rows.  Ants still building read whatever value each entry holds
+ * at the time (old or new).  Full constructions commit in aco_update_pheromone as before, and
+ * the update recomputes every weight from C_gbest, so the state after each update is the usual
+ * function of the l_best population; the tours depend on timing, so runs are not reproducible
+ * and have no oracle counterpart.  on = 0 (default) restores the synchronous iteration.
+ * LBEST mode, single colony (not an instance of a batch), local search off (ACO_ERR_STATE
+ * otherwise); not between construct and update.  The first call with on = 1 allocates the
+ * pheromone table (8 n k bytes) and fills it from the current l_best population (synchronises). */
+aco_status aco_set_async_share(aco_instance* inst, int32_t on);
+
 /* ------------------------------------------------------------------ batched colonies
  * Many independent instances of uneven size solved together: the same method and parameters
  * per instance (Section 3, Algorithm 1), with all of a batch's colonies advanced by single

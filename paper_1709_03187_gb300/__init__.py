@@ -27,6 +27,7 @@ __all__ = [
     "aco_mlp_backward", "aco_mlp_adam", "aco_mlp_train", "aco_mlp_destroy", "aco_edge_features", "aco_tour_labels",
     "aco_set_edge_scores", "EdgeScorer", "aco_set_max_mod_frac", "aco_set_p_partial", "linear_f_schedule",
     "aco_set_local_search",
+    "aco_set_async_share",
 ]
 
 from .batch import Batch  # noqa: E402
@@ -39,5 +40,5 @@ from ._ffi import (ACO_MLP_WEIGHTS, aco_batch_instance, aco_edge_features, aco_m
                    aco_mlp_backward, aco_mlp_create, aco_mlp_destroy, aco_mlp_forward, aco_mlp_get_weights,
                    aco_mlp_train, aco_set_edge_scores, aco_tour_labels)
 from .learned import EdgeScorer  # noqa: E402
-from ._ffi import aco_set_local_search, aco_set_max_mod_frac, aco_set_p_partial  # noqa: E402
+from ._ffi import aco_set_async_share, aco_set_local_search, aco_set_max_mod_frac, aco_set_p_partial  # noqa: E402
 from .colony import linear_f_schedule  # noqa: E402

@@ -92,6 +92,7 @@ def lib():
             "aco_set_max_mod_frac": (S, [V, ctypes.c_double]),
             "aco_set_p_partial": (S, [V, ctypes.c_double]),
             "aco_set_local_search": (S, [V, ctypes.c_double, I32]),
+            "aco_set_async_share": (S, [V, I32]),
             "aco_status_string": (ctypes.c_char_p, [S]),
             "aco_last_error": (ctypes.c_char_p, [V]),
         }
@@ -315,3 +316,7 @@ def aco_set_p_partial(h, p_partial: float):
 
 def aco_set_local_search(h, p: float, window: int = 500):
     _check(lib().aco_set_local_search(h, p, window), "aco_set_local_search", h)
+
+
+def aco_set_async_share(h, on: bool):
+    _check(lib().aco_set_async_share(h, 1 if on else 0), "aco_set_async_share", h)

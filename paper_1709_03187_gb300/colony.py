@@ -79,6 +79,11 @@ class Colony:
     def set_p_partial(self, p_partial: float):
         _ffi.aco_set_p_partial(self._h, p_partial)
 
+    def set_async_share(self, on: bool):
+        """Asynchronous l_best sharing (improved partial rebuilds commit inside the construction
+        launch; not reproducible run to run)."""
+        _ffi.aco_set_async_share(self._h, on)
+
     def iterate(self, iteration: int):
         _ffi.aco_construct_tours(self._h, iteration, None, None)
         _ffi.aco_update_pheromone(self._h)

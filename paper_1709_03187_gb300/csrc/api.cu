@@ -50,7 +50,7 @@ static void free_all(aco_instance* inst) {
                     inst->seg, inst->antit, inst->accq, inst->tau, inst->etab_d, inst->W64d, inst->W32d,
                     inst->tours, inst->succ_d, inst->pred_d, inst->counters, inst->errflag, inst->xy32,
                     inst->ulist, inst->uxy, inst->bel, inst->btx, inst->btq, inst->deg, inst->ghk, inst->ghq,
-                    inst->ls_buf, inst->ls_sel, inst->ls_imp, inst->fcnt, inst->ccnt, inst->csize};
+                    inst->ls_buf, inst->ls_sel, inst->ls_imp, inst->fcnt, inst->ccnt, inst->csize, inst->Qt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -356,6 +356,33 @@ extern "C" aco_status aco_get_state(aco_instance* inst, int32_t* lbest_out_dev, 
         if (tau_out_dev) cudaMemcpyAsync(tau_out_dev, inst->tau, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s);
     }
     return sync_and_check(inst, "get_state");
+}
+
+aco_status launch_reweight(aco_instance* inst);
+
+extern "C" aco_status aco_set_async_share(aco_instance* inst, int32_t on) {
+    if (!inst) return ACO_ERR_INVALID_ARG;
+    if (inst->p.mode != ACO_MODE_LBEST_PARTIAL) return set_err(inst, ACO_ERR_STATE, "set_async_share: LBEST mode only");
+    if (inst->in_batch) return set_err(inst, ACO_ERR_STATE, "set_async_share: not for an instance of a batch");
+    if (inst->constructed) return set_err(inst, ACO_ERR_STATE, "set_async_share: tours constructed, update pending");
+    if (on != 0 && on != 1) return set_err(inst, ACO_ERR_INVALID_ARG, "set_async_share: on must be 0 or 1");
+    if (on && inst->ls_p > 0.0)
+        return set_err(inst, ACO_ERR_STATE, "set_async_share: local search is on (the two exclude each other)");
+    if (on && !inst->Qt) {
+        if (cudaMalloc(&inst->Qt, sizeof(unsigned long long) * (size_t)inst->p.n * inst->p.k) != cudaSuccess) {
+            cudaGetLastError();
+            inst->Qt = nullptr;
+            return set_err(inst, ACO_ERR_OOM, "set_async_share: pheromone table allocation failed");
+        }
+        // the table starts as the integer pheromone of the current l_best population (zero before
+        // the first update); the rebuild keeps it so from then on
+        aco_status st = launch_reweight(inst);
+        if (st != ACO_OK) return st;
+        st = sync_and_check(inst, "set_async_share");
+        if (st != ACO_OK) return st;
+    }
+    inst->async_share = on;
+    return ACO_OK;
 }
 
 extern "C" aco_status aco_set_state(aco_instance* inst, const int32_t* lbest_dev, const double* tau_dev) {

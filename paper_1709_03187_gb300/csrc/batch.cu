@@ -108,6 +108,7 @@ extern "C" aco_status aco_batch_create(const double* xy_dev, const int32_t* n_ho
         q.seed = p->seed + (uint64_t)i;
         aco_instance* ins = nullptr;
         aco_status st = aco_create_instance(xy_dev + 2 * coff, &q, stream, &ins);
+        if (st == ACO_OK) ins->in_batch = true;
         if (st != ACO_OK) {
             free_batch(b);
             delete b;

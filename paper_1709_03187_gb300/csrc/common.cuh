@@ -219,6 +219,7 @@ struct RebuildArgs {
     double* W64;
     uint8_t* rowflag;
     int* errflag;
+    unsigned long long* Qt;  // also stores the integer pheromone Q_ir when not null
 };
 
 // ------------------------------------------------------------------ instance
@@ -286,6 +287,9 @@ struct aco_instance {
     int32_t* csize;        // ncoarse cities per block
     int32_t ncells, ncoarse, cgx, cgy;
     bool scored;           // candidate edges carry learned scores instead of eta^beta
+    int32_t async_share;   // partial rebuilds commit inside the construction launch
+    unsigned long long* Qt;  // n*k integer pheromone of the candidate edges (allocated with async_share)
+    bool in_batch;         // owned by a batch (advanced by the batch's launches only)
 
     // dense mode
     double* tau;           // n*n

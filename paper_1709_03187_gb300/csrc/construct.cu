@@ -70,6 +70,20 @@ struct LbestArgs {
     float2* __restrict__ uxy;
     unsigned long long* __restrict__ counters;
     int* __restrict__ errflag;
+    // asynchronous sharing: an improved partial rebuild commits inside the launch (these tables
+    // are then written while other ants read them)
+    int async_share;
+    unsigned long long* Qt;  // n*k integer pheromone of the candidate edges
+    double* clen;
+    unsigned long long* cfix_w;
+    int* lbest_w;
+    int* nb_w;
+    uint8_t* nbrank_w;
+    CandW* candw_w;
+    double* W64_w;
+    uint8_t* rowflag_w;
+    const double* etab;
+    const int* cand;
 };
 
 // Batched launches: ant slot -> (instance, ant); per-instance descriptors; device iteration.
@@ -1158,6 +1172,97 @@ __host__ __device__ inline size_t stage_bytes(int k) { return (k <= STAGE_K && !
 __host__ __device__ inline size_t boost_offset(int k) { return stage_bytes(k); }
 __host__ __device__ inline size_t bits_offset(int k) { return (boost_offset(k) + sizeof(BoostSmem) + 15) & ~(size_t)15; }
 
+// ---------------------------------------------------------------- asynchronous l_best sharing
+// Candidate rank of `other` in the list of city `c` (0xFF = not a candidate).
+__device__ __forceinline__ uint8_t cand_rank(const int* __restrict__ cand, int k, int c, int other) {
+    const int* row = cand + (size_t)c * k;
+    for (int r = 0; r < k; ++r)
+        if (row[r] == other) return (uint8_t)r;
+    return 0xFF;
+}
+
+// Moves ant a's weight q_a from the old to the new neighbour entry (c, side): the integer pheromone
+// of the old entry's candidate edge loses q_a, the new one's gains it (two's complement adds on
+// the 64-bit table, so the order of all ants' adds does not matter).
+__device__ __forceinline__ void move_entry(const LbestArgs& A, int a, int c, int side, int nbr, unsigned long long qa) {
+    const size_t e = ((size_t)c * A.m + a) * 2 + side;
+    const uint8_t ro = A.nbrank_w[e];
+    if (ro < (uint8_t)A.k) atomicAdd(&A.Qt[(size_t)c * A.k + ro], 0ull - qa);
+    const uint8_t rn = cand_rank(A.cand, A.k, c, nbr);
+    A.nb_w[e] = nbr;
+    A.nbrank_w[e] = rn;
+    if (rn < (uint8_t)A.k) atomicAdd(&A.Qt[(size_t)c * A.k + rn], qa);
+}
+
+// Asynchronous sharing (the paper's CPU colony runs its ants asynchronously, Section 3): a
+// partial rebuild strictly shorter than the ant's l_best replaces it at once, before the update
+// step: the rebuilt positions of l_best, the neighbour entries of the M + 2 cities they touch,
+// the integer pheromone of those entries' candidate edges (the ant keeps the weight q_a of the
+// iteration start until the update step recomputes every weight from C_gbest), and the Eq. 1
+// weights of the touched cities' rows, recomputed from the table.  Other ants read these values
+// while they construct; every value is one aligned 1-, 4- or 8-byte store, so a reader sees an
+// old or a new value.  The update step's commit then finds C_lbest equal to the new length and
+// leaves the ant alone.
+__device__ void async_commit(const LbestArgs& A, int a, const AntIter& it, const int* seg, int lane) {
+    const int n = A.n, k = A.k, M = it.M;
+    if (!(it.newlen < A.clen[a])) return;  // only this ant writes its C_lbest during the launch
+    const unsigned long long qa = A.q[a];
+    int* L = A.lbest_w + (size_t)a * n;
+    const int e = L[(it.s + it.P - 1) % n];  // last preserved city, followed by the segment
+    const int start = it.start;              // first preserved city, preceded by the segment
+    __syncwarp();
+    for (int t = lane; t < M; t += 32) L[(it.s + it.P + t) % n] = seg[t];
+    for (int t = lane; t < M + 2; t += 32) {
+        if (t < M) {
+            const int c = seg[t];
+            move_entry(A, a, c, 0, t == M - 1 ? start : seg[t + 1], qa);
+            move_entry(A, a, c, 1, t == 0 ? e : seg[t - 1], qa);
+        } else if (t == M) {
+            move_entry(A, a, e, 0, seg[0], qa);
+        } else {
+            move_entry(A, a, start, 1, seg[M - 1], qa);
+        }
+    }
+    __syncwarp();
+    // Eq. 1 weights of the touched rows: two rows per pass for k <= 16 (a half-warp each)
+    const int per = k <= 16 ? 2 : 1;
+    const int r = per == 2 ? (lane & 15) : lane;
+    const int half = per == 2 ? (lane >> 4) : 0;
+    const unsigned gmask = per == 2 ? (half ? 0xFFFF0000u : 0x0000FFFFu) : FULL;
+    for (int i0 = 0; i0 < M + 2; i0 += per) {
+        const int i = i0 + half;
+        const bool row = i < M + 2;
+        const int c = !row ? 0 : i < M ? seg[i] : i == M ? e : start;
+        bool flag = false;
+        float w32 = 0.f;
+        double wv = 0.0;
+        const bool act = row && r < k;
+        if (act) {
+            const size_t ix = (size_t)c * k + r;
+            const unsigned long long Q = __ldcg(A.Qt + ix);
+            const double tau = __dadd_rn(A.tau0, __dmul_rn(__ull2double_rn(Q), 0x1.0p-32));
+            wv = __dmul_rn(powr(tau, A.alpha), A.etab[ix]);
+            w32 = __double2float_rn(wv);
+            flag = !(w32 >= FLT_MIN && w32 <= FLT_MAX);
+        }
+        const bool fl = (__ballot_sync(FULL, flag) & gmask) != 0u;
+        if (act) {
+            const size_t ix = (size_t)c * k + r;
+            A.W64_w[ix] = wv;
+            A.candw_w[ix].w = fl ? -1.0f : w32;
+            if (r == 0) A.rowflag_w[c] = fl ? 1 : 0;
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        A.clen[a] = it.newlen;
+        A.cfix_w[2 * a] = it.fix_lo;
+        A.cfix_w[2 * a + 1] = it.fix_hi;
+        atomicAdd(&A.counters[CNT_IMPROVED], 1ull);
+    }
+    __syncwarp();
+}
+
 // One warp per ant.  Single colony: block b is ant b and the descriptor is the launch
 // parameter.  Batched colonies (BATCH): warp w of block b takes ant slot b * warps + w, which
 // names (instance, ant); the descriptor comes from the per-instance array and the iteration
@@ -1377,17 +1482,18 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) construct_lbest_kernel(const
     }
     acc_new = warp_sum_u128(acc_new);
     acc_old = warp_sum_u128(acc_old);
+    u128 total = acc_new;
+    if (partial) {
+        const u128 old = (((u128)A.cfix[2 * a + 1]) << 64) | A.cfix[2 * a];
+        total = old - acc_old + acc_new;
+    }
+    AntIter it;
+    it.s = s; it.P = P; it.M = M; it.start = start;
+    it.newlen = fix_to_len(total);
+    it.fix_lo = (unsigned long long)total;
+    it.fix_hi = (unsigned long long)(total >> 64);
+    if (!BATCH && A.async_share && partial) async_commit(A, a, it, seg, lane);
     if (lane == 0) {
-        u128 total = acc_new;
-        if (partial) {
-            const u128 old = (((u128)A.cfix[2 * a + 1]) << 64) | A.cfix[2 * a];
-            total = old - acc_old + acc_new;
-        }
-        AntIter it;
-        it.s = s; it.P = P; it.M = M; it.start = start;
-        it.newlen = fix_to_len(total);
-        it.fix_lo = (unsigned long long)total;
-        it.fix_hi = (unsigned long long)(total >> 64);
         A.antit[a] = it;
         atomicAdd(&A.counters[CNT_DECISIONS], (unsigned long long)steps);
         atomicAdd(&A.counters[CNT_FALLBACKS], nfall);
@@ -1417,6 +1523,9 @@ void fill_lbest_args(const aco_instance* inst, int32_t iteration, LbestArgs& A) 
     A.fcnt = inst->fcnt; A.ccnt = inst->ccnt; A.csize = inst->csize; A.ncells = inst->ncells;
     A.ncoarse = inst->ncoarse; A.cgx = inst->cgx; A.cgy = inst->cgy; A.uxy = inst->uxy;
     A.counters = inst->counters; A.errflag = inst->errflag;
+    A.async_share = inst->async_share && inst->Qt ? 1 : 0;
+    A.Qt = inst->Qt; A.clen = inst->clen; A.cfix_w = inst->cfix; A.lbest_w = inst->lbest; A.nb_w = inst->nb; A.nbrank_w = inst->nbrank;
+    A.candw_w = inst->candw; A.W64_w = inst->W64; A.rowflag_w = inst->rowflag; A.etab = inst->etab; A.cand = inst->cand;
 }
 
 size_t lbest_args_size() { return sizeof(LbestArgs); }

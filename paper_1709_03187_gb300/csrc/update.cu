@@ -302,6 +302,7 @@ __global__ void __launch_bounds__(256) rebuild_kernel(const __grid_constant__ Re
             if (!isfinite(wv)) atomicOr(R.errflag, DEVERR_NONFINITE);
             flag = !(w32 >= FLT_MIN && w32 <= FLT_MAX);
             R.W64[e] = wv;
+            if (R.Qt) R.Qt[e] = Q;
         }
         const unsigned fl = __ballot_sync(FULL, flag);
         // a row the FP32 screen cannot represent carries negative screen weights: the
@@ -327,6 +328,7 @@ void fill_rebuild_args(const aco_instance* inst, int use_ants, RebuildArgs& R) {
     R.n = p.n; R.m = p.m; R.k = p.k; R.tau0 = p.tau0; R.alpha = p.alpha; R.use_ants = use_ants; R.m_cap = p.m;
     R.nbrank = inst->nbrank; R.q = inst->q; R.etab = inst->etab; R.candw = inst->candw; R.W64 = inst->W64;
     R.rowflag = inst->rowflag; R.errflag = inst->errflag;
+    R.Qt = inst->Qt;
 }
 
 size_t rebuild_smem_bytes(int m_cap, int k, int warps) {
