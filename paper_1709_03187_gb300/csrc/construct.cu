@@ -1173,25 +1173,40 @@ __host__ __device__ inline size_t boost_offset(int k) { return stage_bytes(k); }
 __host__ __device__ inline size_t bits_offset(int k) { return (boost_offset(k) + sizeof(BoostSmem) + 15) & ~(size_t)15; }
 
 // ---------------------------------------------------------------- asynchronous l_best sharing
-// Candidate rank of `other` in the list of city `c` (0xFF = not a candidate).
-__device__ __forceinline__ uint8_t cand_rank(const int* __restrict__ cand, int k, int c, int other) {
-    const int* row = cand + (size_t)c * k;
-    for (int r = 0; r < k; ++r)
-        if (row[r] == other) return (uint8_t)r;
-    return 0xFF;
-}
-
-// Moves ant a's weight q_a from the old to the new neighbour entry (c, side): the integer pheromone
-// of the old entry's candidate edge loses q_a, the new one's gains it (two's complement adds on
-// the 64-bit table, so the order of all ants' adds does not matter).
-__device__ __forceinline__ void move_entry(const LbestArgs& A, int a, int c, int side, int nbr, unsigned long long qa) {
-    const size_t e = ((size_t)c * A.m + a) * 2 + side;
-    const uint8_t ro = A.nbrank_w[e];
-    if (ro < (uint8_t)A.k) atomicAdd(&A.Qt[(size_t)c * A.k + ro], 0ull - qa);
-    const uint8_t rn = cand_rank(A.cand, A.k, c, nbr);
-    A.nb_w[e] = nbr;
-    A.nbrank_w[e] = rn;
-    if (rn < (uint8_t)A.k) atomicAdd(&A.Qt[(size_t)c * A.k + rn], qa);
+// Moves ant a's weight q_a from the old to the new neighbour entries (c, 0) = succ and
+// (c, 1) = pred of city c (side < 0: both; else that side only): the integer pheromone of each old
+// entry's candidate edge loses q_a and each new one's gains it, as two's complement adds on the
+// 64-bit table (so the order of all ants' adds does not matter); a removal and an addition on
+// the same candidate edge cancel and are skipped.
+__device__ __forceinline__ void move_entries(const LbestArgs& A, int a, int c, int side, int succ, int pred,
+                                             unsigned long long qa) {
+    const int k = A.k;
+    const size_t e = ((size_t)c * A.m + a) * 2;
+    uint8_t o0 = 0xFF, o1 = 0xFF, n0 = 0xFF, n1 = 0xFF;
+    if (side < 0) {
+        const uint16_t old2 = *reinterpret_cast<const uint16_t*>(A.nbrank_w + e);
+        o0 = (uint8_t)(old2 & 0xFFu);
+        o1 = (uint8_t)(old2 >> 8);
+        ranks_of(A.cand, k, c, succ, pred, n0, n1);
+        A.nb_w[e] = succ;
+        A.nb_w[e + 1] = pred;
+        *reinterpret_cast<uint16_t*>(A.nbrank_w + e) = (uint16_t)(n0 | (n1 << 8));
+    } else {
+        o0 = A.nbrank_w[e + side];
+        const int nbr = side == 0 ? succ : pred;
+        n0 = rank_of(A.cand, k, c, nbr);
+        A.nb_w[e + side] = nbr;
+        A.nbrank_w[e + side] = n0;
+    }
+    if (o0 == n0) o0 = n0 = 0xFF;
+    else if (o0 == n1) o0 = n1 = 0xFF;
+    if (o1 == n0) o1 = n0 = 0xFF;
+    else if (o1 == n1) o1 = n1 = 0xFF;
+    unsigned long long* Qc = A.Qt + (size_t)c * k;
+    if (o0 < (uint8_t)k) atomicAdd(Qc + o0, 0ull - qa);
+    if (o1 < (uint8_t)k) atomicAdd(Qc + o1, 0ull - qa);
+    if (n0 < (uint8_t)k) atomicAdd(Qc + n0, qa);
+    if (n1 < (uint8_t)k) atomicAdd(Qc + n1, qa);
 }
 
 // Asynchronous sharing (the paper's CPU colony runs its ants asynchronously, Section 3): a
@@ -1200,9 +1215,9 @@ __device__ __forceinline__ void move_entry(const LbestArgs& A, int a, int c, int
 // the integer pheromone of those entries' candidate edges (the ant keeps the weight q_a of the
 // iteration start until the update step recomputes every weight from C_gbest), and the Eq. 1
 // weights of the touched cities' rows, recomputed from the table.  Other ants read these values
-// while they construct; every value is one aligned 1-, 4- or 8-byte store, so a reader sees an
-// old or a new value.  The update step's commit then finds C_lbest equal to the new length and
-// leaves the ant alone.
+// while they construct; every value is one aligned 1-, 2-, 4- or 8-byte store, so a reader sees
+// an old or a new value.  The update step's commit then finds C_lbest equal to the new length
+// and leaves the ant alone.
 __device__ void async_commit(const LbestArgs& A, int a, const AntIter& it, const int* seg, int lane) {
     const int n = A.n, k = A.k, M = it.M;
     if (!(it.newlen < A.clen[a])) return;  // only this ant writes its C_lbest during the launch
@@ -1213,44 +1228,44 @@ __device__ void async_commit(const LbestArgs& A, int a, const AntIter& it, const
     __syncwarp();
     for (int t = lane; t < M; t += 32) L[(it.s + it.P + t) % n] = seg[t];
     for (int t = lane; t < M + 2; t += 32) {
-        if (t < M) {
-            const int c = seg[t];
-            move_entry(A, a, c, 0, t == M - 1 ? start : seg[t + 1], qa);
-            move_entry(A, a, c, 1, t == 0 ? e : seg[t - 1], qa);
-        } else if (t == M) {
-            move_entry(A, a, e, 0, seg[0], qa);
-        } else {
-            move_entry(A, a, start, 1, seg[M - 1], qa);
-        }
+        if (t < M) move_entries(A, a, seg[t], -1, t == M - 1 ? start : seg[t + 1], t == 0 ? e : seg[t - 1], qa);
+        else if (t == M) move_entries(A, a, e, 0, seg[0], 0, qa);
+        else move_entries(A, a, start, 1, 0, seg[M - 1], qa);
     }
     __syncwarp();
-    // Eq. 1 weights of the touched rows: two rows per pass for k <= 16 (a half-warp each)
+    // Eq. 1 weights of the touched rows: two rows per group for k <= 16 (a half-warp each), four
+    // groups per pass so that their table reads are in flight together
     const int per = k <= 16 ? 2 : 1;
     const int r = per == 2 ? (lane & 15) : lane;
     const int half = per == 2 ? (lane >> 4) : 0;
     const unsigned gmask = per == 2 ? (half ? 0xFFFF0000u : 0x0000FFFFu) : FULL;
-    for (int i0 = 0; i0 < M + 2; i0 += per) {
-        const int i = i0 + half;
-        const bool row = i < M + 2;
-        const int c = !row ? 0 : i < M ? seg[i] : i == M ? e : start;
-        bool flag = false;
-        float w32 = 0.f;
-        double wv = 0.0;
-        const bool act = row && r < k;
-        if (act) {
-            const size_t ix = (size_t)c * k + r;
-            const unsigned long long Q = __ldcg(A.Qt + ix);
-            const double tau = __dadd_rn(A.tau0, __dmul_rn(__ull2double_rn(Q), 0x1.0p-32));
-            wv = __dmul_rn(powr(tau, A.alpha), A.etab[ix]);
-            w32 = __double2float_rn(wv);
-            flag = !(w32 >= FLT_MIN && w32 <= FLT_MAX);
+    for (int i0 = 0; i0 < M + 2; i0 += 4 * per) {
+        int c[4];
+        bool act[4];
+        unsigned long long Q[4];
+        double et[4];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const int i = i0 + g * per + half;
+            c[g] = i < M ? seg[i] : i == M ? e : start;
+            act[g] = i < M + 2 && r < k;
+            const size_t ix = (size_t)c[g] * k + r;
+            Q[g] = act[g] ? __ldcg(A.Qt + ix) : 0ull;
+            et[g] = act[g] ? A.etab[ix] : 0.0;
         }
-        const bool fl = (__ballot_sync(FULL, flag) & gmask) != 0u;
-        if (act) {
-            const size_t ix = (size_t)c * k + r;
-            A.W64_w[ix] = wv;
-            A.candw_w[ix].w = fl ? -1.0f : w32;
-            if (r == 0) A.rowflag_w[c] = fl ? 1 : 0;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const double tau = __dadd_rn(A.tau0, __dmul_rn(__ull2double_rn(Q[g]), 0x1.0p-32));
+            const double wv = __dmul_rn(powr(tau, A.alpha), et[g]);
+            const float w32 = __double2float_rn(wv);
+            const bool flag = act[g] && !(w32 >= FLT_MIN && w32 <= FLT_MAX);
+            const bool fl = (__ballot_sync(FULL, flag) & gmask) != 0u;
+            if (act[g]) {
+                const size_t ix = (size_t)c[g] * k + r;
+                A.W64_w[ix] = wv;
+                A.candw_w[ix].w = fl ? -1.0f : w32;
+                if (r == 0) A.rowflag_w[c[g]] = fl ? 1 : 0;
+            }
         }
     }
     __syncwarp();

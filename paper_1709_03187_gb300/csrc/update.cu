@@ -23,40 +23,6 @@
 
 #define FULL 0xffffffffu
 
-__device__ __forceinline__ uint8_t rank_of(const int* __restrict__ cand, int k, int city, int other) {
-    const int* row = cand + (size_t)city * k;
-    for (int r = 0; r < k; ++r)
-        if (row[r] == other) return (uint8_t)r;
-    return 0xFF;
-}
-
-// Candidate ranks of `succ` and `pred` in the list of `c` (0xFF = not a candidate).  For k a
-// multiple of 4 the row is read with 16-byte loads in one round and compared in registers.
-__device__ __forceinline__ void ranks_of(const int* __restrict__ cand, int k, int c, int succ, int pred, uint8_t& rs,
-                                         uint8_t& rp) {
-    rs = rp = 0xFF;
-    if ((k & 3) == 0 && k <= 32) {
-        const int4* row = reinterpret_cast<const int4*>(cand + (size_t)c * k);
-        int4 v[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-            if (4 * q < k) v[q] = __ldg(row + q);
-#pragma unroll
-        for (int q = 7; q >= 0; --q) {  // descending, so the lowest matching rank is kept
-            if (4 * q >= k) continue;
-            const int e[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
-#pragma unroll
-            for (int h = 3; h >= 0; --h) {
-                if (e[h] == succ) rs = (uint8_t)(4 * q + h);
-                if (e[h] == pred) rp = (uint8_t)(4 * q + h);
-            }
-        }
-        return;
-    }
-    rs = rank_of(cand, k, c, succ);
-    rp = rank_of(cand, k, c, pred);
-}
-
 __device__ __forceinline__ void set_neighbours(int* __restrict__ nb, uint8_t* __restrict__ nbrank,
                                                const int* __restrict__ cand, int m, int k, int a, int c, int succ,
                                                int pred) {
