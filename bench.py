@@ -254,7 +254,7 @@ def run_ours(args):
         e2e = run_e2e(args, xy, params, stream)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload.startswith("lbest"):
-        cpu = cpu_baseline_from_state(col, xy, params, it, args.cpu_sample)
+        cpu = cpu_baseline_oracle(xy, params, it, args.cpu_sample)
     col.close()
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "decisions/s", "n_gpus": world, "steps": args.steps,
@@ -324,21 +324,30 @@ def run_e2e(args, xy, params, stream):
                     "are those of the timed iterations only"}
 
 
-def cpu_baseline_from_state(col, xy, params, iteration, sample):
-    """The oracle timed on this host: one PartialACO iteration of `sample` ants of the same
-    colony (its l_best state taken after the GPU warm-up), with the pheromone rebuild over all m
-    ants; projected to the full colony as t_rebuild + (m / sample) * t_construct."""
+def oracle_start(xy, params, seeds=2):
+    """The oracle's own starting colony, built with no input from the device: candidate lists by
+    the exact x-sweep, initial tours of `seeds` ants, repeated over the m ants as their l_best,
+    and the pheromone rebuild (timed).  Returns (oracle, rebuild seconds)."""
     import oracle
 
-    lb, cl, _ = col.state()
-    lb = lb.cpu().numpy()
-    n, m, k = params["n"], params["m"], params["k"]
+    m, k = params["m"], params["k"]
     cand = oracle.knn_sweep(xy, k)
-    ref = oracle.Oracle(xy, cand=cand, **{kk: v for kk, v in params.items()})
-    ref.set_lbest(lb, cl.cpu().numpy())
+    ref = oracle.Oracle(xy, cand=cand, **params)
+    ref.construct(0, ants=np.arange(seeds, dtype=np.int32))  # oracle-built initial tours
+    T = ref.newtours[:seeds]
+    L = oracle.tour_lengths(xy, T)
+    ref.set_lbest(np.ascontiguousarray(T[np.arange(m) % seeds]), L[np.arange(m) % seeds])
     t0 = time.perf_counter()
-    ref.construct(iteration, ants=[])
-    t_rb = time.perf_counter() - t0
+    ref.construct(1, ants=[])
+    return ref, time.perf_counter() - t0
+
+
+def cpu_baseline_oracle(xy, params, iteration, sample):
+    """The oracle timed on this host: one PartialACO iteration of `sample` ants of its own colony
+    (oracle_start), with the pheromone rebuild over all m ants; projected to the full colony as
+    t_rebuild + (m / sample) * t_construct."""
+    ref, t_rb = oracle_start(xy, params)
+    m = params["m"]
     ants = np.random.default_rng(0).choice(m, size=min(sample, m), replace=False).astype(np.int32)
     ref.reset_counters()
     t0 = time.perf_counter()
@@ -348,9 +357,9 @@ def cpu_baseline_from_state(col, xy, params, iteration, sample):
     full_dec = dec * m / ants.size
     full_t = t_rb + t_cs * m / ants.size
     return {"value": round(full_dec / full_t, 1), "unit": "decisions/s", "cores": 1, "kind": "oracle",
-            "sample": f"one iteration (iteration {iteration}) of {ants.size} of the {m} ants from the colony's "
-                      f"state after warm-up, plus the full pheromone rebuild ({t_rb:.2f} s); projected "
-                      f"t_rebuild + (m/sample) t_construct = {full_t:.2f} s for {full_dec:.0f} decisions",
+            "sample": f"one iteration of {ants.size} of the {m} ants of the oracle's own colony (its initial "
+                      f"tours of 2 ants repeated as l_best), plus the full pheromone rebuild ({t_rb:.2f} s); "
+                      f"projected t_rebuild + (m/sample) t_construct = {full_t:.2f} s for {full_dec:.0f} decisions",
             "iterations_per_s": round(1.0 / full_t, 5)}
 
 
@@ -366,17 +375,8 @@ def run_reference(args):
     n, m, k = params["n"], params["m"], params["k"]
     xy = aco_synth.make(args.workload)
     t0 = time.perf_counter()
-    cand = oracle.knn_sweep(xy, k) if params["mode"] == 1 else None
     if params["mode"] == 1:
-        ref = oracle.Oracle(xy, cand=cand, **params)
-        seeds = 2
-        ref.construct(0, ants=np.arange(seeds, dtype=np.int32))  # oracle-built initial tours
-        T = ref.newtours[:seeds]
-        lb = np.ascontiguousarray(T[np.arange(m) % seeds])
-        ref.set_lbest(lb, oracle.tour_lengths(xy, lb))
-        t1 = time.perf_counter()
-        ref.construct(1, ants=[])
-        t_rb = time.perf_counter() - t1
+        ref, t_rb = oracle_start(xy, params)
     else:
         ref = oracle.Oracle(xy, **params)
         t_rb = 0.0
