@@ -47,7 +47,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="lbest200k",
                     choices=sorted(aco_synth.WORKLOADS) + ["batch512", "learned20k", "schedule20k", "ls200k",
-                                                           "async200k"])
+                                                           "async200k", "ir200k"])
     ap.add_argument("--ants", type=int, default=0, help="override m (profiling of smaller cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -568,8 +568,10 @@ def run_learned(args):
 def run_schedule(args):
     """The paper's proposed growing modification limit (Section 7) against a fixed one at
     n = 20,000 (the learned20k instances), m = 512, k = 20: 100 iterations with f = 0.1 fixed,
-    and 100 iterations with f growing linearly from 0.01 to 0.1 over the first 50.  Per seed: the
-    CUDA-event time of the iterations and the final C_gbest."""
+    100 iterations with f growing linearly from 0.01 to 0.1 over the first 50, and 100 iterations
+    at f = 0.1 where an ant rebuilds only part of its l_best with probability 0.95 and builds a
+    full tour otherwise (Table 4's setting).  Per seed: the CUDA-event time of the iterations and
+    the final C_gbest."""
     import torch
 
     from paper_1709_03187_gb300 import Colony, linear_f_schedule
@@ -580,10 +582,12 @@ def run_schedule(args):
     for s in (1, 2, 3):
         xy = aco_synth.clustered(n, 100, 0.01, 20_000 + s)
         res = {}
-        for name, sched in (("fixed", lambda t: 0.1), ("growing", linear_f_schedule(0.01, 0.1, 50))):
+        for name, sched, pp in (("fixed", lambda t: 0.1, 1.0), ("growing", linear_f_schedule(0.01, 0.1, 50), 1.0),
+                                ("partial95", lambda t: 0.1, 0.95)):
             col = Colony(xy, mode=1, n=n, m=m, k=k, max_mod_frac=0.1, seed=s)
             col.build_candidates()
             col.iterate(0)
+            col.set_p_partial(pp)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -595,15 +599,19 @@ def run_schedule(args):
             res[name] = (e0.elapsed_time(e1), col.stats()["gbest"])
             col.close()
         rows.append({"seed": s, "fixed_ms": round(res["fixed"][0], 1), "fixed_gbest": res["fixed"][1],
-                     "growing_ms": round(res["growing"][0], 1), "growing_gbest": res["growing"][1]})
-    out = {"metric": "C_gbest after 100 iterations and GPU time, growing vs fixed modification limit",
+                     "growing_ms": round(res["growing"][0], 1), "growing_gbest": res["growing"][1],
+                     "partial95_ms": round(res["partial95"][0], 1), "partial95_gbest": res["partial95"][1]})
+    out = {"metric": "C_gbest after 100 iterations and GPU time: growing vs fixed modification limit, and "
+                     "p_partial = 0.95 at the fixed limit",
            "workload": "schedule20k: n=20,000 clustered (100 clusters, sigma=0.01), k=20, m=512; f=0.1 fixed vs "
-                       "f from 0.01 to 0.1 over 50 iterations; 3 seeds",
+                       "f from 0.01 to 0.1 over 50 iterations vs f=0.1 with p_partial=0.95; 3 seeds",
            "per_seed": rows,
            "mean_fixed_gbest": float(np.mean([r["fixed_gbest"] for r in rows])),
            "mean_growing_gbest": float(np.mean([r["growing_gbest"] for r in rows])),
            "mean_fixed_ms": float(np.mean([r["fixed_ms"] for r in rows])),
-           "mean_growing_ms": float(np.mean([r["growing_ms"] for r in rows]))}
+           "mean_growing_ms": float(np.mean([r["growing_ms"] for r in rows])),
+           "mean_partial95_gbest": float(np.mean([r["partial95_gbest"] for r in rows])),
+           "mean_partial95_ms": float(np.mean([r["partial95_ms"] for r in rows]))}
     print(json.dumps(out))
 
 
@@ -641,6 +649,44 @@ def run_ls(args):
            "workload": "ls200k: n=200,000 clustered (200 clusters, sigma=0.005), k=16, m=1024, f=0.01",
            "plain": res["plain"], "local_search": res["local_search"],
            "time_ratio": round(res["local_search"]["ms_per_iteration"] / res["plain"]["ms_per_iteration"], 3)}
+    print(json.dumps(out))
+
+
+# ------------------------------------------------------------------ Independent Roulette
+def run_ir(args):
+    """Independent Roulette (the paper's Section 3 selection rule, argmax of tau^alpha eta^beta
+    times a uniform draw) against the Eq. 1 wheel on the 200,000-city workload (m = 1024, k = 16,
+    f = 0.01): 100 iterations after each colony's initial tours, CUDA-event time per iteration,
+    decisions per second and the final C_gbest."""
+    import torch
+
+    from paper_1709_03187_gb300 import Colony
+
+    torch.cuda.set_device(0)
+    params = dict(aco_synth.WORKLOADS["lbest200k"]["params"])
+    xy = aco_synth.make("lbest200k")
+    iters = 100
+    res = {}
+    for name, sel in (("eq1_wheel", 0), ("independent_roulette", 1)):
+        col = Colony(xy, selection=sel, **params)
+        col.build_candidates()
+        col.iterate(0)
+        st0 = col.stats()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for it in range(1, iters + 1):
+            col.iterate(it)
+        e1.record()
+        torch.cuda.synchronize()
+        st = col.stats()
+        ms = e0.elapsed_time(e1)
+        res[name] = {"ms_per_iteration": round(ms / iters, 4),
+                     "decisions_per_s": round((st["decisions"] - st0["decisions"]) / (ms / 1e3), 1),
+                     "initial_gbest": st0["gbest"], "gbest": st["gbest"]}
+        col.close()
+    out = {"metric": "ms per iteration, decisions/s and C_gbest after 100 iterations, Independent Roulette vs Eq. 1",
+           "workload": "ir200k: n=200,000 clustered (200 clusters, sigma=0.005), k=16, m=1024, f=0.01", **res}
     print(json.dumps(out))
 
 
@@ -693,6 +739,9 @@ def main():
     args = parse_args()
     if args.workload == "async200k" and args.impl == "ours":
         run_async(args)
+        return
+    if args.workload == "ir200k" and args.impl == "ours":
+        run_ir(args)
         return
     if args.workload == "ls200k" and args.impl == "ours":
         run_ls(args)

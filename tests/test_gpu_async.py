@@ -41,11 +41,14 @@ def _probs_equal(c1, c2, n, rng, trials=24):
         assert torch.equal(p1, p2), f"city {i}"
 
 
-def test_invariants_and_commits_inside_the_launch():
+@pytest.mark.parametrize("p_partial", [1.0, 0.5])
+def test_invariants_and_commits_inside_the_launch(p_partial):
+    """p_partial = 0.5 mixes partial rebuilds (committed in the launch) with full constructions
+    (committed by the update step)."""
     require_gpu()
     n, m, k = 2000, 64, 16
     xy = aco_synth.clustered(n, 10, 0.02, 3)
-    kw = dict(mode=1, n=n, m=m, k=k, max_mod_frac=0.2, seed=3)
+    kw = dict(mode=1, n=n, m=m, k=k, max_mod_frac=0.2, p_partial=p_partial, seed=3)
     col = _colony(xy, **kw)
     col.iterate(0)
     col.set_async_share(True)
