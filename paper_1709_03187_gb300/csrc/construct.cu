@@ -920,7 +920,9 @@ __device__ __forceinline__ void scan_remaining(int* ul, float2* uxy, int& ucount
         for (int h = 0; h < 8; ++h) {
             const float dx = __fsub_rn(p[h].x, q32.x), dy = __fsub_rn(p[h].y, q32.y);
             const float v = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-            const bool lt1 = kp[h] && (v < d1 || (v == d1 && id[h] < y1));
+            // equal distances need no order here: the runner-up then equals the nearest and the
+            // exact path (ties to the lowest index) decides
+            const bool lt1 = kp[h] && v < d1;
             const bool lt2 = kp[h] && v < d2s;
             d2s = lt1 ? d1 : (lt2 ? v : d2s);
             y1 = lt1 ? id[h] : y1;
@@ -960,18 +962,19 @@ __device__ __forceinline__ int hashed_decision(const LbestArgs& A, BoostSmem& sh
         top2_push(__fmul_rn(A.tau0powf, weight_f32(1.f, d1, 0, A.ib)), y1, w1, x1, w2);
         if (d2s < FLT_MAX) w2 = fmaxf(w2, __fmul_rn(A.tau0powf, weight_f32(1.f, d2s, 0, A.ib)));
     }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        const float ow1 = __shfl_xor_sync(FULL, w1, o), ow2 = __shfl_xor_sync(FULL, w2, o);
-        const int ox1 = __shfl_xor_sync(FULL, x1, o);
-        dmin = fminf(dmin, __shfl_xor_sync(FULL, dmin, o));
-        if (ow1 > w1 || (ow1 == w1 && ox1 < x1)) {
-            w2 = fmaxf(w1, ow2);
-            w1 = ow1;
-            x1 = ox1;
-        } else {
-            w2 = fmaxf(w2, ow1);
-        }
+    // warp top-2 by reductions over the bit patterns of non-negative floats (their order): the
+    // best estimate (ties: the lower city; one lane is taken as its holder) and the best of all
+    // the other estimates
+    {
+        const unsigned wb = __float_as_uint(fmaxf(w1, 0.f));
+        const unsigned wmax = __reduce_max_sync(FULL, wb);
+        const unsigned xmin = __reduce_min_sync(FULL, wb == wmax ? (unsigned)x1 : 0xFFFFFFFFu);
+        const unsigned win = __ballot_sync(FULL, wb == wmax && (unsigned)x1 == xmin);
+        const float rest = lane == __ffs(win) - 1 ? w2 : fmaxf(w1, w2);
+        w2 = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(fmaxf(rest, 0.f))));
+        w1 = __uint_as_float(wmax);
+        x1 = (int)xmin;
+        dmin = __uint_as_float(__reduce_min_sync(FULL, __float_as_uint(dmin)));
     }
     if (!(dmin >= 1e-30f) || !(w1 > 0.f) || !(w1 <= FLT_MAX)) return -1;
     const float eps_d = __fdiv_rn(__fmul_rn(1.1f, d2_bound(dmin, A.coord_r)), dmin);
@@ -987,11 +990,10 @@ __device__ __forceinline__ int hashed_decision(const LbestArgs& A, BoostSmem& sh
 
 // Exhausted step of a partial rebuild, FP32-screened as partial_choice_fast, with the boosted
 // cities aggregated in a shared-memory hash:
-//  1. the non-candidate entries of the rank row of `cur` (held in registers) are listed in `el`
-//     (shared memory: the staging buffer, idle at an exhausted step), their neighbour ids and ant
-//     weights gathered eight per lane, and the unvisited cities inserted into the hash with the
-//     summed weights of their entries (shared-memory atomics on integers: the order of the
-//     insertions does not matter);
+//  1. each lane finds the non-candidate entries among its bytes of the rank row of `cur` (held
+//     in registers), gathers their neighbour ids and ant weights eight per round, and inserts the
+//     unvisited cities into the hash with the summed weights of their entries (shared-memory
+//     atomics on integers: the order of the insertions does not matter);
 //  2. the coordinates of the hashed cities are requested, and one pass over the remaining-city
 //     list (the next round's loads in flight) compacts it and keeps, per lane, the two nearest
 //     cities at tau0; a hashed city also counts there at tau0, which only underestimates it;
@@ -1000,7 +1002,7 @@ __device__ __forceinline__ int hashed_decision(const LbestArgs& A, BoostSmem& sh
 // empty again); -1 when the estimates are too close (the hash is kept for hashed_exact); -2 when
 // the hash overflowed (emptied).
 __device__ int partial_choice_hashed(const LbestArgs& A, int a, int cur, const uint32_t* bits, int& ucount,
-                                     BoostSmem& sh, unsigned short* el, int lane, const RankRow& rr) {
+                                     BoostSmem& sh, int lane, const RankRow& rr) {
     int* ul = A.ulist + (size_t)a * A.ucap;
     float2* uxy = A.uxy + (size_t)a * A.ucap;
     const int* irow = A.nb + (size_t)cur * A.m * 2;
@@ -1020,24 +1022,20 @@ __device__ int partial_choice_hashed(const LbestArgs& A, int a, int cur, const u
             bm |= (unsigned long long)((m8 * 0x00204081u) >> 28) << (4 * (h * 4 + g));
         }
     }
-    int ne = 0;
-    int off = warp_offsets(__popcll(bm), ne, lane);
-    while (bm) {
-        const int b = __ffsll((long long)bm) - 1;
-        bm &= bm - 1;
-        const int word = b >> 2;
-        el[off++] = (unsigned short)((word >> 2) * 512 + lane * 16 + 4 * (word & 3) + (b & 3));
-    }
-    __syncwarp();
-    // 1b. gather and insert, 256 entries per round
+    // 1b. each lane gathers its own non-candidate entries, eight per round, and inserts them
     bool over = false;
-    for (int t0 = 0; t0 < ne; t0 += 256) {
+    while (__any_sync(FULL, bm != 0ull)) {
         int x8[8];
         unsigned long long q8[8];
 #pragma unroll
         for (int h = 0; h < 8; ++h) {
-            const int t = t0 + 32 * h + lane;
-            const int e = t < ne ? (int)el[t] : -1;
+            int e = -1;
+            if (bm) {
+                const int b = __ffsll((long long)bm) - 1;
+                bm &= bm - 1;
+                const int word = b >> 2;
+                e = (word >> 2) * 512 + lane * 16 + 4 * (word & 3) + (b & 3);
+            }
             x8[h] = e >= 0 ? __ldcs(irow + e) : -1;
             q8[h] = e >= 0 ? __ldg(A.q + (e >> 1)) : 0ull;
         }
@@ -1098,7 +1096,7 @@ __device__ void hashed_exact(const LbestArgs& A, BoostSmem& sh, int lane, double
 
 // Exhausted-list rule.  Returns the chosen city (uniform across the warp).
 __device__ int exhausted_choice(const LbestArgs& A, int a, int cur, double u, bool partial, int& ucount,
-                                const uint32_t* bits, BoostSmem& sh, unsigned short* el, int lane) {
+                                const uint32_t* bits, BoostSmem& sh, int lane) {
     __syncwarp();  // the previous city's visited bit (set at the top of the step) is visible
     const double qx = A.xy[2 * cur], qy = A.xy[2 * cur + 1];
     const double tau0pow = powr(A.tau0, A.alpha);
@@ -1111,8 +1109,8 @@ __device__ int exhausted_choice(const LbestArgs& A, int a, int cur, double u, bo
         RankRow rr;
         const bool pre = A.initialized && (A.m & 7) == 0 && A.m <= 1024;
         if (pre) load_rank_row(A, cur, lane, rr);
-        if (partial && A.ia >= 0 && A.ib >= 0 && pre && el) {
-            const int fast = partial_choice_hashed(A, a, cur, bits, ucount, sh, el, lane, rr);
+        if (partial && A.ia >= 0 && A.ib >= 0 && pre) {
+            const int fast = partial_choice_hashed(A, a, cur, bits, ucount, sh, lane, rr);
             if (fast >= 0) return fast;
             if (fast == -1) {  // near tie: exact weights of the near-nearest and of the hashed cities
                 remaining_argmax(A, a, cur, bits, ucount, lane, qx, qy, tau0pow, bw, bc);
@@ -1467,9 +1465,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) construct_lbest_kernel(const
                 counts_remove(A, a, seg, counted, t + 1, lane);
                 counted = t + 1;
             }
-            // no copies were issued this step (every candidate is visited): the staging buffer is free
-            j = exhausted_choice(A, a, cur, __shfl_sync(FULL, my_u, t & 31), partial, ucount, bits, boost,
-                                 staged ? reinterpret_cast<unsigned short*>(stage) : nullptr, lane);
+            j = exhausted_choice(A, a, cur, __shfl_sync(FULL, my_u, t & 31), partial, ucount, bits, boost, lane);
             rowp = A.candw + (size_t)j * k;
         }
         wb ^= 1;
