@@ -35,7 +35,7 @@ METRIC = "city decisions/s and ACO iterations/s at n=200K on 1 GB300; % of mem r
 # DRAM bytes (read + write) per decision of construct_lbest_kernel from one ncu capture of the
 # 200,000-city workload at m = 256 (57.9 MB for 251,025 decisions), valid for the source it was
 # taken on; the bench reports null traffic once construct.cu changes.
-CONSTRUCT_TRAFFIC = {"sha1_12": "9b33fe9b151b", "bytes_per_decision": 57813504.0 / 251025.5}
+CONSTRUCT_TRAFFIC = {"sha1_12": "7e7c4eb7dff0", "bytes_per_decision": 57964544.0 / 251025.5}
 L2_FLUSH_BYTES = 512 << 20  # > 126 MB L2
 
 

@@ -1095,8 +1095,10 @@ __device__ void hashed_exact(const LbestArgs& A, BoostSmem& sh, int lane, double
 }
 
 // Exhausted-list rule.  Returns the chosen city (uniform across the warp).
-__device__ int exhausted_choice(const LbestArgs& A, int a, int cur, double u, bool partial, int& ucount,
-                                const uint32_t* bits, BoostSmem& sh, int lane) {
+// staged: the candidate rows are staged (even k <= 16); the hashed step serves those colonies,
+// partial_choice_fast the others (measured faster for them).
+__device__ int exhausted_choice(const LbestArgs& A, int a, int cur, double u, bool partial, bool staged,
+                                int& ucount, const uint32_t* bits, BoostSmem& sh, int lane) {
     __syncwarp();  // the previous city's visited bit (set at the top of the step) is visible
     const double qx = A.xy[2 * cur], qy = A.xy[2 * cur + 1];
     const double tau0pow = powr(A.tau0, A.alpha);
@@ -1109,7 +1111,7 @@ __device__ int exhausted_choice(const LbestArgs& A, int a, int cur, double u, bo
         RankRow rr;
         const bool pre = A.initialized && (A.m & 7) == 0 && A.m <= 1024;
         if (pre) load_rank_row(A, cur, lane, rr);
-        if (partial && A.ia >= 0 && A.ib >= 0 && pre) {
+        if (partial && A.ia >= 0 && A.ib >= 0 && pre && staged) {
             const int fast = partial_choice_hashed(A, a, cur, bits, ucount, sh, lane, rr);
             if (fast >= 0) return fast;
             if (fast == -1) {  // near tie: exact weights of the near-nearest and of the hashed cities
@@ -1465,7 +1467,8 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) construct_lbest_kernel(const
                 counts_remove(A, a, seg, counted, t + 1, lane);
                 counted = t + 1;
             }
-            j = exhausted_choice(A, a, cur, __shfl_sync(FULL, my_u, t & 31), partial, ucount, bits, boost, lane);
+            j = exhausted_choice(A, a, cur, __shfl_sync(FULL, my_u, t & 31), partial, staged, ucount, bits, boost,
+                                 lane);
             rowp = A.candw + (size_t)j * k;
         }
         wb ^= 1;
