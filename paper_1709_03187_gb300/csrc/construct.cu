@@ -23,6 +23,11 @@
 //   * full construction: the nearest unvisited city is found exactly by a ring search over the
 //     city grid;
 // and the few unvisited l_best neighbours of city i get their exact boosted weight.
+//
+// Independent Roulette (selection = 1, Section 3): each unvisited candidate's exact weight times
+// its own Philox uniform, the largest product wins.  Asynchronous sharing (opt-in, Section 3):
+// an improved partial rebuild commits its l_best and moves its pheromone at the end of its own
+// construction, inside the launch (async_commit).
 #include <float.h>
 #include <math.h>
 
@@ -409,11 +414,10 @@ __device__ __forceinline__ float d2_bound(float d2, float R) {
 
 // Partial rebuild: argmax over the remaining discarded cities (compacted list, FP32 screen).
 // Pass 1 (eight loads per lane in flight) compacts the list in place (visited cities drop out)
-// and keeps, per lane, the two
-// smallest screened distances and where the smallest now sits.  Only cities whose screened
-// distance is within the error bound of the minimum can carry the largest weight; they get the
-// exact FP64 weight.  A second pass over the list is needed only when some lane holds two such
-// cities.
+// and keeps, per lane, the two smallest screened distances and where the smallest now sits.
+// Only cities whose screened distance is within the error bound of the minimum can carry the
+// largest weight; they get the exact FP64 weight.  A second pass over the list is needed only
+// when some lane holds two such cities.
 __device__ void remaining_argmax(const LbestArgs& A, int a, int cur, const uint32_t* bits, int& ucount, int lane,
                                  double qx, double qy, double tau0pow, double& bw, int& bc) {
     int* ul = A.ulist + (size_t)a * A.ucap;
