@@ -1409,28 +1409,50 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) construct_lbest_kernel(const
         int pick = -1;
         if (fmask && A.selection == 1) {
             // Independent Roulette: the candidate's exact weight times its own uniform; the
-            // largest positive product wins, ties to the lowest rank
-            double prod = 0.0;
+            // largest positive product wins, ties to the lowest rank.  Screen first: the staged
+            // FP32 weight times the FP32 uniform is within 4 * 2^-24 (relative) of the exact
+            // product, so a normal best screen product above every other one by the factor
+            // 1 + 2^-18 belongs to the exact winner; otherwise (a near tie, or a row the screen
+            // cannot represent) the exact FP64 products decide.
+            uint32_t xr = 0u;
             if (feas) {
-                const double w64 = A.W64[(size_t)cur * k + lane];
-                if (w64 > 0.0) {
-                    const Draw4 d = aco_draw(A.seed, 8u * (uint32_t)t + (uint32_t)(lane >> 2), a, iteration, PURPOSE_IR);
-                    const uint32_t xr = (lane & 3) == 0 ? d.x0 : (lane & 3) == 1 ? d.x1 : (lane & 3) == 2 ? d.x2 : d.x3;
-                    prod = __dmul_rn(w64, __dmul_rn(__dadd_rn(__uint2double_rn(xr), 0.5), 0x1.0p-32));
+                const Draw4 d = aco_draw(A.seed, 8u * (uint32_t)t + (uint32_t)(lane >> 2), a, iteration, PURPOSE_IR);
+                xr = (lane & 3) == 0 ? d.x0 : (lane & 3) == 1 ? d.x1 : (lane & 3) == 2 ? d.x2 : d.x3;
+            }
+            int p32 = -1;
+            if (!__any_sync(FULL, feas && !(w > 0.f))) {
+                const float uf = __fmul_rn(__fadd_rn(__uint2float_rn(xr), 0.5f), 0x1.0p-32f);
+                const unsigned key = feas ? __float_as_uint(__fmul_rn(w, uf)) : 0u;  // order of non-negative floats
+                const unsigned amax = __reduce_max_sync(FULL, key);
+                const unsigned win = __ballot_sync(FULL, feas && key == amax);
+                if (__popc(win) == 1 && amax >= __float_as_uint(FLT_MIN)) {
+                    const int wl = __ffs(win) - 1;
+                    const unsigned second = __reduce_max_sync(FULL, lane == wl ? 0u : key);
+                    if (__uint_as_float(amax) > __fmul_rn(__uint_as_float(second), 1.0f + 0x1.0p-18f)) p32 = wl;
                 }
             }
-            double bp = prod;
-            int bl = prod > 0.0 ? lane : 32;
+            if (p32 >= 0) {
+                pick = p32;
+            } else {
+                ++nres;
+                double prod = 0.0;
+                if (feas) {
+                    const double w64 = A.W64[(size_t)cur * k + lane];
+                    if (w64 > 0.0) prod = __dmul_rn(w64, __dmul_rn(__dadd_rn(__uint2double_rn(xr), 0.5), 0x1.0p-32));
+                }
+                double bp = prod;
+                int bl = prod > 0.0 ? lane : 32;
 #pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                const double ob = __shfl_xor_sync(FULL, bp, o);
-                const int ol = __shfl_xor_sync(FULL, bl, o);
-                if (ob > bp || (ob == bp && ol < bl)) {
-                    bp = ob;
-                    bl = ol;
+                for (int o = 16; o; o >>= 1) {
+                    const double ob = __shfl_xor_sync(FULL, bp, o);
+                    const int ol = __shfl_xor_sync(FULL, bl, o);
+                    if (ob > bp || (ob == bp && ol < bl)) {
+                        bp = ob;
+                        bl = ol;
+                    }
                 }
+                pick = bl < 32 ? bl : -1;
             }
-            pick = bl < 32 ? bl : -1;
         } else if (fmask) {
             float S = feas ? w : 0.f;
 #pragma unroll
