@@ -276,6 +276,10 @@ def run_ours(args):
                    "n": n, "m": m, "k": k, "parallelism": f"replicas x{world}" if world > 1 else "single colony",
                    "l2": "flushed (512 MB write) before every timed step, outside the events",
                    "decisions_per_step": decisions / args.steps,
+                   # every ant's new tour has n positions; those not decided this step stay in
+                   # place in l_best (the preserved part, never copied) or are a drawn start city
+                   "positions_per_step": float(m * n),
+                   "kept_positions_per_step": m * n - decisions / args.steps,
                    "fallbacks_per_step": (st_after["fallbacks"] - st_before["fallbacks"]) / args.steps,
                    "exact_resolves_per_step": (st_after["exact_resolves"] - st_before["exact_resolves"]) / args.steps,
                    "improved_per_step": (st_after["improved"] - st_before["improved"]) / args.steps,
