@@ -665,6 +665,72 @@ def run_ls(args):
     print(json.dumps(out))
 
 
+# ------------------------------------------------------------------ dense form (Section 2)
+def run_dense(args):
+    """The Section 2 form on its workload (dense100: n = 100 uniform cities, m = 100 ants; Eq. 1
+    over every unvisited city, then Eq. 2 and Eq. 3-5 on the n x n matrix): CUDA-event time of the
+    construction and of the update per iteration, decisions and iterations per second, the
+    construction's roofline (per decision the current city's FP32 weight row, 4 n bytes; per ant
+    its tour, 4 n bytes) and the update's (tau read and written, eta^beta read, FP64 and FP32
+    weights written: 36 n^2 bytes; tours, successors and predecessors: 12 m n bytes), and the
+    oracle's iterations timed on one host core."""
+    import torch
+
+    import oracle
+    from paper_1709_03187_gb300 import Colony
+
+    torch.cuda.set_device(0)
+    params = dict(aco_synth.WORKLOADS["dense100"]["params"])
+    xy = aco_synth.make("dense100")
+    n, m = params["n"], params["m"]
+    col = Colony(xy, **params)
+    col.build_candidates()
+    for it in range(args.warmup):
+        col.iterate(it)
+    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(args.steps)]
+    st0 = col.stats()
+    torch.cuda.synchronize()
+    for i, (e0, e1, e2) in enumerate(ev):
+        e0.record()
+        col.construct(args.warmup + i)
+        e1.record()
+        col.update()
+        e2.record()
+    torch.cuda.synchronize()
+    st = col.stats()
+    t_con = sum(a.elapsed_time(b) for a, b, _ in ev) / 1e3
+    t_upd = sum(b.elapsed_time(c) for _, b, c in ev) / 1e3
+    col.close()
+    dec = st["decisions"] - st0["decisions"]
+    hbm_peak, peak_kind = read_peaks()
+    c_bytes = (dec * 4 * n + m * 4 * n) / args.steps
+    u_bytes = 36 * n * n + 12 * m * n
+    c_gbs = c_bytes / (t_con / args.steps) / 1e9
+    u_gbs = u_bytes / (t_upd / args.steps) / 1e9
+    ref = oracle.Oracle(xy, **params)
+    ref.reset_counters()
+    t0 = time.perf_counter()
+    for it in range(3):
+        ref.iterate(it)
+    t_or = time.perf_counter() - t0
+    dec_or = ref.counters()["decisions"]
+    out = {"metric": "decisions/s and iterations/s, dense Section 2 form", "workload":
+           "dense100: n=100 uniform, m=100, alpha=1, beta=2, rho=0.5, tau0=1 (Eq. 1 over all unvisited; Eq. 2, 3-5)",
+           "value": round(dec / (t_con + t_upd), 1), "unit": "decisions/s",
+           "iterations_per_s": round(args.steps / (t_con + t_upd), 1), "steps": args.steps, "warmup": args.warmup,
+           "ms_construct": round(t_con / args.steps * 1e3, 4), "ms_update": round(t_upd / args.steps * 1e3, 4),
+           "roofline": {"bound": "hbm", "peak": hbm_peak, "unit": "GB/s", "peak_source": f"{peak_kind} hbm_gbs",
+                        "construct_dense_kernel": {"alg_bytes": c_bytes, "achieved": round(c_gbs, 2),
+                                                   "frac": round(c_gbs / hbm_peak, 6)},
+                        "update (dense_tau + dense_weights)": {"alg_bytes": u_bytes, "achieved": round(u_gbs, 2),
+                                                               "frac": round(u_gbs / hbm_peak, 6)},
+                        "note": "the whole state (80 KB tau) is L2-resident; one block per ant and a few "
+                                "launches per iteration: launch- and latency-bound"},
+           "cpu_baseline": {"value": round(dec_or / t_or, 1), "unit": "decisions/s", "cores": 1,
+                            "kind": "oracle", "sample": "3 full iterations of the oracle's own dense colony"}}
+    print(json.dumps(out))
+
+
 # ------------------------------------------------------------------ Independent Roulette
 def run_ir(args):
     """Independent Roulette (the paper's Section 3 selection rule, argmax of tau^alpha eta^beta
@@ -752,6 +818,9 @@ def main():
     args = parse_args()
     if args.workload == "async200k" and args.impl == "ours":
         run_async(args)
+        return
+    if args.workload == "dense100" and args.impl == "ours":
+        run_dense(args)
         return
     if args.workload == "ir200k" and args.impl == "ours":
         run_ir(args)
