@@ -1,0 +1,33 @@
+"""Host-side logic of bench.py that needs no GPU: the key of the stored construction traffic.
+
+The ncu traffic figure is valid for the kernel code it was captured on.  bench.py keys it to a
+hash of construct.cu without comments and blank lines: an edit of comments keeps the key, an
+edit of code changes it (and the bench then reports null traffic)."""
+import importlib.util
+import os
+import shutil
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_code_hash_ignores_comments_and_blank_lines_only(tmp_path):
+    b = _bench()
+    csrc = tmp_path / "paper_1709_03187_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    src = os.path.join(ROOT, "paper_1709_03187_gb300", "csrc", "construct.cu")
+    shutil.copy(src, csrc / "construct.cu")
+    b.ROOT = str(tmp_path)
+    h0 = b.code_sha1("construct.cu")
+    text = (csrc / "construct.cu").read_text()
+    (csrc / "construct.cu").write_text("// a new header comment\n\n" + text.replace("\n", "  // note\n", 3))
+    assert b.code_sha1("construct.cu") == h0
+    (csrc / "construct.cu").write_text(text.replace("#define FULL 0xffffffffu", "#define FULL 0xfffffffeu"))
+    assert b.code_sha1("construct.cu") != h0
+
