@@ -124,6 +124,8 @@ def test_dense_probabilities_within_1e5():
     (40, 1, 6, 0.5, 8, 1.0, 0),      # a single ant
     (60, 6, 1, 0.5, 6, 1.0, 0),      # one candidate: nearly every step is an exhausted step
     (90, 5, 2, 1.0, 6, 0.5, 1),      # two candidates, the Eq. 1 wheel over all unvisited
+    (600, 1032, 8, 0.3, 4, 1.0, 0),  # m > 1024: rebuild weights from shared memory, rank rows in blocks
+    (300, 1030, 6, 0.5, 3, 1.0, 0),  # m > 1024 and not a multiple of 8: the scalar rank-row paths
 ])
 def test_partialaco_iterations_bit_exact(n, m, k, f, iters, p_partial, fallback):
     xy = aco_synth.clustered(n, max(1, n // 50), 0.02, n + m)
