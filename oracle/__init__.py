@@ -100,6 +100,7 @@ def lib():
             "or_ls_moves": (ctypes.c_int64, [P]),
             "or_two_opt_windowed": (ctypes.c_int, [ctypes.c_int, f64p, i32p, ctypes.c_int, ctypes.c_int]),
             "or_set_p_partial": (None, [P, ctypes.c_double]),
+            "or_exhausted_step": (ctypes.c_int, [P, ctypes.c_int, u8p, ctypes.c_double, ctypes.c_void_p]),
             "or_ir_pick": (ctypes.c_int, [f64p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                           ctypes.c_uint32]),
         }
@@ -282,9 +283,11 @@ class Oracle:
         return out
 
     def counters(self) -> dict:
-        out = np.zeros(3, np.int64)
+        """decisions, exhausted-list steps (fallbacks), weights evaluated (scans), and exhausted-list
+        picks whose pheromone lies above tau0 (boosted: an l_best neighbour outside the list)."""
+        out = np.zeros(4, np.int64)
         lib().or_get_counters(self._h, out)
-        return dict(decisions=int(out[0]), fallbacks=int(out[1]), scans=int(out[2]))
+        return dict(decisions=int(out[0]), fallbacks=int(out[1]), scans=int(out[2]), boosted=int(out[3]))
 
     def reset_counters(self):
         lib().or_reset_counters(self._h)
@@ -327,6 +330,14 @@ class Oracle:
         if not np.all(np.isfinite(s)) or not np.all(s > 0):
             raise ValueError("edge scores must be finite and > 0")
         lib().or_set_edge_scores(self._h, s.ctypes.data)
+
+    def exhausted_step(self, i: int, visited: np.ndarray, u: float = 0.0):
+        """The exhausted-list rule at city i (mode 1) for the given visited set and draw u, as a
+        construction applies it: (city picked, weight of every city with 0 for visited ones)."""
+        v = np.ascontiguousarray(visited, np.uint8)
+        w = np.zeros(self.n, np.float64)
+        j = lib().or_exhausted_step(self._h, i, v, float(u), w.ctypes.data)
+        return int(j), w
 
     def step_probs(self, i: int, visited: np.ndarray):
         """Eq. 1 probabilities at city i; returns (probs, exhausted)."""

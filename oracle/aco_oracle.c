@@ -204,6 +204,7 @@ typedef struct {
     int64_t ls_moves;
     /* counters */
     int64_t decisions, fallbacks, scans;
+    int64_t boosted; /* exhausted-list picks with pheromone above tau0 */
     /* scratch */
     unsigned char* visited; /* n */
 } or_state;
@@ -353,9 +354,49 @@ int or_ir_pick(const double* w, int k, uint64_t seed, uint32_t t, uint32_t ant, 
     return best;
 }
 
+/* Weight tau_ij^alpha eta_ij^beta of the edge (i, j) with tau_ij taken from the whole l_best
+ * population (Section 3): the weight Eq. 1 gives an edge once the candidate list is exhausted. */
+static double any_weight(const or_state* st, int i, int j) {
+    double tau = tau_from_Q(st, Q_any(st, i, j));
+    return or_powr(tau, st->p.alpha) * eta_pow(st->xy, i, j, st->p.beta);
+}
+
+/* The exhausted-list rule at city i over the unvisited cities (st->visited): the argmax of the
+ * weight, ties to the lowest index (fallback 0), or the Eq. 1 wheel over every unvisited city in
+ * index order (fallback 1, the ordinary rule of Section 6).  Counts the picks whose pheromone lies
+ * above tau0 (an l_best neighbour of i outside its candidate list). */
+static int exhausted_pick(or_state* st, int i, double u) {
+    const or_params* p = &st->p;
+    int n = p->n;
+    int pick = -1;
+    if (p->fallback == 0) {
+        double bw = -1.0;
+        for (int j = 0; j < n; ++j) {
+            if (st->visited[j]) continue;
+            st->scans++;
+            double wj = any_weight(st, i, j);
+            if (wj > bw) { bw = wj; pick = j; }
+        }
+    } else {
+        double* wa = (double*)malloc(sizeof(double) * (size_t)n);
+        int lowest = -1;
+        for (int j = 0; j < n; ++j) {
+            if (st->visited[j]) { wa[j] = 0.0; continue; }
+            if (lowest < 0) lowest = j;
+            st->scans++;
+            wa[j] = any_weight(st, i, j);
+        }
+        pick = wheel(wa, n, u);
+        free(wa);
+        if (pick < 0) pick = lowest;
+    }
+    if (pick >= 0 && Q_any(st, i, pick) > 0) st->boosted++;
+    return pick;
+}
+
 static int decide_cand(or_state* st, int ant, int i, uint32_t t, uint32_t iteration) {
     const or_params* p = &st->p;
-    int n = p->n, k = p->k;
+    int k = p->k;
     uint32_t x[4];
     draw(p->seed, t, (uint32_t)ant, iteration, 0, x);
     double u = or_u53(x[0], x[1]);
@@ -372,30 +413,7 @@ static int decide_cand(or_state* st, int ant, int i, uint32_t t, uint32_t iterat
     if (r >= 0) return row[r];
     /* every candidate visited */
     st->fallbacks++;
-    if (p->fallback == 0) {
-        int best = -1;
-        double bw = -1.0;
-        for (int j = 0; j < n; ++j) {
-            if (st->visited[j]) continue;
-            st->scans++;
-            double tau = tau_from_Q(st, Q_any(st, i, j));
-            double wj = or_powr(tau, p->alpha) * eta_pow(st->xy, i, j, p->beta);
-            if (wj > bw) { bw = wj; best = j; }
-        }
-        return best;
-    }
-    double* wa = (double*)malloc(sizeof(double) * (size_t)n);
-    int lowest = -1;
-    for (int j = 0; j < n; ++j) {
-        if (st->visited[j]) { wa[j] = 0.0; continue; }
-        if (lowest < 0) lowest = j;
-        st->scans++;
-        double tau = tau_from_Q(st, Q_any(st, i, j));
-        wa[j] = or_powr(tau, p->alpha) * eta_pow(st->xy, i, j, p->beta);
-    }
-    int j = wheel(wa, n, u);
-    free(wa);
-    return j >= 0 ? j : lowest;
+    return exhausted_pick(st, i, u);
 }
 
 /* One decision at city i (dense mode, Eq. 1 over every unvisited city in index order). */
@@ -623,10 +641,10 @@ void or_get_etab(const or_state* st, double* out) {
     if (st->p.mode == 0) memcpy(out, st->etab_d, sizeof(double) * (size_t)st->p.n * st->p.n);
     else memcpy(out, st->etab, sizeof(double) * (size_t)st->p.n * st->p.k);
 }
-void or_get_counters(const or_state* st, int64_t* out3) {
-    out3[0] = st->decisions; out3[1] = st->fallbacks; out3[2] = st->scans;
+void or_get_counters(const or_state* st, int64_t* out4) {
+    out4[0] = st->decisions; out4[1] = st->fallbacks; out4[2] = st->scans; out4[3] = st->boosted;
 }
-void or_reset_counters(or_state* st) { st->decisions = st->fallbacks = st->scans = 0; }
+void or_reset_counters(or_state* st) { st->decisions = st->fallbacks = st->scans = st->boosted = 0; }
 int or_initialized(const or_state* st) { return st->initialized; }
 
 /* Candidate-edge weights tau^alpha * eta^beta of the current l_best population (n*k), i.e.
@@ -684,6 +702,20 @@ int or_step_probs(or_state* st, int i, const unsigned char* visited, double* out
     if (total == 0.0) return 1;
     for (int r = 0; r < k; ++r) out[r] = out[r] / total;
     return 0;
+}
+
+/* The exhausted-list rule (Section 6's fallback to the ordinary rule, with the Section 3
+ * pheromone of the l_best population) at city i for the unvisited set `visited` (1 = visited)
+ * and the draw u (used by fallback 1): the city picked, exactly as a construction picks it.
+ * w_out (n entries, may be NULL): the weight of every unvisited city, 0 for visited ones. */
+int or_exhausted_step(or_state* st, int i, const unsigned char* visited, double u, double* w_out) {
+    if (st->p.mode != 1) return -1;
+    lbest_pheromone(st);
+    int n = st->p.n;
+    memcpy(st->visited, visited, (size_t)n);
+    if (w_out)
+        for (int j = 0; j < n; ++j) w_out[j] = visited[j] ? 0.0 : any_weight(st, i, j);
+    return exhausted_pick(st, i, u);
 }
 
 /* ------------------------------------------------------------------ large-n helpers */
