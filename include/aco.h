@@ -221,14 +221,15 @@ void aco_batch_destroy(aco_batch* b);
 
 /* Candidate lists (the same exact lists as aco_build_candidates) for callers that cannot allocate
  * device memory.  The paper has no counterpart: this is a deployment variant of the library.
- * The working memory is a fixed array inside the library (about 1.8 MB per GPU, held until the
+ * The working memory is a fixed array inside the library (1,966,080 bytes per GPU, held until the
  * process exits); the caller passes only its input and output buffers, and nothing is allocated.
  * xy_dev: n*2 FP64 device coordinates; cand_out_dev: n*k int32 device output (row i = the k
  * nearest other cities of city i, key (d^2, index) ascending).  n <= 65536 (larger n returns
- * ACO_ERR_INVALID_ARG), 1 <= k <= min(32, n-1).  The first call on a device looks up the array's
- * device address (make that call before any stream capture).  All calls share the array and it
- * keeps the last call's contents; calls that overlap on the GPU race and must be serialised by the
- * caller.  Synchronises the stream; coincident or non-finite cities give ACO_ERR_INVALID_ARG. */
+ * ACO_ERR_INVALID_ARG), 1 <= k <= min(32, n-1).  The first call on a device (and the first after
+ * the device's context was reset) looks up the array's device address (make that call before any
+ * stream capture).  All calls share the array and it keeps the last call's contents; calls that
+ * overlap on the GPU race and must be serialised by the caller.  Synchronises the stream;
+ * coincident or non-finite cities give ACO_ERR_INVALID_ARG. */
 aco_status aco_build_candidates_noalloc(const double* xy_dev, int32_t n, int32_t k, int32_t* cand_out_dev,
                                         void* stream);
 

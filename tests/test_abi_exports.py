@@ -19,7 +19,7 @@ def _declared():
 def test_header_declares_the_boundary():
     names = _declared()
     for required in ["aco_create_instance", "aco_build_candidates", "aco_construct_tours", "aco_update_pheromone",
-                     "aco_tour_lengths", "aco_destroy_instance"]:
+                     "aco_tour_lengths", "aco_destroy_instance", "aco_build_candidates_noalloc"]:
         assert required in names
 
 

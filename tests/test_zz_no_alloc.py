@@ -30,7 +30,9 @@ def test_noalloc_matches_regular_on_two_calls_in_a_row():
     require_gpu()
     from paper_1709_03187_gb300 import aco_build_candidates_noalloc
 
-    cases = [(aco_synth.clustered(20_000, 40, 0.01, 5), 16), (aco_synth.uniform(3_001, 6), 20)]
+    # the largest size the array holds first, then a smaller one that reuses what it left behind
+    cases = [(aco_synth.uniform(65_536, 8), 8), (aco_synth.clustered(20_000, 40, 0.01, 5), 16),
+             (aco_synth.uniform(3_001, 6), 20)]
     for xy, k in cases:
         n = xy.shape[0]
         dev = torch.from_numpy(xy).cuda()
@@ -57,3 +59,15 @@ def test_noalloc_rejects_what_its_array_cannot_hold():
         aco_build_candidates_noalloc(dev, 100, 8, out)
     with pytest.raises(AcoError):
         aco_build_candidates_noalloc(dev, 100, 33, torch.empty((100, 33), dtype=torch.int32, device="cuda"))
+    # non-finite coordinates are reported (the grid is then a unit box and every index clamped)
+    for bad in (float("nan"), float("inf")):
+        xy = aco_synth.uniform(100, 2)
+        xy[11, 1] = bad
+        with pytest.raises(AcoError) as e:
+            aco_build_candidates_noalloc(torch.from_numpy(xy).cuda(), 100, 8, out)
+        assert e.value.status == 1
+    # and a valid call right after the rejected ones gives the regular lists again
+    xy = aco_synth.uniform(500, 3)
+    good = torch.empty((500, 8), dtype=torch.int32, device="cuda")
+    aco_build_candidates_noalloc(torch.from_numpy(xy).cuda(), 500, 8, good)
+    assert torch.equal(good, _regular(xy, 8))
