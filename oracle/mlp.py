@@ -100,15 +100,23 @@ def labels(tour: np.ndarray, cand: np.ndarray) -> np.ndarray:
     return out
 
 
-def forward(wflat, X):
-    """z, h1, h2 and the pre-activations a1, a2 of every row, in FP64."""
+def forward(wflat, X, round_hidden: bool = False):
+    """z, h1, h2 and the pre-activations a1, a2 of every row, in FP64.
+
+    round_hidden: round h1 and h2 to BF16 after their FP64 sums, as the network of the learned
+    proposal is defined (BF16 weights and activations); the default keeps them exact (the
+    differentiable network the finite-difference pins check)."""
     W1, W2, w3 = split(wflat)
     X = np.asarray(X, np.float64)
     a1 = X @ W1.T
     h1 = np.maximum(a1, 0.0)
+    if round_hidden:
+        h1 = bf16_round(h1)
     h1[:, H - 1] = 1.0
     a2 = h1 @ W2.T
     h2 = np.maximum(a2, 0.0)
+    if round_hidden:
+        h2 = bf16_round(h2)
     h2[:, H - 1] = 1.0
     z = h2 @ w3
     return z, h1, h2, a1, a2
@@ -131,16 +139,100 @@ def z_error_bound(wflat, X) -> np.ndarray:
     return e2 @ np.abs(w3) + g * (np.abs(h2) @ np.abs(w3))
 
 
-def loss_and_grads(wflat, X, target, k: int, scale: float = 1.0):
+def grad_error_bound(wflat, X, target, k: int, scale: float = 1.0, rows_per_block: int = 256,
+                     round_hidden: bool = False) -> np.ndarray:
+    """Per weight entry, how far the gradient of a kernel may lie from ``loss_and_grads``' FP64
+    gradient when it rounds h1 and h2 to BF16 in the forward pass, computes the softmax in FP32,
+    rounds dh2 = dz w3, dh1 = dh2 W2 and dz itself to BF16 for the weight-gradient products, and
+    sums those products in FP32 in blocks of `rows_per_block` rows (then the blocks in order).
+
+    First-order propagation of every rounding, as in ``z_error_bound``: the z error moves the
+    softmax by at most p_r (e_r + sum_s p_s e_s); a mask [a > 0] may differ where |a| is within
+    its own error, and there the whole product counts as error; an FP32 sum of K terms errs by
+    at most K 2^-24 times the sum of their magnitudes.  Returned over the flat (W1, W2, w3) vector;
+    the caller adds a factor for the second-order terms.
+
+    round_hidden: the bound against ``loss_and_grads(..., round_hidden=True)``, whose h1 and h2 are
+    already rounded to BF16.  A kernel's activation then differs from the oracle's only where its
+    FP32 sum and the FP64 one round to different BF16 values: by at most
+    bf16(relu(a + e)) - bf16(relu(a - e)) for a sum error e (zero away from rounding boundaries)."""
+    W1, W2, w3 = split(wflat)
+    X = np.asarray(X, np.float64)
+    u, g = 2.0 ** -8, 64 * 2.0 ** -24
+    aW1, aW2, aw3, aX = np.abs(W1), np.abs(W2), np.abs(w3), np.abs(X)
+    z, h1, h2, a1, a2 = forward(wflat, X, round_hidden)
+    # forward errors (pre-activation a, activation h after rounding, output z)
+    S1 = aX @ aW1.T
+    if round_hidden:
+        gr = g + 2.0 ** -50  # the oracle's own FP64 sums decide its roundings too
+        e1_pre = gr * S1
+        e1 = bf16_round(np.maximum(a1 + e1_pre, 0.0)) - bf16_round(np.maximum(a1 - e1_pre, 0.0))
+        e1[:, H - 1] = 0.0
+        S2 = np.abs(h1) @ aW2.T
+        e2_pre = e1 @ aW2.T + gr * S2
+        e2 = bf16_round(np.maximum(a2 + e2_pre, 0.0)) - bf16_round(np.maximum(a2 - e2_pre, 0.0))
+        e2[:, H - 1] = 0.0
+        ez = e2 @ aw3 + gr * (np.abs(h2) @ aw3)
+    else:
+        e1_pre = g * S1
+        e1 = u * np.abs(h1) + (1 + u) * e1_pre
+        e1[:, H - 1] = 0.0
+        S2 = np.abs(h1) @ aW2.T
+        e2_pre = e1 @ aW2.T + g * S2
+        e2 = e2_pre + u * (np.abs(a2) + e2_pre)
+        e2[:, H - 1] = 0.0
+        ez = e2 @ aw3 + g * (np.abs(h2) @ aw3)
+    # softmax per city (FP32 exp and division: 2^-18 relative, generous)
+    cities = len(target)
+    zc = z.reshape(cities, k)
+    live = np.array([int(t) != 0 for t in target])
+    p = np.exp(zc - zc.max(axis=1, keepdims=True))
+    p /= p.sum(axis=1, keepdims=True)
+    ezc = ez.reshape(cities, k)
+    ep = p * (ezc + (p * ezc).sum(axis=1, keepdims=True)) + 2.0 ** -18 * p
+    _, _, dz = loss_and_grads(wflat, X, target, k, 1.0, round_hidden)
+    D = np.abs(scale * dz)
+    eD = (np.abs(scale) * np.where(live[:, None], ep, 0.0)).reshape(-1) + 2.0 ** -24 * D
+    # dh2 = D w3 [a2 > 0], rounded to BF16
+    P2 = np.outer(D, aw3)
+    on2 = a2 > 0
+    flip2 = np.abs(a2) <= e2_pre
+    edh2 = on2 * ((1 + u) * np.outer(eD, aw3) + (u + 2.0 ** -24) * P2) + flip2 * P2
+    edh2[:, H - 1] = 0.0
+    dh2 = P2 * on2
+    dh2[:, H - 1] = 0.0
+    # dh1 = (dh2 W2) [a1 > 0], rounded to BF16
+    T1 = dh2 @ aW2
+    E1 = edh2 @ aW2
+    on1 = a1 > 0
+    flip1 = np.abs(a1) <= e1_pre
+    edh1 = on1 * ((1 + u) * (E1 + g * T1) + u * T1) + flip1 * (T1 + E1)
+    edh1[:, H - 1] = 0.0
+    dh1 = T1 * on1
+    dh1[:, H - 1] = 0.0
+    # weight gradients: FP32 sums over rows, block partials then the blocks in order
+    # (tensor-core accumulation may truncate rather than round: twice the rounding bound)
+    R = X.shape[0]
+    gam = 2 * (rows_per_block + -(-R // rows_per_block) + 2) * 2.0 ** -24
+    eD16 = eD + u * (D + eD)  # dz rounded to BF16 for dw3
+    gW2 = edh2.T @ np.abs(h1) + dh2.T @ e1 + edh2.T @ e1 + gam * (dh2.T @ np.abs(h1))
+    gW1 = edh1.T @ aX + gam * (dh1.T @ aX)
+    gw3 = eD16 @ np.abs(h2) + D @ e2 + eD16 @ e2 + gam * (D @ np.abs(h2))
+    return np.concatenate([gW1.ravel(), gW2.ravel(), gw3])
+
+
+def loss_and_grads(wflat, X, target, k: int, scale: float = 1.0, round_hidden: bool = False):
     """Summed cross-entropy over cities (times `scale`), its gradient over the flat weights and
     the unscaled dz = softmax - y of every row.
 
     Backward pass by the chain rule: dz = softmax - y per city; dw3 = h2^T dz;
     dh2 = dz w3^T masked by [a2 > 0] (and 0 on the constant unit); dW2 = dh2^T h1;
-    dh1 = dh2 W2 masked by [a1 > 0] (0 on the constant unit); dW1 = dh1^T x."""
+    dh1 = dh2 W2 masked by [a1 > 0] (0 on the constant unit); dW1 = dh1^T x.  With round_hidden
+    the forward pass rounds h1 and h2 to BF16 (``forward``) and the chain rule runs through the
+    rounded activations, the rounding itself passed as the identity, as the kernels do."""
     W1, W2, w3 = split(wflat)
     X = np.asarray(X, np.float64)
-    z, h1, h2, a1, a2 = forward(wflat, X)
+    z, h1, h2, a1, a2 = forward(wflat, X, round_hidden)
     cities = len(target)
     zc = z.reshape(cities, k)
     y = np.zeros((cities, k))

@@ -3,8 +3,8 @@
 The oracle cannot run the whole colony at this size in seconds, so it checks sampled outputs it
 can compute one by one:
   * candidate lists of sampled cities by brute force (bit-exact);
-  * initial tours (Algorithm 1, before its iterations) of sampled ants, built by the oracle from scratch with
-    its own candidate lists (bit-exact tours and lengths);
+  * initial tours (Algorithm 1, before its iterations) of eight sampled ants, built by the oracle from
+    scratch with its own candidate lists, one host process each (bit-exact tours and lengths);
   * a PartialACO iteration of sampled ants from a synthetic l_best population (spatially coherent
     random tours from the input generators) loaded into both the colony and the oracle, each
     computing its own exact lengths;
@@ -18,6 +18,7 @@ import pytest
 
 import aco_synth
 import oracle
+from tests import oracle_pool
 from tests.gpu_common import exact_tour_lengths, require_gpu
 
 torch = pytest.importorskip("torch")
@@ -60,13 +61,12 @@ def test_fullsize_iterations(colony200k):
     for a in sample:
         assert np.array_equal(np.sort(T0[a]), np.arange(n))
     assert np.array_equal(L0[sample], exact_tour_lengths(xy, T0[sample]))
+    # eight of the sampled ants rebuilt by the oracle from scratch, one host process each
+    built = oracle_pool.initial_tours(xy, ocand, p, sample[:8])
+    for a, (t, ln) in built.items():
+        assert np.array_equal(t, T0[a]), f"initial tour of ant {a} differs"
+        assert ln == L0[a]
     ref = oracle.Oracle(xy, cand=ocand, **p)
-    built = sample[:2].astype(np.int32)
-    ref.construct(0, ants=built)
-    R0 = ref.newtours
-    for a in built:
-        assert np.array_equal(R0[a], T0[a]), f"initial tour of ant {a} differs"
-    del R0
     col.update()
     lb, cl, _ = col.state()
     prev_l = cl.cpu().numpy()

@@ -1,8 +1,9 @@
 """Learned edge proposal on the GPU against the FP64 oracle (oracle/mlp.py, oracle edge scores).
 
 Network outputs are compared with the oracle's FP64 network on the same BF16 weights and inputs
-within the a-priori bound of BF16 hidden activations; gradients within 1e-2 relative (Frobenius,
-per weight matrix); the features within one BF16 step; degree counts, labels and every tour built
+within the a-priori bound of BF16 hidden activations; every gradient entry within the a-priori
+bound of the kernels' roundings against the network with BF16 activations; the features within
+one BF16 step; degree counts, labels and every tour built
 with learned scores bit for bit."""
 import numpy as np
 import pytest
@@ -74,12 +75,16 @@ def test_backward_matches_oracle_gradients():
     sc = EdgeScorer(w, max_rows=cities * k)
     g, loss = sc.backward(_to_dev_bf16(X), torch.from_numpy(T).cuda(), k, scale=1.0 / cities)
     g = g.cpu().numpy().astype(np.float64)
-    lo, go, _ = mlp.loss_and_grads(_oracle_weights(w), X, T.astype(np.uint32), k, scale=1.0 / cities)
-    assert loss.item() == pytest.approx(lo, rel=1e-2)
-    for name, a, b in zip(("W1", "W2", "w3"), mlp.split(g), mlp.split(go)):
-        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
-        assert rel <= 1e-2, f"{name}: relative error {rel}"
-    assert np.all(g[mlp.trainable_mask() == 0] == 0.0)
+    # the network with BF16 activations, and per entry the a-priori bound of the kernels' roundings
+    wo, To = _oracle_weights(w), T.astype(np.uint32)
+    lo, go, _ = mlp.loss_and_grads(wo, X, To, k, scale=1.0 / cities, round_hidden=True)
+    bound = 1.25 * mlp.grad_error_bound(wo, X, To, k, scale=1.0 / cities, round_hidden=True)
+    assert loss.item() == pytest.approx(lo, rel=1e-3)
+    on = mlp.trainable_mask() == 1
+    err = np.abs(g - go)
+    bad = np.nonzero(on & (err > bound))[0]
+    assert bad.size == 0, f"{bad.size} entries off bound, first {bad[0]}: gpu {g[bad[0]]} oracle {go[bad[0]]}"
+    assert np.all(g[~on] == 0.0)
     sc.close()
 
 

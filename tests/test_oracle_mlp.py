@@ -181,3 +181,79 @@ def test_edge_scores_equal_to_eta_reproduce_the_plain_method():
     assert np.allclose(p, [0, 0, 0, 0.25, 0.25, 0.25, 0.25], rtol=1e-15, atol=0)
     flat.set_edge_scores(None)
     assert np.array_equal(flat.etab, plain.etab)
+
+
+def _emulated_kernel_grads(w, X, T, k, scale):
+    """A numpy model of the backward kernels' roundings: BF16 h1, h2 in the forward pass, FP32
+    softmax, dz * scale in FP32, BF16 dh2 = dz w3 [h2 > 0], BF16 dh1 = (dh2 W2) [h1 > 0], BF16 dz
+    for dw3, FP32 sums of the weight-gradient products."""
+    f32 = np.float32
+    W1, W2, w3 = mlp.split(w)
+    a1 = (X.astype(f32) @ W1.T.astype(f32)).astype(np.float64)
+    h1 = mlp.bf16_round(np.maximum(a1, 0)); h1[:, H - 1] = 1
+    a2 = (h1.astype(f32) @ W2.T.astype(f32)).astype(np.float64)
+    h2 = mlp.bf16_round(np.maximum(a2, 0)); h2[:, H - 1] = 1
+    z = (h2.astype(f32) @ w3.astype(f32)).reshape(-1, k)
+    e = np.exp(z - z.max(axis=1, keepdims=True)).astype(f32)
+    p = (e / e.sum(axis=1, keepdims=True, dtype=f32)).astype(f32)
+    y = np.zeros_like(p)
+    for c, t in enumerate(T):
+        r = [b for b in range(k) if (int(t) >> b) & 1]
+        y[c, r] = f32(1.0 / len(r)) if r else 0
+    live = np.array([int(t) != 0 for t in T])[:, None]
+    dz = (np.where(live, p - y, 0).astype(f32) * f32(scale)).reshape(-1).astype(f32)
+    dh2 = mlp.bf16_round((dz[:, None] * w3.astype(f32)[None, :]).astype(np.float64) * (h2 > 0))
+    dh2[:, H - 1] = 0
+    dh1 = mlp.bf16_round((dh2.astype(f32) @ W2.astype(f32)).astype(np.float64) * (h1 > 0))
+    dh1[:, H - 1] = 0
+    dzb = mlp.bf16_round(dz.astype(np.float64))
+    gW2 = dh2.astype(f32).T @ h1.astype(f32)
+    gW1 = dh1.astype(f32).T @ X.astype(f32)
+    gw3 = dzb.astype(f32) @ h2.astype(f32)
+    return np.concatenate([gW1.ravel(), gW2.ravel(), gw3]).astype(np.float64)
+
+
+def test_grad_error_bound_covers_a_rounding_kernel_entry_by_entry():
+    """Against the network with BF16 activations (round_hidden), a numpy model of the kernels'
+    roundings stays within the per-entry bound, and the bound is a small fraction of the
+    gradients themselves (a wrong entry cannot hide behind it)."""
+    X, w = _random_problem(11, cities=300, k=20, scale=1.0)
+    W1, W2, w3 = (mlp.bf16_round(a) for a in mlp.split(w))
+    wb = np.concatenate([W1.ravel(), W2.ravel(), w3]) * mlp.trainable_mask()
+    rng = np.random.default_rng(12)
+    T = np.array([sum(1 << int(r) for r in rng.choice(20, rng.integers(0, 3), replace=False)) for _ in range(300)],
+                 np.uint32)
+    scale = 1.0 / 300
+    _, go, _ = mlp.loss_and_grads(wb, X, T, 20, scale=scale, round_hidden=True)
+    ge = _emulated_kernel_grads(wb, X, T, 20, scale)
+    bound = mlp.grad_error_bound(wb, X, T, 20, scale=scale, round_hidden=True)
+    on = mlp.trainable_mask() == 1
+    err = np.abs(ge - go)[on]
+    assert np.all(err <= 1.25 * bound[on])
+    assert err.max() > 0  # the model does round
+    assert np.median(bound[on] / (np.abs(go[on]) + 1e-30)) < 0.1
+
+
+def test_round_hidden_network_pins():
+    """round_hidden changes nothing where every activation is already a BF16 value (weights and
+    inputs small multiples of powers of two), and otherwise its activations are the exact ones
+    rounded to BF16."""
+    rng = np.random.default_rng(5)
+    X = np.zeros((40, IN))
+    X[:, :5] = rng.integers(-1, 2, (40, 5))
+    X[:, 5] = 1.0
+    W2 = np.zeros((H, H))  # three entries of +-1 per row: |a2| <= 18, an 8-bit integer
+    for r in range(H):
+        W2[r, rng.choice(H, 3, replace=False)] = rng.choice([-1.0, 1.0], 3)
+    w = np.concatenate([rng.integers(-1, 2, H * IN).astype(np.float64), W2.ravel(),
+                        rng.integers(-2, 3, H) / 4.0]) * mlp.trainable_mask()
+    T = np.array([0b11, 0b100, 0, 0b1000] * 2, np.uint32)
+    a = mlp.loss_and_grads(w, X, T, 5)
+    b = mlp.loss_and_grads(w, X, T, 5, round_hidden=True)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+    Xr, wr = _random_problem(3, cities=20, k=5)
+    z0, h10, h20, a10, a20 = mlp.forward(wr, Xr)
+    z1, h11, h21, a11, a21 = mlp.forward(wr, Xr, round_hidden=True)
+    assert np.array_equal(h11, mlp.bf16_round(h10))
+    assert np.array_equal(h21[:, :H - 1], mlp.bf16_round(np.maximum(h11 @ mlp.split(wr)[1].T, 0))[:, :H - 1])
+    assert not np.array_equal(z0, z1)

@@ -40,3 +40,18 @@ def test_snake_tours_are_seeded_permutations():
     # spatially coherent: far shorter than random permutations of the same cities
     rand = aco_synth.permutations(6, 5000, 1)
     assert oracle.tour_lengths(xy, a).max() < 0.2 * oracle.tour_lengths(xy, rand).min()
+
+
+def test_oracle_pool_gives_the_oracles_initial_tours():
+    """The spawn pool used by the full-size parity test returns what one oracle builds itself."""
+    from tests import oracle_pool
+
+    xy = aco_synth.clustered(300, 4, 0.05, 8)
+    p = dict(mode=1, n=300, m=12, k=8, alpha=1.0, beta=2.0, tau0=1.0, max_mod_frac=0.3, p_partial=1.0, seed=4)
+    cand = oracle.knn(xy, 8)
+    got = oracle_pool.initial_tours(xy, cand, p, [3, 7, 11], workers=2)
+    ref = oracle.Oracle(xy, cand=cand, **p)
+    ref.construct(0)
+    for a in (3, 7, 11):
+        assert np.array_equal(got[a][0], ref.newtours[a])
+        assert got[a][1] == ref.newlen[a]
