@@ -8,9 +8,9 @@ lists, initial tours) is untimed.  Prints one JSON line (rank 0).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun every rank runs an independent replica colony (seed + rank): the workload is one
-instance and the method has no exchange step at this scale, so the N-GPU figure is weak-scaled
-replica throughput.
+Under torchrun the ranks run one colony split by ants (every rank the whole colony state, its
+share of the ants built, one all-gather of the improved ants' commits per iteration): the same
+work as on one GPU, so the N-GPU figure is strong-scaled.
 """
 from __future__ import annotations
 
@@ -58,11 +58,6 @@ def parse_args():
 
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
-
-
-def replica_seed(seed: int, rank: int) -> int:
-    """Rank r runs its own colony, seeded seed + r: replicas, with no exchange between ranks."""
-    return int(seed) + int(rank)
 
 
 def aggregate_over_ranks(t_step: float, units: float, world: int, device="cpu"):
@@ -154,14 +149,23 @@ def code_sha1(name: str) -> str:
     return hashlib.sha1("\n".join(lines).encode()).hexdigest()[:12]
 
 
-def construct_bytes(decisions: int, k: int, m: int) -> int:
-    """Algorithmic bytes of one construction launch.
+def construct_bytes_model(decisions: int, fallbacks: int, fallback_rebuilt: int, k: int, m: int) -> int:
+    """Algorithmic bytes of one construction launch by the method's byte model.
 
-    Per decision: the candidate row (k x (4 B city + 4 B FP32 weight)) and the 4 B segment write.
-    Per rebuilt city: its old l_best entry (bitset set-up, 4 B), the new segment read back (4 B)
-    and one coordinate pair for each of the old and the new path (2 x 16 B).  Per ant: the two
-    closing coordinate pairs of each path (64 B).
-    """
+    Per decision: the current city's candidate row, its pheromone and its heuristic entries, one
+    FP32 word each per candidate (3 x 4k B), and the 4 B segment write.  Per exhausted-list step:
+    the current city's neighbour row over all ants (8 m B) and the ant's list of discarded cities
+    (4 M B, M = the ant's rebuilt count, summed over the steps by a device counter).  Per ant: the
+    segment read and written (8 M B) and the incremental length over 2 M coordinate gathers
+    (16 B each); summed over the ants, M is the number of decisions."""
+    return decisions * (12 * k + 4) + fallbacks * 8 * m + 4 * fallback_rebuilt + decisions * (8 + 32)
+
+
+def construct_bytes_layout(decisions: int, k: int, m: int) -> int:
+    """The bytes this kernel's own layout needs, narrower than the model: per decision one
+    candidate row of (4 B city + 4 B FP32 weight) x k and the 4 B segment write; per rebuilt city
+    its old l_best entry (4 B), the segment read back (4 B) and one coordinate pair for each of
+    the old and the new path (2 x 16 B); per ant the two closing coordinate pairs of each path."""
     return decisions * (8 * k + 4) + decisions * (4 + 4 + 32) + 64 * m
 
 
@@ -172,12 +176,32 @@ def rebuild_bytes(n: int, m: int, k: int) -> int:
     return 2 * n * m + n * k * (8 + 8 + 4) + 8 * m
 
 
+def measure_l2_peak(stream, nbytes: int = 32 << 20, passes: int = 64):
+    """L2 bandwidth from the library's STREAM-style probe on a buffer well inside L2 (32 MB of the
+    126 MB): read GB/s (16-byte loads cached in L2 only) and copy GB/s (bytes read + written)."""
+    import torch
+
+    from paper_1709_03187_gb300 import aco_probe_bandwidth
+
+    buf = torch.ones(nbytes // 4, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    best_r = best_c = 0.0
+    for _ in range(3):
+        ms = aco_probe_bandwidth(buf, nbytes, 0, passes, stream)
+        best_r = max(best_r, (nbytes - 16) * passes / (ms / 1e3) / 1e9)
+        ms = aco_probe_bandwidth(buf, nbytes, 1, passes, stream)
+        best_c = max(best_c, nbytes * passes / (ms / 1e3) / 1e9)
+    del buf
+    return {"read_gbs": best_r, "copy_gbs": best_c, "buffer_mb": nbytes >> 20, "passes": passes,
+            "how": "aco_probe_bandwidth, best of 3 launches of 64 passes, CUDA events"}
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_1709_03187_gb300 import Colony
+    from paper_1709_03187_gb300 import Colony, ShardedColony
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -187,8 +211,13 @@ def run_ours(args):
     params = dict(wl["params"])
     if args.ants:
         params["m"] = args.ants
-    params["seed"] = replica_seed(params["seed"], rank)
     n, m, k = params["n"], params["m"], params["k"]
+
+    def make_colony(coords):
+        # N ranks: one colony split by ants (every rank the same instance and seed)
+        if world > 1:
+            return ShardedColony(coords, rank=rank, world=world, stream=stream, **params)
+        return Colony(coords, stream=stream, **params)
     xy = aco_synth.make(args.workload)
     stream = torch.cuda.Stream()
 
@@ -198,7 +227,7 @@ def run_ours(args):
             dist.barrier()
 
     t0 = time.perf_counter()
-    col = Colony(xy, stream=stream, **params)
+    col = make_colony(xy)
     col.build_candidates()
     col.iterate(0)  # Algorithm 1: initial tours
     s0 = col.stats()
@@ -221,6 +250,8 @@ def run_ours(args):
             e0.record(stream)
             col.construct(it)
             e1.record(stream)
+            if world > 1:
+                col.exchange()  # every rank's commits (export, all-gather, import)
             col.update()
             e2.record(stream)
             it += 1
@@ -233,17 +264,22 @@ def run_ours(args):
     decisions = st_after["decisions"] - st_before["decisions"]
     t_max, dec_all = aggregate_over_ranks(t_step, decisions, world, "cuda")
     value = dec_all / t_max
-    its = args.steps * world / t_max
+    its = args.steps / t_max  # one colony (split over the ranks when N > 1)
 
     hbm_peak, peak_kind = read_peaks()
     launches = args.steps
-    c_bytes = construct_bytes(decisions, k, m) / launches
+    fb = st_after["fallbacks"] - st_before["fallbacks"]
+    fb_m = st_after["fallback_rebuilt"] - st_before["fallback_rebuilt"]
+    fb_scan = st_after["fallback_scanned"] - st_before["fallback_scanned"]
+    c_bytes = construct_bytes_model(decisions, fb, fb_m, k, m) / launches
+    c_layout = construct_bytes_layout(decisions, k, m) / launches
     r_bytes = rebuild_bytes(n, m, k)
     c_avg = t_con / launches
     u_avg = t_upd / launches
+    l2 = measure_l2_peak(stream)
     kernels = {
-        "construct_lbest_kernel": {"avg_ms": c_avg * 1e3, "alg_bytes": c_bytes,
-                                   "achieved_gbs": c_bytes / c_avg / 1e9},
+        "construct_lbest_kernel": {"avg_ms": c_avg * 1e3, "alg_bytes": c_bytes, "achieved_gbs": c_bytes / c_avg / 1e9,
+                                   "layout_bytes": c_layout, "layout_gbs": c_layout / c_avg / 1e9},
         "update (commit + gbest_q + rebuild)": {"avg_ms": u_avg * 1e3, "alg_bytes": r_bytes,
                                                 "achieved_gbs": r_bytes / u_avg / 1e9},
     }
@@ -254,13 +290,21 @@ def run_ours(args):
         traffic = round(CONSTRUCT_TRAFFIC["bytes_per_decision"] * decisions / launches)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 2), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(ach / hbm_peak, 5), "peak_source": f"{peak_kind} hbm_gbs", "traffic": traffic,
+                "bytes_model": "per decision 12k + 4 B (candidate, pheromone, heuristic rows in FP32; segment "
+                               "write); per exhausted step 8m B (neighbour row) + 4M B (discarded list, M from "
+                               "a device counter); per rebuilt city 8 + 32 B (segment, coordinate gathers)",
+                "exhausted_steps_per_launch": fb / launches, "mean_M_at_exhausted_step": fb_m / max(1, fb),
+                "mean_list_scanned_at_exhausted_step": fb_scan / max(1, fb),
+                "l2_peak_gbs": round(l2["read_gbs"], 1), "frac_l2": round(ach / l2["read_gbs"], 5),
+                "l2_probe": l2,
+                "layout_frac_l2": round(kernels["construct_lbest_kernel"]["layout_gbs"] / l2["read_gbs"], 5),
                 "note": "each ant is a dependent chain of Eq. 1 decisions; a launch lasts as long as the "
-                        "longest chain, so the kernel is latency-bound",
+                        "longest chain, so the kernel is latency-bound; its working set sits in L2",
                 "kernels": {kn: {kk: round(v, 4) for kk, v in kv.items()} for kn, kv in kernels.items()}}
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, xy, params, stream)
+        e2e = run_e2e(args, xy, params, stream, make_colony, world)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload.startswith("lbest"):
         cpu = cpu_baseline_oracle(xy, params, it, args.cpu_sample)
@@ -268,12 +312,12 @@ def run_ours(args):
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "decisions/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_max / args.steps * 1e3, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "iterations_per_s": round(its, 2),
         "config": {"workload": f"{args.workload}: n={n} clustered (200 Gaussian clusters, sigma=0.005), k={k}, m={m}, "
                                f"f={params['max_mod_frac']}, alpha={params['alpha']}, beta={params['beta']}, "
                                f"tau0={params['tau0']}, p_partial={params['p_partial']}",
-                   "n": n, "m": m, "k": k, "parallelism": f"replicas x{world}" if world > 1 else "single colony",
+                   "n": n, "m": m, "k": k, "parallelism": f"one colony split by ants over {world} GPUs" if world > 1 else "single colony",
                    "l2": "flushed (512 MB write) before every timed step, outside the events",
                    "decisions_per_step": decisions / args.steps,
                    # every ant's new tour has n positions; those not decided this step stay in
@@ -297,22 +341,25 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_e2e(args, xy, params, stream):
+def run_e2e(args, xy, params, stream, make_colony, world=1):
     """The same metric through the public API from host buffers: pinned coordinates copied in,
     candidate lists, initial tours and `steps` iterations, C_gbest read back every step and the
     best tour read back at the end.  Decisions of the `steps` iterations / wall time of the whole
-    solve (set-up time counted, set-up decisions not)."""
+    solve (set-up time counted, set-up decisions not); with N ranks, the decisions of every rank
+    over the slowest rank's wall time."""
     import torch
-
-    from paper_1709_03187_gb300 import Colony
 
     host = torch.from_numpy(xy).pin_memory()
     torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
         dev = host.to("cuda", non_blocking=True)
     stream.synchronize()
-    col = Colony(dev, stream=stream, **params)
+    col = make_colony(dev)
     col.build_candidates()
     gb = []
     dec0 = 0
@@ -329,24 +376,26 @@ def run_e2e(args, xy, params, stream):
     wall = time.perf_counter() - t0
     col.close()
     del best
-    return {"value": round((st["decisions"] - dec0) / wall, 1), "unit": "decisions/s",
+    wall, dec = aggregate_over_ranks(wall, st["decisions"] - dec0, world, "cuda")
+    t_setup_note = ("wall time includes instance creation, candidate lists and the initial tours; decisions "
+                    "are those of the timed iterations only")
+    return {"value": round(dec / wall, 1), "unit": "decisions/s",
             "h2d_bytes_per_step": round(host.numel() * 8 / (args.steps + 1), 1),
             "d2h_bytes_per_step": round(8 + 4 * params["n"] / (args.steps + 1), 1),
-            "wall_s": round(wall, 3), "iterations": args.steps + 1,
-            "note": "wall time includes instance creation, candidate lists and the initial tours; decisions "
-                    "are those of the timed iterations only"}
+            "wall_s": round(wall, 3), "iterations": args.steps + 1, "note": t_setup_note}
 
 
 def oracle_start(xy, params, seeds=2):
     """The oracle's own starting colony, built with no input from the device: candidate lists by
-    the exact x-sweep, initial tours of `seeds` ants, repeated over the m ants as their l_best,
-    and the pheromone rebuild (timed).  Returns (oracle, rebuild seconds)."""
+    the exact x-sweep, initial tours of `seeds` ants (one host thread each), repeated over the m
+    ants as their l_best, and the pheromone rebuild (timed, one core).  Returns (oracle, rebuild
+    seconds)."""
     import oracle
 
     m, k = params["m"], params["k"]
     cand = oracle.knn_sweep(xy, k)
     ref = oracle.Oracle(xy, cand=cand, **params)
-    ref.construct(0, ants=np.arange(seeds, dtype=np.int32))  # oracle-built initial tours
+    ref.construct(0, ants=np.arange(seeds, dtype=np.int32), threads=seeds)  # oracle-built initial tours
     T = ref.newtours[:seeds]
     L = oracle.tour_lengths(xy, T)
     ref.set_lbest(np.ascontiguousarray(T[np.arange(m) % seeds]), L[np.arange(m) % seeds])
@@ -355,25 +404,44 @@ def oracle_start(xy, params, seeds=2):
     return ref, time.perf_counter() - t0
 
 
-def cpu_baseline_oracle(xy, params, iteration, sample):
-    """The oracle timed on this host: one PartialACO iteration of `sample` ants of its own colony
-    (oracle_start), with the pheromone rebuild over all m ants; projected to the full colony as
-    t_rebuild + (m / sample) * t_construct."""
-    ref, t_rb = oracle_start(xy, params)
-    m = params["m"]
-    ants = np.random.default_rng(0).choice(m, size=min(sample, m), replace=False).astype(np.int32)
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def time_oracle_sample(ref, iteration, ants, threads):
+    """Seconds and decisions of one PartialACO iteration of the listed ants (pheromone kept)."""
     ref.reset_counters()
     t0 = time.perf_counter()
-    ref.construct(iteration, ants=ants, rebuild=False)
-    t_cs = max(time.perf_counter() - t0, 1e-9)
-    dec = ref.counters()["decisions"]
-    full_dec = dec * m / ants.size
-    full_t = t_rb + t_cs * m / ants.size
-    return {"value": round(full_dec / full_t, 1), "unit": "decisions/s", "cores": 1, "kind": "oracle",
-            "sample": f"one iteration of {ants.size} of the {m} ants of the oracle's own colony (its initial "
-                      f"tours of 2 ants repeated as l_best), plus the full pheromone rebuild ({t_rb:.2f} s); "
-                      f"projected t_rebuild + (m/sample) t_construct = {full_t:.2f} s for {full_dec:.0f} decisions",
-            "iterations_per_s": round(1.0 / full_t, 5)}
+    ref.construct(iteration, ants=ants, rebuild=False, threads=threads)
+    return max(time.perf_counter() - t0, 1e-9), ref.counters()["decisions"]
+
+
+def cpu_baseline_oracle(xy, params, iteration, sample):
+    """The oracle timed on this host on its own colony (oracle_start): one PartialACO iteration of
+    a sample of ants on one core, and of a larger sample spread over every core; each projected to
+    the full colony as t_rebuild + (m / sample) * t_construct (the rebuild runs on one core)."""
+    ref, t_rb = oracle_start(xy, params)
+    m = params["m"]
+    rng = np.random.default_rng(0)
+    cores = host_cores()
+    out = {}
+    for label, threads, size in (("one_core", 1, min(sample, m)), ("all_cores", cores, min(m, 8 * cores))):
+        ants = rng.choice(m, size=size, replace=False).astype(np.int32)
+        t_cs, dec = time_oracle_sample(ref, iteration, ants, threads)
+        full_dec = dec * m / ants.size
+        full_t = t_rb + t_cs * m / ants.size
+        out[label] = {"value": round(full_dec / full_t, 1), "cores": threads, "sample_ants": int(ants.size),
+                      "construct_s": round(t_cs, 3), "projected_iteration_s": round(full_t, 3)}
+    best = out["all_cores"]
+    return {"value": best["value"], "unit": "decisions/s", "cores": best["cores"], "kind": "oracle",
+            "sample": f"one iteration of sampled ants of the {m}-ant colony of the oracle's own start (its initial "
+                      f"tours of 2 ants repeated as l_best): {out['all_cores']['sample_ants']} ants over "
+                      f"{cores} threads, and {out['one_core']['sample_ants']} on one core; plus the full "
+                      f"pheromone rebuild on one core ({t_rb:.2f} s); projected t_rebuild + (m/sample) t_construct",
+            "one_core": out["one_core"], "all_cores": out["all_cores"], "host_cores": cores}
 
 
 # ------------------------------------------------------------------ reference arm (the oracle)
@@ -394,17 +462,14 @@ def run_reference(args):
         ref = oracle.Oracle(xy, **params)
         t_rb = 0.0
     setup = time.perf_counter() - t0
-    sample = max(1, min(args.cpu_sample, 4, 150 // max(1, args.warmup + args.steps)))
+    cores = host_cores()
+    sample = max(1, min(m, cores))  # one sampled ant per host thread and step
     rng = np.random.default_rng(1)
     per = []
     for step in range(args.warmup + args.steps):
         if params["mode"] == 1:
             ants = rng.choice(m, size=sample, replace=False).astype(np.int32)
-            ref.reset_counters()
-            t1 = time.perf_counter()
-            ref.construct(step + 2, ants=ants, rebuild=False)
-            t_cs = max(time.perf_counter() - t1, 1e-9)
-            dec = ref.counters()["decisions"]
+            t_cs, dec = time_oracle_sample(ref, step + 2, ants, cores)
             # the rebuild (measured once in set-up) plus the sampled ants projected to the colony
             t_full = t_rb + t_cs * m / sample
             per.append((dec * m / sample, t_full))
@@ -417,15 +482,20 @@ def run_reference(args):
     dec = sum(d for d, _ in timed)
     tt = sum(t for _, t in timed)
     value = dec / tt
+    if params["mode"] == 1:
+        how = (f"each step: {sample} random ants of the {m}-ant colony over {cores} host threads (the oracle's own "
+               f"start: initial tours of 2 ants, repeated as l_best), plus the pheromone rebuild over all ants on one "
+               f"core ({t_rb:.2f} s, measured once); the step time is projected as t_rebuild + (m/sample) "
+               f"t_construct; set-up {setup:.1f} s")
+    else:
+        how = f"every step is a whole iteration of the colony, one core; set-up {setup:.1f} s"
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "decisions/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tt / max(1, len(timed)) * 1e3, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "projected": params["mode"] == 1,
            "config": {"workload": args.workload, "n": n, "m": m, "k": k},
-           "cpu_baseline": {"value": round(value, 1), "unit": "decisions/s", "cores": 1, "kind": "oracle",
-                            "sample": f"each step: {sample} random ants of the {m}-ant colony (initial tours built "
-                                      f"by the oracle for 2 ants, repeated), pheromone rebuild over all ants "
-                                      f"({t_rb:.2f} s, measured once); step time projected as t_rebuild + "
-                                      f"(m/sample) t_construct; setup {setup:.1f} s"},
+           "cpu_baseline": {"value": round(value, 1), "unit": "decisions/s",
+                            "cores": cores if params["mode"] == 1 else 1, "kind": "oracle", "sample": how},
            "e2e": {"value": round(value, 1), "unit": "decisions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

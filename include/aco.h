@@ -80,6 +80,10 @@ typedef struct aco_stats {
     int32_t gbest_ant;       /* ant holding it (lowest index among equals), -1 if none       */
     int32_t iterations;      /* completed construct + update pairs                           */
     uint64_t ls_moves;       /* 2-opt moves made by the local search                         */
+    uint64_t fallback_rebuilt; /* sum over exhausted-list steps of the ant's rebuilt count M
+                                  (n - 1 for a full construction)                            */
+    uint64_t fallback_scanned; /* sum over exhausted-list steps of the remaining cities listed
+                                  for the step (before the visited ones drop out)             */
 } aco_stats;
 
 typedef struct aco_instance aco_instance; /* opaque: owns all device state of one colony */
@@ -184,6 +188,38 @@ aco_status aco_set_local_search(aco_instance* inst, double p, int32_t window);
  * otherwise); not between construct and update.  The first call with on = 1 allocates the
  * pheromone table (8 n k bytes) and fills it from the current l_best population (synchronises). */
 aco_status aco_set_async_share(aco_instance* inst, int32_t on);
+
+/* ------------------------------------------------------------------ one colony over several GPUs
+ * Section 3's colony draws its pheromone from every ant's l_best, and within an iteration the
+ * ants only read it (synchronous reading): the ants can be split over GPUs.  Every rank creates
+ * the same instance (same coordinates and parameters) and keeps the whole colony state; it
+ * constructs its own range of ants, exports the commits of its ants that improved, receives
+ * every rank's records (e.g. by an all-gather), imports them and runs aco_update_pheromone.  A
+ * commit touches only its own ant's l_best and neighbour entries and the pheromone sums are exact
+ * integers, so each rank's state after the update equals the single colony's bit for bit.
+ *
+ * Records (int32 words): word 0 the number of records, word 1 zero, words 2-3 the words used (an
+ * int64 counting these four), then per record: ant, s, P, M, start, L (segment length: M for a
+ * partial rebuild, n for a full construction), new length (2 words, FP64 bits, low word first),
+ * exact length (4 words: the 128-bit fixed-point value, low 64 bits first), then L city indices.
+ * The first construction builds full tours (n cities per record). */
+
+/* The ants this instance constructs: [ant_begin, ant_end) (default: all).  LBEST mode, not for an
+ * instance of a batch, and not with local search or asynchronous sharing unless the range is the
+ * whole colony (ACO_ERR_STATE).  Not between construct and update. */
+aco_status aco_set_ant_range(aco_instance* inst, int32_t ant_begin, int32_t ant_end);
+/* After aco_construct_tours: writes the records of the instance's own ants whose new tour is
+ * strictly shorter than their l_best into buf_dev (cap_words int32 words, 8-byte aligned), in any
+ * order.  *words_out = the words used (also when they exceed cap_words: then nothing usable is
+ * written and ACO_ERR_INVALID_ARG is returned).  At most (ant_end - ant_begin) (12 + n) + 4 words.
+ * Synchronises. */
+aco_status aco_export_commits(aco_instance* inst, int32_t* buf_dev, int64_t cap_words, int64_t* words_out);
+/* Before aco_update_pheromone: the records of `count` buffers laid out stride_words apart
+ * (8-byte aligned, stride even), typically every rank's export; records of the instance's own
+ * ants are skipped.  Ants outside the own range that have no record commit nothing this
+ * iteration.  A malformed record gives ACO_ERR_INVALID_ARG at the next synchronising call.
+ * Enqueued. */
+aco_status aco_import_commits(aco_instance* inst, const int32_t* bufs_dev, int32_t count, int64_t stride_words);
 
 /* ------------------------------------------------------------------ batched colonies
  * Many independent instances of uneven size solved together: the same method and parameters
@@ -303,6 +339,17 @@ aco_status aco_tour_labels(aco_instance* inst, uint32_t* target_dev);
  * (ACO_ERR_STATE).  Synchronises when score_dev is given (a non-finite or non-positive score
  * gives ACO_ERR_INVALID_ARG and leaves the scores in use unchanged). */
 aco_status aco_set_edge_scores(aco_instance* inst, const float* score_dev);
+
+/* Bandwidth probe (a measurement aid, not part of the method): the roofline of the construction
+ * kernel, whose working set sits in L2, needs the L2 bandwidth, which this measures on the caller's
+ * buffer.  buf_dev: `bytes` bytes of device memory (16-byte aligned, bytes a multiple of 32 and
+ * >= 4096; contents are read and, in mode 1, overwritten).  mode 0: one launch of reps passes that
+ * read the buffer (after its first 16 bytes) with 16-byte loads cached in L2 only; mode 1: one
+ * launch of reps passes that copy its first half to its second half.  One untimed pass first;
+ * *ms_out = the device time of the timed launch (CUDA events on `stream`).  Changes no device
+ * setting.  Synchronises. */
+aco_status aco_probe_bandwidth(void* buf_dev, int64_t bytes, int32_t mode, int32_t reps, void* stream,
+                               float* ms_out);
 
 void aco_destroy_instance(aco_instance* inst);
 const char* aco_status_string(aco_status s);

@@ -43,7 +43,7 @@ def build(force: bool = False) -> str:
             return _LIB
         os.makedirs(_LIB_DIR, exist_ok=True)
         tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+        cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-pthread",
                _SRC, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
@@ -75,6 +75,7 @@ def lib():
             "or_destroy": (None, [P]),
             "or_construct": (None, [P, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
             "or_construct_ex": (None, [P, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+            "or_construct_mt": (None, [P, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
             "or_update": (None, [P]),
             "or_get_lbest": (None, [P, i32p]),
             "or_get_clen": (None, [P, f64p]),
@@ -100,6 +101,8 @@ def lib():
             "or_ls_moves": (ctypes.c_int64, [P]),
             "or_two_opt_windowed": (ctypes.c_int, [ctypes.c_int, f64p, i32p, ctypes.c_int, ctypes.c_int]),
             "or_set_p_partial": (None, [P, ctypes.c_double]),
+            "or_set_newtour": (None, [P, ctypes.c_int, i32p, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
+            "or_clear_built": (None, [P]),
             "or_exhausted_step": (ctypes.c_int, [P, ctypes.c_int, u8p, ctypes.c_double, ctypes.c_void_p]),
             "or_ir_pick": (ctypes.c_int, [f64p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                           ctypes.c_uint32]),
@@ -215,14 +218,16 @@ class Oracle:
             lib().or_destroy(h)
             self._h = None
 
-    def construct(self, iteration: int, ants=None, rebuild: bool = True):
+    def construct(self, iteration: int, ants=None, rebuild: bool = True, threads: int = 1):
         """Build new tours (all ants, or the listed ones).  rebuild=False reuses the pheromone of
-        the previous call (valid while the l_best population is unchanged)."""
+        the previous call (valid while the l_best population is unchanged).  threads > 1 spreads
+        the ants over host threads (same result)."""
         if ants is None:
-            lib().or_construct_ex(self._h, iteration, None, 0, int(rebuild))
+            lib().or_construct_mt(self._h, iteration, None, 0, int(rebuild), threads)
         else:
             a = np.ascontiguousarray(ants, np.int32)
-            lib().or_construct_ex(self._h, iteration, a.ctypes.data_as(ctypes.c_void_p), a.size, int(rebuild))
+            lib().or_construct_mt(self._h, iteration, a.ctypes.data_as(ctypes.c_void_p), a.size, int(rebuild),
+                                  threads)
 
     def update(self):
         lib().or_update(self._h)
@@ -330,6 +335,58 @@ class Oracle:
         if not np.all(np.isfinite(s)) or not np.all(s > 0):
             raise ValueError("edge scores must be finite and > 0")
         lib().or_set_edge_scores(self._h, s.ctypes.data)
+
+    # ---- a colony split over processes by ants (the records of the library's commit exchange:
+    # ant, s, P, M, start, L, new length as two words, four words of exact length (zero here:
+    # the oracle measures lengths itself), then L cities; buffer header of four words)
+    def export_commits(self, a0: int, a1: int) -> np.ndarray:
+        """Records of ants a0..a1-1 built by the last construct whose new tour is strictly shorter
+        than their l_best."""
+        tours, lens, clen = self.newtours, self.newlen, self.clen
+        s_arr, M_arr = self.segments()
+        words = [0, 0, 0, 0]
+        recs = 0
+        for a in range(a0, a1):
+            if not lens[a] < clen[a]:
+                continue
+            s, M, n = int(s_arr[a]), int(M_arr[a]), self.n
+            seg = tours[a][(s + (n - M) + np.arange(M)) % n] if s >= 0 else tours[a]
+            start = int(tours[a][s]) if s >= 0 else int(tours[a][0])
+            bits = np.array([lens[a]], np.float64).view(np.int32)
+            words += [a, s, n - M if s >= 0 else 0, M, start, len(seg), int(bits[0]), int(bits[1]), 0, 0, 0, 0]
+            words += [int(c) for c in seg]
+            recs += 1
+        out = np.array(words, np.int64).astype(np.int32)
+        out[0] = recs
+        out[2:4] = np.array([out.size], np.int64).view(np.int32)
+        return out
+
+    def import_commits(self, bufs, a0: int, a1: int):
+        """Sets the new tours of every record outside a0..a1 (the own ants keep theirs); ants that
+        are neither own nor recorded commit nothing."""
+        own = self.newtours[a0:a1].copy()
+        own_len, (own_s, own_M) = self.newlen[a0:a1].copy(), self.segments()
+        lib().or_clear_built(self._h)
+        lb = self.lbest
+        for a in range(a0, a1):
+            lib().or_set_newtour(self._h, a, np.ascontiguousarray(own[a - a0]), float(own_len[a - a0]),
+                                 int(own_s[a]), int(own_M[a]))
+        for b in bufs:
+            b = np.asarray(b, np.int32)
+            recs, pos = int(b[0]), 4
+            for _ in range(recs):
+                a, s, P, M, start, L = (int(x) for x in b[pos:pos + 6])
+                ln = float(b[pos + 6:pos + 8].copy().view(np.float64)[0])
+                seg = b[pos + 12:pos + 12 + L]
+                pos += 12 + L
+                if a0 <= a < a1:
+                    continue
+                if s >= 0:
+                    t = lb[a].copy()
+                    t[(s + P + np.arange(M)) % self.n] = seg
+                else:
+                    t = seg.copy()
+                lib().or_set_newtour(self._h, a, np.ascontiguousarray(t, np.int32), ln, s, M)
 
     def exhausted_step(self, i: int, visited: np.ndarray, u: float = 0.0):
         """The exhausted-list rule at city i (mode 1) for the given visited set and draw u, as a

@@ -49,6 +49,7 @@
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared (no FMA contraction anywhere).
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -528,6 +529,35 @@ int or_two_opt_windowed(int n, const double* xy, int32_t* T, int W, int max_pass
     return moves;
 }
 
+/* One ant's tour of the iteration: partial rebuild of its l_best (Algorithm 1) or a full
+ * construction, then local search if drawn (at most OR_LS_MAX_ANTS ants, counted in *ls_count). */
+static void construct_one(or_state* st, int a, int iteration, int* ls_count) {
+    int partial = 0;
+    if (st->p.mode == 1 && st->initialized) {
+        partial = 1;
+        if (st->p.p_partial < 1.0) {
+            uint32_t x[4];
+            draw(st->p.seed, 0, (uint32_t)a, (uint32_t)iteration, 3, x);
+            partial = or_u53(x[0], x[1]) < st->p.p_partial;
+        }
+    }
+    if (partial) build_partial(st, a, (uint32_t)iteration);
+    else build_full(st, a, (uint32_t)iteration);
+    if (st->p.mode == 1 && st->ls_p > 0.0 && *ls_count < OR_LS_MAX_ANTS) {
+        uint32_t x[4];
+        draw(st->p.seed, 0, (uint32_t)a, (uint32_t)iteration, 5, x);
+        if (or_u53(x[0], x[1]) < st->ls_p) {
+            ++*ls_count;
+            st->ls_moves += or_two_opt_windowed(st->p.n, st->xy, st->newtour + (size_t)a * st->p.n,
+                                                st->ls_window, OR_LS_MAX_PASSES);
+            st->seg_s[a] = -1;  /* committed as a whole tour */
+            st->seg_M[a] = st->p.n - 1;
+        }
+    }
+    st->newlen[a] = or_tour_length(st->p.n, st->xy, st->newtour + (size_t)a * st->p.n);
+    st->built[a] = 1;
+}
+
 /* Tour construction for every ant (ants == NULL) or for the listed ants only.  rebuild = 0
  * reuses the pheromone computed by the previous call (same l_best population). */
 void or_construct_ex(or_state* st, int iteration, const int32_t* ants, int count, int rebuild) {
@@ -536,33 +566,62 @@ void or_construct_ex(or_state* st, int iteration, const int32_t* ants, int count
     if (!ants) count = m;
     memset(st->built, 0, sizeof(int32_t) * (size_t)m);
     int ls_count = 0;
-    for (int c = 0; c < count; ++c) {
-        int a = ants ? ants[c] : c;
-        int partial = 0;
-        if (st->p.mode == 1 && st->initialized) {
-            partial = 1;
-            if (st->p.p_partial < 1.0) {
-                uint32_t x[4];
-                draw(st->p.seed, 0, (uint32_t)a, (uint32_t)iteration, 3, x);
-                partial = or_u53(x[0], x[1]) < st->p.p_partial;
-            }
-        }
-        if (partial) build_partial(st, a, (uint32_t)iteration);
-        else build_full(st, a, (uint32_t)iteration);
-        if (st->p.mode == 1 && st->ls_p > 0.0 && ls_count < OR_LS_MAX_ANTS) {
-            uint32_t x[4];
-            draw(st->p.seed, 0, (uint32_t)a, (uint32_t)iteration, 5, x);
-            if (or_u53(x[0], x[1]) < st->ls_p) {
-                ++ls_count;
-                st->ls_moves += or_two_opt_windowed(st->p.n, st->xy, st->newtour + (size_t)a * st->p.n,
-                                                    st->ls_window, OR_LS_MAX_PASSES);
-                st->seg_s[a] = -1;  /* committed as a whole tour */
-                st->seg_M[a] = st->p.n - 1;
-            }
-        }
-        st->newlen[a] = or_tour_length(st->p.n, st->xy, st->newtour + (size_t)a * st->p.n);
-        st->built[a] = 1;
+    for (int c = 0; c < count; ++c) construct_one(st, ants ? ants[c] : c, iteration, &ls_count);
+}
+
+/* The same construction with the ants spread over `threads` host threads (ant c on thread
+ * c mod threads).  Within an iteration the ants only read the shared state (the pheromone is
+ * fixed, Section 3 read synchronously) and each writes its own rows, so every thread works on a
+ * shallow copy of the state with its own visited scratch and counters; the result is identical
+ * to or_construct_ex.  Local search (whose at-most-8 cap follows the ant order) runs sequentially. */
+typedef struct {
+    or_state view;
+    const int32_t* ants;
+    int count, first, step, iteration;
+} or_worker;
+
+static void* or_worker_run(void* arg) {
+    or_worker* w = (or_worker*)arg;
+    int ls_count = 0;
+    for (int c = w->first; c < w->count; c += w->step) construct_one(&w->view, w->ants ? w->ants[c] : c, w->iteration, &ls_count);
+    return NULL;
+}
+
+void or_construct_mt(or_state* st, int iteration, const int32_t* ants, int count, int rebuild, int threads) {
+    if (!ants) count = st->p.m;
+    if (threads > count) threads = count;
+    if (threads <= 1 || st->ls_p > 0.0) {
+        or_construct_ex(st, iteration, ants, count, rebuild);
+        return;
     }
+    if (st->p.mode == 1 && rebuild) lbest_pheromone(st);
+    memset(st->built, 0, sizeof(int32_t) * (size_t)st->p.m);
+    or_worker* w = (or_worker*)calloc((size_t)threads, sizeof(or_worker));
+    pthread_t* tid = (pthread_t*)calloc((size_t)threads, sizeof(pthread_t));
+    int* started = (int*)calloc((size_t)threads, sizeof(int));
+    for (int t = 0; t < threads; ++t) {
+        w[t].view = *st;
+        w[t].view.visited = (unsigned char*)malloc((size_t)st->p.n);
+        w[t].view.decisions = w[t].view.fallbacks = w[t].view.scans = w[t].view.boosted = 0;
+        w[t].ants = ants;
+        w[t].count = count;
+        w[t].first = t;
+        w[t].step = threads;
+        w[t].iteration = iteration;
+        started[t] = pthread_create(&tid[t], NULL, or_worker_run, &w[t]) == 0;
+        if (!started[t]) or_worker_run(&w[t]);
+    }
+    for (int t = 0; t < threads; ++t) {
+        if (started[t]) pthread_join(tid[t], NULL);
+        st->decisions += w[t].view.decisions;
+        st->fallbacks += w[t].view.fallbacks;
+        st->scans += w[t].view.scans;
+        st->boosted += w[t].view.boosted;
+        free(w[t].view.visited);
+    }
+    free(w);
+    free(tid);
+    free(started);
 }
 
 void or_construct(or_state* st, int iteration, const int32_t* ants, int count) {
@@ -668,6 +727,19 @@ void or_set_edge_scores(or_state* st, const double* score) {
             st->etab[(size_t)i * k + r] =
                 score ? score[(size_t)i * k + r] : eta_pow(st->xy, i, st->cand[(size_t)i * k + r], st->p.beta);
 }
+
+/* The new tour of ant a built elsewhere (a colony split over processes by ants): l_best layout,
+ * its length, and whether it was a partial rebuild (s >= 0, M rebuilt cities) or a full tour. */
+void or_set_newtour(or_state* st, int a, const int32_t* tour, double len, int s, int M) {
+    memcpy(st->newtour + (size_t)a * st->p.n, tour, sizeof(int32_t) * (size_t)st->p.n);
+    st->newlen[a] = len;
+    st->seg_s[a] = s;
+    st->seg_M[a] = M;
+    st->built[a] = 1;
+}
+
+/* Forget which ants were built (before the tours of another process's ants are set). */
+void or_clear_built(or_state* st) { memset(st->built, 0, sizeof(int32_t) * (size_t)st->p.m); }
 
 /* Replace the l_best population (checkpoint restore / teacher forcing). */
 void or_set_lbest(or_state* st, const int32_t* lbest, const double* clen) {

@@ -38,7 +38,7 @@ class Stats(ctypes.Structure):
         ("decisions", ctypes.c_uint64), ("fallbacks", ctypes.c_uint64), ("exact_resolves", ctypes.c_uint64),
         ("improved", ctypes.c_uint64), ("partial_ants", ctypes.c_uint64), ("full_ants", ctypes.c_uint64),
         ("gbest", ctypes.c_double), ("gbest_ant", ctypes.c_int32), ("iterations", ctypes.c_int32),
-        ("ls_moves", ctypes.c_uint64),
+        ("ls_moves", ctypes.c_uint64), ("fallback_rebuilt", ctypes.c_uint64), ("fallback_scanned", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:
@@ -69,6 +69,10 @@ def lib():
             "aco_step_probs": (S, [V, I32, V, V, V]),
             "aco_destroy_instance": (None, [V]),
             "aco_build_candidates_noalloc": (S, [V, I32, I32, V, V]),
+            "aco_set_ant_range": (S, [V, I32, I32]),
+            "aco_export_commits": (S, [V, V, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+            "aco_import_commits": (S, [V, V, I32, ctypes.c_int64]),
+            "aco_probe_bandwidth": (S, [V, ctypes.c_int64, I32, I32, V, ctypes.POINTER(ctypes.c_float)]),
             "aco_batch_create": (S, [V, V, I32, ctypes.POINTER(Params), V, ctypes.POINTER(V)]),
             "aco_batch_build_candidates": (S, [V]),
             "aco_batch_run": (S, [V, I32, I32, I32]),
@@ -226,6 +230,30 @@ def aco_build_candidates_noalloc(xy_dev, n: int, k: int, cand_out_dev, stream=No
     status = lib().aco_build_candidates_noalloc(_ptr(xy_dev), n, k, _ptr(cand_out_dev), _stream_handle(stream))
     if status != 0:
         raise AcoError(status, "aco_build_candidates_noalloc", "")
+
+
+def aco_set_ant_range(h, ant_begin: int, ant_end: int):
+    _check(lib().aco_set_ant_range(h, ant_begin, ant_end), "aco_set_ant_range", h)
+
+
+def aco_export_commits(h, buf_dev, cap_words: int) -> int:
+    words = ctypes.c_int64()
+    _check(lib().aco_export_commits(h, _ptr(buf_dev), cap_words, ctypes.byref(words)), "aco_export_commits", h)
+    return int(words.value)
+
+
+def aco_import_commits(h, bufs_dev, count: int, stride_words: int):
+    _check(lib().aco_import_commits(h, _ptr(bufs_dev), count, stride_words), "aco_import_commits", h)
+
+
+def aco_probe_bandwidth(buf_dev, nbytes: int, mode: int, reps: int, stream=None) -> float:
+    """Milliseconds for `reps` passes of the bandwidth probe over the caller's buffer (mode 0: read
+    it; mode 1: copy its first half to its second half)."""
+    ms = ctypes.c_float()
+    status = lib().aco_probe_bandwidth(_ptr(buf_dev), nbytes, mode, reps, _stream_handle(stream), ctypes.byref(ms))
+    if status != 0:
+        raise AcoError(status, "aco_probe_bandwidth", "")
+    return float(ms.value)
 
 
 def aco_destroy_instance(h):

@@ -27,6 +27,8 @@ UNITS = [
     ("batch.cu", []),
     ("mlp.cu", []),
     ("localsearch.cu", []),
+    ("probe.cu", []),
+    ("shard.cu", []),
 ]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -50,7 +50,8 @@ static void free_all(aco_instance* inst) {
                     inst->seg, inst->antit, inst->accq, inst->tau, inst->etab_d, inst->W64d, inst->W32d,
                     inst->tours, inst->succ_d, inst->pred_d, inst->counters, inst->errflag, inst->xy32,
                     inst->ulist, inst->uxy, inst->bel, inst->btx, inst->btq, inst->deg, inst->ghk, inst->ghq,
-                    inst->ls_buf, inst->ls_sel, inst->ls_imp, inst->fcnt, inst->ccnt, inst->csize, inst->Qt};
+                    inst->ls_buf, inst->ls_sel, inst->ls_imp, inst->fcnt, inst->ccnt, inst->csize, inst->Qt,
+                    inst->rec_off, inst->nrec};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -159,6 +160,8 @@ extern "C" aco_status aco_create_instance(const double* xy_dev, const aco_params
         ok &= dalloc(&inst->uxy, m * inst->ucap, &total);
         ok &= dalloc(&inst->xy32, n, &total);
         ok &= dalloc(&inst->deg, n, &total);
+        ok &= dalloc(&inst->rec_off, m, &total);
+        ok &= dalloc(&inst->nrec, 1, &total);
     } else {
         ok &= dalloc(&inst->tau, n * n, &total);
         ok &= dalloc(&inst->etab_d, n * n, &total);
@@ -251,6 +254,8 @@ extern "C" aco_status aco_create_instance(const double* xy_dev, const aco_params
         }
     }
     inst->last_iteration = -1;
+    inst->ant0 = 0;
+    inst->ant1 = p->m;
     *out = inst;
     return ACO_OK;
 }
@@ -274,6 +279,7 @@ aco_status sync_and_check(aco_instance* inst, const char* what) {
         if (flag & DEVERR_BAD_TOUR) return set_err(inst, ACO_ERR_INVALID_ARG, "%s: tour index out of range", what);
         if (flag & DEVERR_NONFINITE) return set_err(inst, ACO_ERR_INVALID_ARG, "%s: non-finite weight", what);
         if (flag & DEVERR_BAD_SCORE) return set_err(inst, ACO_ERR_INVALID_ARG, "%s: edge score not finite and > 0", what);
+        if (flag & DEVERR_BAD_RECORD) return set_err(inst, ACO_ERR_INVALID_ARG, "%s: malformed commit record", what);
         return set_err(inst, ACO_ERR_CUDA, "%s: device error flag %d", what, flag);
     }
     return ACO_OK;
@@ -368,6 +374,8 @@ extern "C" aco_status aco_set_async_share(aco_instance* inst, int32_t on) {
     if (on != 0 && on != 1) return set_err(inst, ACO_ERR_INVALID_ARG, "set_async_share: on must be 0 or 1");
     if (on && inst->ls_p > 0.0)
         return set_err(inst, ACO_ERR_STATE, "set_async_share: local search is on (the two exclude each other)");
+    if (on && (inst->ant0 != 0 || inst->ant1 != inst->p.m))
+        return set_err(inst, ACO_ERR_STATE, "set_async_share: the colony is split over ranks");
     if (on && !inst->Qt) {
         if (cudaMalloc(&inst->Qt, sizeof(unsigned long long) * (size_t)inst->p.n * inst->p.k) != cudaSuccess) {
             cudaGetLastError();
@@ -420,6 +428,8 @@ extern "C" aco_status aco_get_stats(aco_instance* inst, aco_stats* out_host) {
     out_host->partial_ants = c[CNT_PARTIAL];
     out_host->full_ants = c[CNT_FULL];
     out_host->ls_moves = c[CNT_LS_MOVES];
+    out_host->fallback_rebuilt = c[CNT_FB_REBUILT];
+    out_host->fallback_scanned = c[CNT_FB_SCANNED];
     out_host->gbest = INFINITY;
     out_host->gbest_ant = -1;
     if (inst->initialized) {

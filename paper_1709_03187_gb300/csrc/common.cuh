@@ -171,6 +171,7 @@ enum : int {
     DEVERR_NONFINITE = 4,      // eta^beta or a weight is not finite
     DEVERR_NO_CHOICE = 8,      // an ant found no unvisited city (internal inconsistency)
     DEVERR_BAD_SCORE = 16,     // an edge score that is not finite and > 0
+    DEVERR_BAD_RECORD = 32,    // an imported commit record that does not fit the colony
 };
 
 // ------------------------------------------------------------------ grid
@@ -217,7 +218,12 @@ struct CandW {
     float w;
 };
 
-enum : int { CNT_DECISIONS = 0, CNT_FALLBACKS, CNT_RESOLVES, CNT_IMPROVED, CNT_PARTIAL, CNT_FULL, CNT_LS_MOVES, CNT_N };
+enum : int {
+    CNT_DECISIONS = 0, CNT_FALLBACKS, CNT_RESOLVES, CNT_IMPROVED, CNT_PARTIAL, CNT_FULL, CNT_LS_MOVES,
+    CNT_FB_REBUILT,   // sum over exhausted-list steps of the ant's rebuilt count M
+    CNT_FB_SCANNED,   // sum over exhausted-list steps of the remaining-list entries scanned
+    CNT_N
+};
 
 // ------------------------------------------------------------------ update kernel arguments
 struct CommitArgs {
@@ -325,6 +331,9 @@ struct aco_instance {
     int32_t async_share;   // partial rebuilds commit inside the construction launch
     unsigned long long* Qt;  // n*k integer pheromone of the candidate edges (allocated with async_share)
     bool in_batch;         // owned by a batch (advanced by the batch's launches only)
+    int32_t ant0, ant1;    // the ants this instance constructs (a rank's share of a sharded colony)
+    long long* rec_off;    // m: where each imported commit record starts
+    int32_t* nrec;         // 1: imported records
 
     // dense mode
     double* tau;           // n*n

@@ -42,6 +42,7 @@ struct LbestArgs {
     int fallback, iteration, initialized;
     int selection;  // 0 = Eq. 1 wheel, 1 = Independent Roulette
     int ucap;       // capacity of the per-ant remaining-city list
+    int ant0;       // first ant of the launch (a rank's share of a sharded colony)
     float coord_r;  // max |coordinate| (FP32 screen error bound)
     int ia, ib;     // alpha, beta as small integers (0..16) for the FP32 screen, else -1
     float tau0f, tau0powf;  // tau0 and tau0^alpha in FP32
@@ -1286,22 +1287,12 @@ __device__ void async_commit(const LbestArgs& A, int a, const AntIter& it, const
 // parameter.  Batched colonies (BATCH): warp w of block b takes ant slot b * warps + w, which
 // names (instance, ant); the descriptor comes from the per-instance array and the iteration
 // from device memory, so one captured launch serves every iteration.
-template <bool BATCH, int WARPS, int MINB>
-__global__ void __launch_bounds__(32 * WARPS, MINB) construct_lbest_kernel(const __grid_constant__ LbestArgs Ap,
-                                                                                   const __grid_constant__ BatchMap B) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int a = blockIdx.x, inst = 0;
-    if (BATCH) {
-        const int slot = blockIdx.x * WARPS + warp;
-        if (slot >= B.slots) return;  // no block-wide synchronisation below: warps are independent
-        const int2 sa = B.slot[slot];
-        inst = sa.x;
-        a = sa.y;
-    }
-    const LbestArgs& A = BATCH ? B.args[inst] : Ap;
-    const int iteration = BATCH ? *B.iteration : Ap.iteration;
-    unsigned char* my_smem = smem_raw + (BATCH ? (size_t)warp * B.smem_per_ant : 0);
+// One ant's tour of the iteration, built by one warp (lane = this thread's lane) in the ant's
+// shared memory my_smem: the draws of Algorithm 1, the visited set, the Eq. 1 decisions and the
+// exhausted-list steps, and the exact length.  BATCH: the ant belongs to a batched colony.
+template <bool BATCH>
+__device__ __forceinline__ void construct_ant(const LbestArgs& A, int a, int iteration, unsigned char* my_smem,
+                                              int lane) {
     // double-buffered copies of the candidate rows of the current city's unvisited candidates:
     // the next city is one of them, so its row is in shared memory when the next decision starts
     CandW(*stage)[STAGE_K][STAGE_K] = reinterpret_cast<CandW(*)[STAGE_K][STAGE_K]>(my_smem);
@@ -1370,7 +1361,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) construct_lbest_kernel(const
     const int scan_lim = k <= 16 ? 16 : 32;  // Kogge-Stone levels needed for k lanes
     double my_u = 0.0;
     float my_uf = 0.f;
-    unsigned long long nfall = 0, nres = 0;
+    unsigned long long nfall = 0, nres = 0, nfb_m = 0, nfb_scan = 0;
     const CandW* rowp = A.candw + (size_t)cur * k;  // current row (global or a staged copy)
     int wb = 0;                                      // staging buffer written this step
     int pend = -1;                                   // chosen city whose visited bit is set next step
@@ -1489,6 +1480,8 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) construct_lbest_kernel(const
             rowp = staged ? &stage[wb][pick][0] : A.candw + (size_t)j * k;
         } else {
             ++nfall;
+            nfb_m += (unsigned long long)M;
+            nfb_scan += (unsigned long long)(partial ? ucount : n - 1 - t);
             if (!partial && A.fallback == 0) {  // the cities chosen so far leave the unvisited counts
                 counts_remove(A, a, seg, counted, t + 1, lane);
                 counted = t + 1;
@@ -1537,9 +1530,30 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) construct_lbest_kernel(const
         A.antit[a] = it;
         atomicAdd(&A.counters[CNT_DECISIONS], (unsigned long long)steps);
         atomicAdd(&A.counters[CNT_FALLBACKS], nfall);
+        atomicAdd(&A.counters[CNT_FB_REBUILT], nfb_m);
+        atomicAdd(&A.counters[CNT_FB_SCANNED], nfb_scan);
         atomicAdd(&A.counters[CNT_RESOLVES], nres);
         atomicAdd(&A.counters[partial ? CNT_PARTIAL : CNT_FULL], 1ull);
     }
+}
+
+template <bool BATCH, int WARPS, int MINB>
+__global__ void __launch_bounds__(32 * WARPS, MINB) construct_lbest_kernel(const __grid_constant__ LbestArgs Ap,
+                                                                                   const __grid_constant__ BatchMap B) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int a = Ap.ant0 + (int)blockIdx.x, inst = 0;
+    if (BATCH) {
+        const int slot = blockIdx.x * WARPS + warp;
+        if (slot >= B.slots) return;  // no block-wide synchronisation below: warps are independent
+        const int2 sa = B.slot[slot];
+        inst = sa.x;
+        a = sa.y;
+    }
+    const LbestArgs& A = BATCH ? B.args[inst] : Ap;
+    const int iteration = BATCH ? *B.iteration : Ap.iteration;
+    unsigned char* my_smem = smem_raw + (BATCH ? (size_t)warp * B.smem_per_ant : 0);
+    construct_ant<BATCH>(A, a, iteration, my_smem, lane);
 }
 
 void fill_lbest_args(const aco_instance* inst, int32_t iteration, LbestArgs& A) {
@@ -1549,6 +1563,7 @@ void fill_lbest_args(const aco_instance* inst, int32_t iteration, LbestArgs& A) 
     A.seed = p.seed; A.fallback = p.fallback; A.iteration = iteration; A.initialized = inst->initialized ? 1 : 0;
     A.selection = p.selection;
     A.ucap = inst->ucap; A.coord_r = inst->coord_r;
+    A.ant0 = inst->ant0;
     const bool ia_ok = p.alpha >= 0 && p.alpha <= 16 && floor(p.alpha) == p.alpha;
     const bool ib_ok = p.beta >= 0 && p.beta <= 16 && floor(p.beta) == p.beta;
     A.ia = ia_ok ? (int)p.alpha : -1;
@@ -1590,7 +1605,7 @@ aco_status launch_construct_lbest(aco_instance* inst, int32_t iteration) {
         if (e != cudaSuccess) return set_err(inst, ACO_ERR_CUDA, "smem attribute: %s", cudaGetErrorString(e));
     }
     BatchMap none{};
-    construct_lbest_kernel<false, 1, 8><<<p.m, 32, smem, inst->stream>>>(A, none);
+    construct_lbest_kernel<false, 1, 8><<<inst->ant1 - inst->ant0, 32, smem, inst->stream>>>(A, none);
     return check_launch(inst, "construct_lbest_kernel");
 }
 

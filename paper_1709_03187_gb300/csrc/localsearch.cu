@@ -264,6 +264,8 @@ extern "C" aco_status aco_set_local_search(aco_instance* inst, double p, int32_t
     if (window < 2 || window > 4096) return set_err(inst, ACO_ERR_INVALID_ARG, "set_local_search: window in [2, 4096]");
     if (p > 0.0 && inst->async_share)
         return set_err(inst, ACO_ERR_STATE, "set_local_search: asynchronous sharing is on (the two exclude each other)");
+    if (p > 0.0 && (inst->ant0 != 0 || inst->ant1 != inst->p.m))
+        return set_err(inst, ACO_ERR_STATE, "set_local_search: the colony is split over ranks");
     if (p > 0.0 && !inst->ls_buf) {
         bool ok = cudaMalloc(&inst->ls_buf, sizeof(int) * (size_t)ACO_LS_MAX_ANTS * inst->p.n) == cudaSuccess;
         ok = ok && cudaMalloc(&inst->ls_sel, sizeof(int) * (ACO_LS_MAX_ANTS + 1)) == cudaSuccess;

@@ -31,3 +31,13 @@ def test_code_hash_ignores_comments_and_blank_lines_only(tmp_path):
     (csrc / "construct.cu").write_text(text.replace("#define FULL 0xffffffffu", "#define FULL 0xfffffffeu"))
     assert b.code_sha1("construct.cu") != h0
 
+
+
+def test_construct_byte_model():
+    """Per decision 3 x 4k + 4 B, per exhausted step 8m + 4M B, per rebuilt city 8 + 32 B."""
+    b = _bench()
+    assert b.construct_bytes_model(1, 0, 0, 16, 1024) == 12 * 16 + 4 + 40
+    assert b.construct_bytes_model(0, 1, 1000, 16, 1024) == 8 * 1024 + 4 * 1000
+    # the 200,000-city line: about 1e6 decisions, 6e4 exhausted steps with M about 1,000
+    assert 0.9e9 < b.construct_bytes_model(10 ** 6, 6 * 10 ** 4, 6 * 10 ** 7, 16, 1024) < 1.1e9
+    assert b.construct_bytes_layout(1, 16, 0) == 8 * 16 + 4 + 40

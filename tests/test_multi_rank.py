@@ -1,8 +1,8 @@
 """The N > 1 path of the benchmark on CPU: world size 2 over gloo (127.0.0.1).
 
-Ranks run independent replica colonies (the path has no exchange step), so the only
-cross-rank logic is the seed of each replica and the whole-job aggregation: the slowest rank's
-time and the sum of the units every rank processed.  The reference arm runs on rank 0 only."""
+The ranks run one colony split by ants (its exchange is tested in test_multi_rank_sharded.py);
+here: the whole-job aggregation (the slowest rank's time, the sum of the units every rank
+processed) and the reference arm, which runs on rank 0 only."""
 import os
 import socket
 
@@ -27,9 +27,8 @@ def _worker(rank, world, port, q):
         import bench
 
         t, u = bench.aggregate_over_ranks(1.0 + 0.5 * rank, 10.0 * (rank + 1), world, "cpu")
-        seed = bench.replica_seed(3, rank)
-        seeds = [None] * world
-        dist.all_gather_object(seeds, seed)
+        ranks = [None] * world
+        dist.all_gather_object(ranks, rank)
         ran_reference = []
 
         class _Args:
@@ -38,12 +37,12 @@ def _worker(rank, world, port, q):
         # rank != 0 returns before touching the oracle or any work
         if rank != 0:
             ran_reference.append(bench.run_reference(_Args()) is None)
-        q.put((rank, t, u, seeds, ran_reference))
+        q.put((rank, t, u, ranks, ran_reference))
     finally:
         dist.destroy_process_group()
 
 
-def test_two_ranks_aggregate_and_seed_replicas():
+def test_two_ranks_aggregate():
     world, port = 2, _free_port()
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
@@ -54,9 +53,9 @@ def test_two_ranks_aggregate_and_seed_replicas():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    for rank, t, u, seeds, ran in out:
+    for rank, t, u, ranks, ran in out:
         assert t == 1.5 and u == 30.0  # slowest rank's time; units of both ranks
-        assert seeds == [3, 4]          # distinct replica seeds
+        assert ranks == [0, 1]
         if rank == 1:
             assert ran == [True]
 
@@ -65,4 +64,3 @@ def test_single_rank_is_the_identity():
     import bench
 
     assert bench.aggregate_over_ranks(2.5, 7, 1) == (2.5, 7.0)
-    assert bench.replica_seed(9, 0) == 9

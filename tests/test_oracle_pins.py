@@ -395,3 +395,24 @@ def test_oracle_with_supplied_candidates_is_identical():
         a.iterate(it)
         b.iterate(it)
     assert np.array_equal(a.lbest, b.lbest) and np.array_equal(a.clen, b.clen)
+
+
+@pytest.mark.parametrize("p_partial,fallback", [(1.0, 0), (0.6, 1)])
+def test_threaded_construction_equals_sequential(p_partial, fallback):
+    """Ants spread over host threads build the same tours with the same counters."""
+    n, m = 400, 24
+    xy = aco_synth.clustered(n, 5, 0.03, 19)
+    kw = dict(mode=oracle.MODE_LBEST, n=n, m=m, k=8, max_mod_frac=0.3, p_partial=p_partial, seed=19,
+              fallback=fallback)
+    a, b = oracle.Oracle(xy, **kw), oracle.Oracle(xy, **kw)
+    for it in range(5):
+        a.construct(it)
+        b.construct(it, threads=5)
+        assert np.array_equal(a.newtours, b.newtours) and np.array_equal(a.newlen, b.newlen)
+        assert a.counters() == b.counters()
+        a.update()
+        b.update()
+    sub = np.array([3, 17, 5, 22], np.int32)
+    a.construct(5, ants=sub)
+    b.construct(5, ants=sub, threads=3)
+    assert np.array_equal(a.newtours[sub], b.newtours[sub])
