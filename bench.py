@@ -524,7 +524,7 @@ def run_batch(args):
     b.run(0, iters + 1, tune=True)
     stream.synchronize()
     t_batch = time.perf_counter() - t0
-    (warps, minb), tune_ms = b.schedule()
+    (sched, warps, minb, pull), tune_ms = b.schedule()
     best = b.best()
     b.close()
     order = np.argsort(ns)
@@ -547,7 +547,9 @@ def run_batch(args):
            "batched_instances_per_s": round(count / t_batch, 2), "batched_s": round(t_batch, 3),
            "per_instance_instances_per_s": round(count / t_inst_all, 3),
            "per_instance_s_estimated": round(t_inst_all, 2), "per_instance_sample": int(len(sample)),
-           "speedup": round(t_inst_all / t_batch, 1), "schedule_warps_per_block": warps, "schedule_min_blocks": minb,
+           "speedup": round(t_inst_all / t_batch, 1), "schedule": sched,
+           "schedule_kind": "persistent launch" if sched >= 8 else "four launches per iteration, CUDA graph",
+           "schedule_warps_per_block": warps, "schedule_min_blocks": minb, "schedule_ants_per_pull": pull,
            "tune_ms": [round(float(x), 3) for x in tune_ms], "mean_gbest": float(np.mean(best))}
     print(json.dumps(out))
 

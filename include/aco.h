@@ -238,20 +238,39 @@ aco_status aco_batch_create(const double* xy_dev, const int32_t* n_host, int32_t
                             void* stream, aco_batch** out);
 /* Candidate lists and eta^beta tables of every instance (as aco_build_candidates).  Synchronises. */
 aco_status aco_batch_build_candidates(aco_batch* b);
+/* Launch schedules of a batch: 0 .. 7 run an iteration as four launches over every colony
+ * (construct, commit, C_gbest and weights, pheromone rebuild) replayed as a CUDA graph, with 1-4
+ * ants per block and a register cap; 8 .. 11 run all iterations of a call in ONE persistent
+ * cooperative launch whose resident warps pull (instance, ant) slots and city chunks from device
+ * work queues, with grid-wide barriers between the phases (warps per block, register cap and
+ * ants per pull vary).  Every schedule gives the same results. */
+#define ACO_BATCH_SCHEDULES 12
+
 /* `iterations` iterations of every colony, keyed first_iteration, first_iteration + 1, ...  The
- * first call builds the initial tours in its first iteration.  tune != 0: the first (up to eight)
- * iterations of the first tuned call are timed with eight launch schedules (ants per block 1-4 and
- * a register cap per thread) and the fastest is kept.  Enqueued on the batch's stream. */
+ * first call builds the initial tours in its first iteration.  tune != 0 (and no schedule set by
+ * aco_batch_set_schedule): the first iterations of the first tuned call (one per schedule, up to
+ * twelve) are timed with every schedule and the fastest is kept.  Enqueued on the batch's stream.
+ * A persistent launch whose barrier wait runs out (aco_batch_set_wait_limit) ends early; the next
+ * aco_batch_get_state / aco_batch_get_best returns ACO_ERR_TIMEOUT and the batch cannot run any
+ * more (ACO_ERR_STATE). */
 aco_status aco_batch_run(aco_batch* b, int32_t first_iteration, int32_t iterations, int32_t tune);
 /* l_best tours (instance i at offset sum_{j<i} m_j n_j, row-major m_i x n_i) and lengths
  * (offset sum_{j<i} m_j); either pointer may be NULL.  Synchronises. */
 aco_status aco_batch_get_state(aco_batch* b, int32_t* lbest_out_dev, double* clen_out_dev);
 /* C_gbest of every instance (count doubles).  Synchronises. */
 aco_status aco_batch_get_best(aco_batch* b, double* best_len_host);
-/* The schedule in use (ants per block, minimum resident blocks per SM) and the tuning times
- * (8 floats, ms per iteration; 0 where not tuned).  Any pointer may be NULL. */
-aco_status aco_batch_schedule(const aco_batch* b, int32_t* warps_out, int32_t* min_blocks_out,
-                              float* tune_ms_out8);
+/* The schedule in use (0 .. ACO_BATCH_SCHEDULES - 1), its warps per block and minimum resident
+ * blocks per SM, its ants per pull (0 for the four-launch schedules), and the tuning times
+ * (ACO_BATCH_SCHEDULES floats, ms per iteration; 0 where not tuned).  Any pointer may be NULL. */
+aco_status aco_batch_schedule(const aco_batch* b, int32_t* schedule_out, int32_t* warps_out,
+                              int32_t* min_blocks_out, int32_t* ants_per_pull_out, float* tune_ms_out);
+/* Fix the schedule (0 .. ACO_BATCH_SCHEDULES - 1) for every later call, tuning off; -1 gives the
+ * choice back to the autotuner.  Host-side only. */
+aco_status aco_batch_set_schedule(aco_batch* b, int32_t schedule);
+/* The longest a warp of a persistent launch waits at one of its grid-wide barriers (default
+ * 10 s; 0 <= seconds <= 3600; 0 gives up at once, which makes a launch of more than one block
+ * end with ACO_ERR_TIMEOUT).  Host-side only. */
+aco_status aco_batch_set_wait_limit(aco_batch* b, double seconds);
 const char* aco_batch_last_error(const aco_batch* b);
 void aco_batch_destroy(aco_batch* b);
 

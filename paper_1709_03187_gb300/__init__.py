@@ -28,13 +28,14 @@ __all__ = [
     "aco_set_edge_scores", "EdgeScorer", "aco_set_max_mod_frac", "aco_set_p_partial", "linear_f_schedule",
     "aco_set_local_search",
     "aco_set_async_share", "aco_probe_bandwidth", "aco_set_ant_range", "aco_export_commits", "aco_import_commits",
-    "ShardedColony", "exchange_records",
+    "ShardedColony", "exchange_records", "aco_batch_set_schedule", "aco_batch_set_wait_limit", "ACO_BATCH_SCHEDULES",
 ]
 
 from .batch import Batch  # noqa: E402
 from ._ffi import (aco_batch_build_candidates, aco_batch_create, aco_batch_destroy, aco_batch_get_best,  # noqa: E402
                    aco_batch_get_state, aco_batch_run, aco_batch_schedule)
 from ._ffi import aco_export_commits, aco_import_commits, aco_probe_bandwidth, aco_set_ant_range  # noqa: E402
+from ._ffi import ACO_BATCH_SCHEDULES, aco_batch_set_schedule, aco_batch_set_wait_limit  # noqa: E402
 from .sharded import ShardedColony, exchange_records  # noqa: E402
 from ._ffi import (aco_build_candidates, aco_build_candidates_noalloc, aco_construct_tours, aco_create_instance, aco_destroy_instance,  # noqa: E402
                    aco_get_state, aco_get_stats, aco_set_state, aco_step_probs, aco_tour_lengths,

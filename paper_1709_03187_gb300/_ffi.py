@@ -78,7 +78,9 @@ def lib():
             "aco_batch_run": (S, [V, I32, I32, I32]),
             "aco_batch_get_state": (S, [V, V, V]),
             "aco_batch_get_best": (S, [V, V]),
-            "aco_batch_schedule": (S, [V, V, V, V]),
+            "aco_batch_schedule": (S, [V, V, V, V, V, V]),
+            "aco_batch_set_schedule": (S, [V, I32]),
+            "aco_batch_set_wait_limit": (S, [V, ctypes.c_double]),
             "aco_batch_last_error": (ctypes.c_char_p, [V]),
             "aco_batch_destroy": (None, [V]),
             "aco_batch_instance": (S, [V, I32, ctypes.POINTER(V)]),
@@ -210,15 +212,26 @@ def aco_batch_get_best(b, count: int):
     return out
 
 
+ACO_BATCH_SCHEDULES = 12
+
+
 def aco_batch_schedule(b):
+    """(schedule, warps per block, min blocks per SM, ants per pull (0: four launches)), tuning ms."""
     import numpy as np
 
-    w = ctypes.c_int32()
-    mb = ctypes.c_int32()
-    ms = np.zeros(8, np.float32)
-    _bcheck(lib().aco_batch_schedule(b, ctypes.byref(w), ctypes.byref(mb), ms.ctypes.data_as(ctypes.c_void_p)),
-            "aco_batch_schedule", b)
-    return (int(w.value), int(mb.value)), ms
+    sc, w, mb, pull = (ctypes.c_int32() for _ in range(4))
+    ms = np.zeros(ACO_BATCH_SCHEDULES, np.float32)
+    _bcheck(lib().aco_batch_schedule(b, ctypes.byref(sc), ctypes.byref(w), ctypes.byref(mb), ctypes.byref(pull),
+                                     ms.ctypes.data_as(ctypes.c_void_p)), "aco_batch_schedule", b)
+    return (int(sc.value), int(w.value), int(mb.value), int(pull.value)), ms
+
+
+def aco_batch_set_schedule(b, schedule: int):
+    _bcheck(lib().aco_batch_set_schedule(b, schedule), "aco_batch_set_schedule", b)
+
+
+def aco_batch_set_wait_limit(b, seconds: float):
+    _bcheck(lib().aco_batch_set_wait_limit(b, seconds), "aco_batch_set_wait_limit", b)
 
 
 def aco_batch_destroy(b):

@@ -47,7 +47,16 @@ class Batch:
         return _ffi.aco_batch_get_best(self._h, self.count)
 
     def schedule(self):
+        """((schedule, warps per block, min blocks per SM, ants per pull), tuning ms per schedule)."""
         return _ffi.aco_batch_schedule(self._h)
+
+    def set_schedule(self, schedule: int):
+        """Fix the launch schedule (0-7: four launches per iteration; 8-11: one persistent launch),
+        -1 = autotune."""
+        _ffi.aco_batch_set_schedule(self._h, schedule)
+
+    def set_wait_limit(self, seconds: float):
+        _ffi.aco_batch_set_wait_limit(self._h, seconds)
 
     def state(self):
         """Per-instance (l_best (m_i, n_i), lengths (m_i,)) as numpy arrays."""

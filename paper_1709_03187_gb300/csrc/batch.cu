@@ -5,11 +5,13 @@
 //   construction (ant slots ordered longest instance first; `warps` ants per block),
 //   commit (one block per ant slot), C_gbest and weights (one block per colony),
 //   pheromone rebuild (block map over every colony's cities),
-// plus a one-thread increment of the device iteration counter.  After the initial tours, the
-// iteration is captured once as a CUDA graph and replayed.  The schedule does not change any
-// result (each ant's work is deterministic), so the autotuner times live iterations with each
-// launch schedule -- ants per block and a register cap (minimum resident blocks per SM) -- and
-// keeps the fastest.
+// plus a one-thread increment of the device iteration counter, captured once as a CUDA graph and
+// replayed -- or all iterations of a call in one persistent cooperative launch (construct.cu:
+// work queues of ant slots and city chunks, grid-wide barriers with bounded waits).  The schedule
+// does not change any result (each ant's work is deterministic), so the autotuner times live
+// iterations with each schedule -- for the four launches, ants per block and a register cap
+// (minimum resident blocks per SM); for the persistent launch, warps per block, register cap and
+// ant slots per pull -- and keeps the fastest.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -35,6 +37,10 @@ cudaError_t launch_update_batch(const CommitArgs* cargs, const int2* slot, int s
                                 int k, cudaStream_t s);
 size_t lbest_args_size();
 void fill_lbest_args_bytes(const aco_instance* inst, int32_t iteration, void* out);
+cudaError_t launch_persistent_batch(PersistArgs P, int config, int num_sms, cudaStream_t s, int* grid_out);
+extern const int kPersistConfigs[ACO_PERSIST_CONFIGS][3];
+
+#define ACO_ALL_SCHEDULES (ACO_BATCH_CONFIGS + ACO_PERSIST_CONFIGS)
 
 __global__ void bump_iteration_kernel(int* it) { *it += 1; }
 
@@ -55,12 +61,19 @@ struct aco_batch {
     int4* d_rmap = nullptr;
     int* d_iter = nullptr;
     int slots = 0, rblocks = 0, smem_per_ant = 0, m_cap = 0;
-    int config = 0;  // index into kBatchConfigs
+    // schedule: 0 .. ACO_BATCH_CONFIGS-1 = four launches per iteration (kBatchConfigs), replayed
+    // as a CUDA graph; ACO_BATCH_CONFIGS + c = one persistent launch (kPersistConfigs[c])
+    int config = 0;
+    int pinned = -1;  // schedule fixed by the caller (no tuning), -1 = none
     bool tuned = false;
     cudaGraphExec_t graph[ACO_BATCH_CONFIGS] = {};
-    bool built = false, initialized = false;
+    bool built = false, initialized = false, failed = false;
     int iterations = 0;
-    float tune_ms[ACO_BATCH_CONFIGS] = {};
+    float tune_ms[ACO_ALL_SCHEDULES] = {};
+    int num_sms = 1;
+    unsigned* d_queue = nullptr;  // persistent launch: work counters (4) and barrier (2)
+    int* d_status = nullptr;      // bit 0: a barrier wait of a persistent launch ran out
+    unsigned long long wait_ns = 10000000000ull;
     char err[512] = {0};
 };
 
@@ -75,7 +88,8 @@ static void free_batch(aco_batch* b) {
     for (auto& g : b->graph)
         if (g) cudaGraphExecDestroy(g);
     for (aco_instance* i : b->inst) aco_destroy_instance(i);
-    void* ptrs[] = {b->d_largs, b->d_cargs, b->d_gargs, b->d_rargs, b->d_slot, b->d_rmap, b->d_iter};
+    void* ptrs[] = {b->d_largs, b->d_cargs, b->d_gargs, b->d_rargs, b->d_slot, b->d_rmap, b->d_iter, b->d_queue,
+                    b->d_status};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -147,6 +161,8 @@ extern "C" aco_status aco_batch_create(const double* xy_dev, const int32_t* n_ho
     ok &= cudaMalloc(&b->d_slot, sizeof(int2) * slot.size()) == cudaSuccess;
     ok &= cudaMalloc(&b->d_rmap, sizeof(int4) * rmap.size()) == cudaSuccess;
     ok &= cudaMalloc(&b->d_iter, sizeof(int)) == cudaSuccess;
+    ok &= cudaMalloc(&b->d_queue, sizeof(unsigned) * 8) == cudaSuccess;
+    ok &= cudaMalloc(&b->d_status, sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_batch(b);
@@ -155,6 +171,12 @@ extern "C" aco_status aco_batch_create(const double* xy_dev, const int32_t* n_ho
     }
     cudaMemcpy(b->d_slot, slot.data(), sizeof(int2) * slot.size(), cudaMemcpyHostToDevice);
     cudaMemcpy(b->d_rmap, rmap.data(), sizeof(int4) * rmap.size(), cudaMemcpyHostToDevice);
+    cudaMemset(b->d_queue, 0, sizeof(unsigned) * 8);
+    cudaMemset(b->d_status, 0, sizeof(int));
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (b->num_sms < 1) b->num_sms = 1;
     *out = b;
     return ACO_OK;
 }
@@ -204,6 +226,38 @@ static cudaError_t enqueue_iteration(aco_batch* b, int config) {
     return cudaGetLastError();
 }
 
+// `iterations` iterations in one persistent launch (schedule ACO_BATCH_CONFIGS + pc).
+static cudaError_t enqueue_persistent(aco_batch* b, int pc, int iterations) {
+    cudaError_t e = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned) * 5, b->stream);  // counters, arrivals
+    if (e != cudaSuccess) return e;
+    PersistArgs P{};
+    P.largs = reinterpret_cast<const LbestArgs*>(b->d_largs);
+    P.cargs = b->d_cargs;
+    P.gargs = b->d_gargs;
+    P.rargs = b->d_rargs;
+    P.slot = b->d_slot;
+    P.rmap = b->d_rmap;
+    P.slots = b->slots;
+    P.ritems = b->rblocks;
+    P.count = b->count;
+    P.iterations = iterations;
+    P.smem_per_ant = b->smem_per_ant;
+    P.m_cap = b->m_cap;
+    P.k = b->p.k;
+    P.iteration = b->d_iter;
+    P.queue = b->d_queue;
+    P.bar = b->d_queue + 4;
+    P.wait_ns = b->wait_ns;
+    P.status = b->d_status;
+    return launch_persistent_batch(P, pc, b->num_sms, b->stream, nullptr);
+}
+
+// One iteration with any schedule (four launches or one persistent launch).
+static cudaError_t enqueue_any(aco_batch* b, int schedule) {
+    if (schedule >= ACO_BATCH_CONFIGS) return enqueue_persistent(b, schedule - ACO_BATCH_CONFIGS, 1);
+    return enqueue_iteration(b, schedule);
+}
+
 static aco_status graph_for(aco_batch* b, int choice) {
     if (b->graph[choice]) return ACO_OK;
     cudaGraph_t g = nullptr;
@@ -226,14 +280,31 @@ static aco_status graph_for(aco_batch* b, int choice) {
     return ACO_OK;
 }
 
+// The persistent launch's barrier status: ACO_ERR_TIMEOUT once a wait ran out (the batch is then
+// unusable).  Synchronises.
+static aco_status check_status(aco_batch* b) {
+    if (b->failed) return berr(b, ACO_ERR_TIMEOUT, "a barrier wait of the persistent launch ran out");
+    int st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return berr(b, ACO_ERR_CUDA, cudaGetErrorString(e));
+    if (st & 1) {
+        b->failed = true;
+        return berr(b, ACO_ERR_TIMEOUT, "a barrier wait of the persistent launch ran out");
+    }
+    return ACO_OK;
+}
+
 extern "C" aco_status aco_batch_run(aco_batch* b, int32_t first_iteration, int32_t iterations, int32_t tune) {
     if (!b || iterations < 0 || first_iteration < 0) return ACO_ERR_INVALID_ARG;
     if (!b->built) return berr(b, ACO_ERR_STATE, "run before build_candidates");
+    if (b->failed) return berr(b, ACO_ERR_STATE, "the batch failed earlier (barrier wait ran out)");
     if (iterations == 0) return ACO_OK;
+    if (b->pinned >= 0) b->config = b->pinned;
     if (!b->initialized) {  // initial tours (Algorithm 1, before its iterations): every ant builds a full tour
         aco_status st = upload_args(b, first_iteration);
         if (st != ACO_OK) return st;
-        if (enqueue_iteration(b, b->config) != cudaSuccess) return berr(b, ACO_ERR_CUDA, "initial iteration failed");
+        if (enqueue_any(b, b->config) != cudaSuccess) return berr(b, ACO_ERR_CUDA, "initial iteration failed");
         for (aco_instance* i : b->inst) {
             i->initialized = true;
             i->iterations++;
@@ -248,19 +319,22 @@ extern "C" aco_status aco_batch_run(aco_batch* b, int32_t first_iteration, int32
         cudaMemcpyAsync(b->d_iter, &first_iteration, sizeof(int), cudaMemcpyHostToDevice, b->stream);
     }
     int done = 0;
-    if (tune && !b->tuned) {  // time live iterations with each schedule, keep the fastest
+    if (tune && !b->tuned && b->pinned < 0) {  // time live iterations with each schedule, keep the fastest
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         float best = 1e30f;
         int best_choice = 0;
-        for (int c = 0; c < ACO_BATCH_CONFIGS && done < iterations; ++c, ++done) {
-            aco_status st = graph_for(b, c);
-            if (st != ACO_OK) return st;
+        for (int c = 0; c < ACO_ALL_SCHEDULES && done < iterations; ++c, ++done) {
+            if (c < ACO_BATCH_CONFIGS) {
+                aco_status st = graph_for(b, c);
+                if (st != ACO_OK) return st;
+            }
             cudaEventRecord(e0, b->stream);
-            cudaGraphLaunch(b->graph[c], b->stream);
+            cudaError_t e = c < ACO_BATCH_CONFIGS ? cudaGraphLaunch(b->graph[c], b->stream) : enqueue_any(b, c);
             cudaEventRecord(e1, b->stream);
             cudaEventSynchronize(e1);
+            if (e != cudaSuccess) return berr(b, ACO_ERR_CUDA, cudaGetErrorString(e));
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
             b->tune_ms[c] = ms;
@@ -270,12 +344,22 @@ extern "C" aco_status aco_batch_run(aco_batch* b, int32_t first_iteration, int32
         cudaEventDestroy(e1);
         b->config = best_choice;
         b->tuned = true;
+        aco_status st = check_status(b);
+        if (st != ACO_OK) return st;
     }
     const int choice = b->config;
-    aco_status st = graph_for(b, choice);
-    if (st != ACO_OK) return st;
-    for (; done < iterations; ++done)
-        if (cudaGraphLaunch(b->graph[choice], b->stream) != cudaSuccess) return berr(b, ACO_ERR_CUDA, "graph launch failed");
+    if (choice >= ACO_BATCH_CONFIGS) {
+        if (done < iterations) {
+            cudaError_t e = enqueue_persistent(b, choice - ACO_BATCH_CONFIGS, iterations - done);
+            if (e != cudaSuccess) return berr(b, ACO_ERR_CUDA, cudaGetErrorString(e));
+        }
+    } else {
+        aco_status st = graph_for(b, choice);
+        if (st != ACO_OK) return st;
+        for (; done < iterations; ++done)
+            if (cudaGraphLaunch(b->graph[choice], b->stream) != cudaSuccess)
+                return berr(b, ACO_ERR_CUDA, "graph launch failed");
+    }
     for (aco_instance* i : b->inst) i->iterations += iterations;
     b->iterations += iterations;
     cudaError_t e = cudaGetLastError();
@@ -285,9 +369,11 @@ extern "C" aco_status aco_batch_run(aco_batch* b, int32_t first_iteration, int32
 
 extern "C" aco_status aco_batch_get_state(aco_batch* b, int32_t* lbest_out_dev, double* clen_out_dev) {
     if (!b) return ACO_ERR_INVALID_ARG;
+    aco_status st = check_status(b);
+    if (st != ACO_OK) return st;
     for (int i = 0; i < b->count; ++i) {
-        aco_status st = aco_get_state(b->inst[i], lbest_out_dev ? lbest_out_dev + b->tour_off[i] : nullptr,
-                                      clen_out_dev ? clen_out_dev + b->ant_off[i] : nullptr, nullptr);
+        st = aco_get_state(b->inst[i], lbest_out_dev ? lbest_out_dev + b->tour_off[i] : nullptr,
+                           clen_out_dev ? clen_out_dev + b->ant_off[i] : nullptr, nullptr);
         if (st != ACO_OK) return berr(b, st, aco_last_error(b->inst[i]));
     }
     return ACO_OK;
@@ -295,22 +381,41 @@ extern "C" aco_status aco_batch_get_state(aco_batch* b, int32_t* lbest_out_dev, 
 
 extern "C" aco_status aco_batch_get_best(aco_batch* b, double* best_len_host) {
     if (!b || !best_len_host) return ACO_ERR_INVALID_ARG;
+    aco_status st = check_status(b);
+    if (st != ACO_OK) return st;
     for (int i = 0; i < b->count; ++i) {
         aco_stats s;
-        aco_status st = aco_get_stats(b->inst[i], &s);
+        st = aco_get_stats(b->inst[i], &s);
         if (st != ACO_OK) return berr(b, st, aco_last_error(b->inst[i]));
         best_len_host[i] = s.gbest;
     }
     return ACO_OK;
 }
 
-extern "C" aco_status aco_batch_schedule(const aco_batch* b, int32_t* warps_out, int32_t* min_blocks_out,
-                                         float* tune_ms_out8) {
+extern "C" aco_status aco_batch_schedule(const aco_batch* b, int32_t* schedule_out, int32_t* warps_out,
+                                         int32_t* min_blocks_out, int32_t* persistent_out, float* tune_ms_out) {
     if (!b) return ACO_ERR_INVALID_ARG;
-    if (warps_out) *warps_out = kBatchConfigs[b->config][0];
-    if (min_blocks_out) *min_blocks_out = kBatchConfigs[b->config][1];
-    if (tune_ms_out8)
-        for (int c = 0; c < ACO_BATCH_CONFIGS; ++c) tune_ms_out8[c] = b->tune_ms[c];
+    const int c = b->config;
+    const bool pers = c >= ACO_BATCH_CONFIGS;
+    if (schedule_out) *schedule_out = c;
+    if (warps_out) *warps_out = pers ? kPersistConfigs[c - ACO_BATCH_CONFIGS][0] : kBatchConfigs[c][0];
+    if (min_blocks_out) *min_blocks_out = pers ? kPersistConfigs[c - ACO_BATCH_CONFIGS][1] : kBatchConfigs[c][1];
+    if (persistent_out) *persistent_out = pers ? kPersistConfigs[c - ACO_BATCH_CONFIGS][2] : 0;
+    if (tune_ms_out)
+        for (int i = 0; i < ACO_ALL_SCHEDULES; ++i) tune_ms_out[i] = b->tune_ms[i];
+    return ACO_OK;
+}
+
+extern "C" aco_status aco_batch_set_schedule(aco_batch* b, int32_t schedule) {
+    if (!b || schedule < -1 || schedule >= ACO_ALL_SCHEDULES) return ACO_ERR_INVALID_ARG;
+    b->pinned = schedule;
+    if (schedule >= 0) b->config = schedule;
+    return ACO_OK;
+}
+
+extern "C" aco_status aco_batch_set_wait_limit(aco_batch* b, double seconds) {
+    if (!b || !(seconds >= 0.0 && seconds <= 3600.0)) return ACO_ERR_INVALID_ARG;
+    b->wait_ns = (unsigned long long)(seconds * 1e9);
     return ACO_OK;
 }
 

@@ -17,7 +17,8 @@
 #include "../../include/aco.h"
 
 #define ACO_MAX_K 32
-#define ACO_BATCH_CONFIGS 8  // launch schedules the batch autotuner times
+#define ACO_BATCH_CONFIGS 8    // four-launch schedules the batch autotuner times
+#define ACO_PERSIST_CONFIGS 4  // persistent schedules it times as well
 
 typedef unsigned __int128 u128;
 
@@ -261,6 +262,23 @@ struct RebuildArgs {
     uint8_t* rowflag;
     int* errflag;
     unsigned long long* Qt;  // also stores the integer pheromone Q_ir when not null
+};
+
+// ------------------------------------------------------------------ persistent batched launch
+struct LbestArgs;  // construct.cu
+struct PersistArgs {
+    const LbestArgs* largs;
+    const CommitArgs* cargs;
+    const GbestArgs* gargs;
+    const RebuildArgs* rargs;
+    const int2* slot;        // ant slots (instance, ant), longest instance first
+    const int4* rmap;        // rebuild chunks (instance, first city, end city)
+    int slots, ritems, count, iterations, smem_per_ant, pull, m_cap, k;
+    int* iteration;          // device iteration counter, advanced at the end of each iteration
+    unsigned* queue;         // work counters of the construct, commit and rebuild phases (zero at launch)
+    unsigned* bar;           // barrier: [0] arrivals, [1] generation (arrivals zero at launch)
+    unsigned long long wait_ns;
+    int* status;             // bit 0: a barrier wait ran out
 };
 
 // ------------------------------------------------------------------ instance

@@ -20,20 +20,9 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "update_dev.cuh"
 
 #define FULL 0xffffffffu
-
-__device__ __forceinline__ void set_neighbours(int* __restrict__ nb, uint8_t* __restrict__ nbrank,
-                                               const int* __restrict__ cand, int m, int k, int a, int c, int succ,
-                                               int pred) {
-    const size_t e = ((size_t)c * m + a) * 2;
-    nb[e] = succ;
-    nb[e + 1] = pred;
-    uint8_t rs, rp;
-    ranks_of(cand, k, c, succ, pred, rs, rp);
-    nbrank[e] = rs;
-    nbrank[e + 1] = rp;
-}
 
 // One warp per ant.  Batched colonies: block b is ant slot b, naming (instance, ant).
 template <bool BATCH>
@@ -48,42 +37,7 @@ __global__ void __launch_bounds__(32) commit_kernel(const __grid_constant__ Comm
         a = sa.y;
     }
     const CommitArgs& C = BATCH ? batch[inst] : Cp;
-    const int n = C.n, m = C.m, k = C.k, lane = threadIdx.x;
-    const AntIter it = C.antit[a];
-    if (!(it.newlen < C.clen[a])) return;
-    int* L = C.lbest + (size_t)a * n;
-    const int* S = C.seg + (size_t)a * n;
-    if (it.s < 0) {
-        for (int t = lane; t < n; t += 32) L[t] = S[t];
-        __syncwarp();
-        for (int t = lane; t < n; t += 32)
-            set_neighbours(C.nb, C.nbrank, C.cand, m, k, a, S[t], S[t + 1 == n ? 0 : t + 1], S[t == 0 ? n - 1 : t - 1]);
-    } else {
-        const int e = L[(it.s + it.P - 1) % n];
-        const int start = L[it.s];
-        const int M = it.M;
-        __syncwarp();
-        for (int t = lane; t < M; t += 32) L[(it.s + it.P + t) % n] = S[t];
-        for (int t = lane; t < M; t += 32) {
-            const int pc = t == 0 ? e : S[t - 1];
-            const int sc = t == M - 1 ? start : S[t + 1];
-            set_neighbours(C.nb, C.nbrank, C.cand, m, k, a, S[t], sc, pc);
-        }
-        if (lane == 0) {
-            const size_t ee = ((size_t)e * m + a) * 2;
-            C.nb[ee] = S[0];
-            C.nbrank[ee] = rank_of(C.cand, k, e, S[0]);
-            const size_t es = ((size_t)start * m + a) * 2 + 1;
-            C.nb[es] = S[M - 1];
-            C.nbrank[es] = rank_of(C.cand, k, start, S[M - 1]);
-        }
-    }
-    if (lane == 0) {
-        C.clen[a] = it.newlen;
-        C.cfix[2 * a] = it.fix_lo;
-        C.cfix[2 * a + 1] = it.fix_hi;
-        atomicAdd(&C.counters[CNT_IMPROVED], 1ull);
-    }
+    commit_ant(C, a, threadIdx.x);
 }
 
 // One block per colony: C_gbest, its ant, and the per-ant deposit weights.  keep_prev: fold in
@@ -258,23 +212,8 @@ __global__ void __launch_bounds__(256) rebuild_kernel(const __grid_constant__ Re
             }
             __syncwarp();
         }
-        bool flag = false;
-        float w32 = 0.f;
-        if (lane < k) {
-            const size_t e = (size_t)i * k + lane;
-            const double tau = __dadd_rn(tau0, __dmul_rn(__ull2double_rn(Q), 0x1.0p-32));
-            const double wv = __dmul_rn(powr(tau, alpha), regq ? ecur : R.etab[e]);
-            w32 = __double2float_rn(wv);
-            if (!isfinite(wv)) atomicOr(R.errflag, DEVERR_NONFINITE);
-            flag = !(w32 >= FLT_MIN && w32 <= FLT_MAX);
-            R.W64[e] = wv;
-            if (R.Qt) R.Qt[e] = Q;
-        }
-        const unsigned fl = __ballot_sync(FULL, flag);
-        // a row the FP32 screen cannot represent carries negative screen weights: the
-        // construction kernel then evaluates it exactly in FP64
-        if (lane < k) R.candw[(size_t)i * k + lane].w = fl ? -1.0f : w32;
-        if (lane == 0) R.rowflag[i] = fl ? 1 : 0;
+        const double eta = lane < k ? (regq ? ecur : R.etab[(size_t)i * k + lane]) : 0.0;
+        finish_row(R, i, Q, eta, lane);
     }
 }
 
