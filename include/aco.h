@@ -84,6 +84,8 @@ typedef struct aco_stats {
                                   (n - 1 for a full construction)                            */
     uint64_t fallback_scanned; /* sum over exhausted-list steps of the remaining cities listed
                                   for the step (before the visited ones drop out)             */
+    uint64_t fallback_fast;  /* exhausted-list steps whose nearest unvisited city was found among
+                                the city's 32 nearest cities (no scan of the remaining ones)  */
 } aco_stats;
 
 typedef struct aco_instance aco_instance; /* opaque: owns all device state of one colony */

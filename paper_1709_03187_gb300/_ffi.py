@@ -39,6 +39,7 @@ class Stats(ctypes.Structure):
         ("improved", ctypes.c_uint64), ("partial_ants", ctypes.c_uint64), ("full_ants", ctypes.c_uint64),
         ("gbest", ctypes.c_double), ("gbest_ant", ctypes.c_int32), ("iterations", ctypes.c_int32),
         ("ls_moves", ctypes.c_uint64), ("fallback_rebuilt", ctypes.c_uint64), ("fallback_scanned", ctypes.c_uint64),
+        ("fallback_fast", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:

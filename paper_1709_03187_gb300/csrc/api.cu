@@ -51,7 +51,7 @@ static void free_all(aco_instance* inst) {
                     inst->tours, inst->succ_d, inst->pred_d, inst->counters, inst->errflag, inst->xy32,
                     inst->ulist, inst->uxy, inst->bel, inst->btx, inst->btq, inst->deg, inst->ghk, inst->ghq,
                     inst->ls_buf, inst->ls_sel, inst->ls_imp, inst->fcnt, inst->ccnt, inst->csize, inst->Qt,
-                    inst->rec_off, inst->nrec};
+                    inst->rec_off, inst->nrec, inst->ext};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -162,6 +162,10 @@ extern "C" aco_status aco_create_instance(const double* xy_dev, const aco_params
         ok &= dalloc(&inst->deg, n, &total);
         ok &= dalloc(&inst->rec_off, m, &total);
         ok &= dalloc(&inst->nrec, 1, &total);
+        // extended neighbour lists speed up the exhausted-list rule
+        inst->kx = (int32_t)(n - 1 < ACO_KX ? n - 1 : ACO_KX);
+        if (inst->kx > k) ok &= dalloc(&inst->ext, n * inst->kx, &total);
+        else inst->kx = 0;
     } else {
         ok &= dalloc(&inst->tau, n * n, &total);
         ok &= dalloc(&inst->etab_d, n * n, &total);
@@ -430,6 +434,7 @@ extern "C" aco_status aco_get_stats(aco_instance* inst, aco_stats* out_host) {
     out_host->ls_moves = c[CNT_LS_MOVES];
     out_host->fallback_rebuilt = c[CNT_FB_REBUILT];
     out_host->fallback_scanned = c[CNT_FB_SCANNED];
+    out_host->fallback_fast = c[CNT_FB_FAST];
     out_host->gbest = INFINITY;
     out_host->gbest_ant = -1;
     if (inst->initialized) {

@@ -28,6 +28,7 @@ enum : uint32_t { PURPOSE_WHEEL = 0, PURPOSE_START = 1, PURPOSE_KEEP = 2, PURPOS
 #define ACO_CBLK 8            // grid cells per edge of a coarse block (nearest-unvisited search)
 #define ACO_LS_MAX_ANTS 8     // ants improved by local search per iteration, at most
 #define ACO_LS_MAX_PASSES 16  // windowed 2-opt passes, at most
+#define ACO_KX 32             // extended neighbour list: the 32 nearest cities (candidates first)
 
 struct Draw4 { uint32_t x0, x1, x2, x3; };
 
@@ -223,6 +224,7 @@ enum : int {
     CNT_DECISIONS = 0, CNT_FALLBACKS, CNT_RESOLVES, CNT_IMPROVED, CNT_PARTIAL, CNT_FULL, CNT_LS_MOVES,
     CNT_FB_REBUILT,   // sum over exhausted-list steps of the ant's rebuilt count M
     CNT_FB_SCANNED,   // sum over exhausted-list steps of the remaining-list entries scanned
+    CNT_FB_FAST,      // exhausted-list steps whose nearest remaining city came from the extended list
     CNT_N
 };
 
@@ -352,6 +354,8 @@ struct aco_instance {
     int32_t ant0, ant1;    // the ants this instance constructs (a rank's share of a sharded colony)
     long long* rec_off;    // m: where each imported commit record starts
     int32_t* nrec;         // 1: imported records
+    int32_t kx;            // extended list length min(ACO_KX, n - 1) (0 = no extended list)
+    int32_t* ext;          // n*kx: the kx nearest other cities, key (d^2, index); its first k are the candidates
 
     // dense mode
     double* tau;           // n*n

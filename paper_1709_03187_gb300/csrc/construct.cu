@@ -44,6 +44,8 @@ struct LbestArgs {
     int selection;  // 0 = Eq. 1 wheel, 1 = Independent Roulette
     int ucap;       // capacity of the per-ant remaining-city list
     int ant0;       // first ant of the launch (a rank's share of a sharded colony)
+    int kx;         // extended list length (0 = none)
+    const int* __restrict__ ext;                 // n*kx nearest cities (candidates first)
     float coord_r;  // max |coordinate| (FP32 screen error bound)
     int ia, ib;     // alpha, beta as small integers (0..16) for the FP32 screen, else -1
     float tau0f, tau0powf;  // tau0 and tau0^alpha in FP32
@@ -789,13 +791,66 @@ __device__ int wheel_all_unvisited(const LbestArgs& A, int a, int cur, double u,
     return choice;
 }
 
+// The extended list of `cur` holds its kx nearest cities, key (d^2, index), candidates first.  At
+// an exhausted step every candidate is visited, so the first unvisited entry of rank >= k is the
+// nearest unvisited city c1, and every other unvisited city lies at least as far as the next
+// unvisited entry c2 -- or, when there is none, as the last entry (every city outside the list
+// is at least that far).  Both helpers give up (false / -1) when the list holds no unvisited city
+// or only its last entry; the caller then takes the full path.
+
+// Full construction before any pheromone (initial tours, tau = tau0 everywhere): the nearest
+// unvisited city wins unless the runner-up lies within 2^-40 of it (a possible tie of the rounded
+// weights), compared exactly in FP64.
+__device__ int ext_full_choice(const LbestArgs& A, int cur, const uint32_t* bits, int lane) {
+    __syncwarp();  // the previous city's visited bit is visible
+    const int kx = A.kx, k = A.k;
+    const int e = lane < kx ? __ldg(A.ext + (size_t)cur * kx + lane) : -1;
+    const unsigned um = __ballot_sync(FULL, lane >= k && lane < kx && !is_visited(bits, e));
+    const unsigned more = um & (um - 1u);
+    const int r1 = __ffs(um) - 1;
+    if (um == 0u || (!more && r1 == kx - 1)) return -1;
+    const int r2 = more ? __ffs(more) - 1 : kx - 1;
+    const int c1 = __shfl_sync(FULL, e, r1), c2 = __shfl_sync(FULL, e, r2);
+    const double qx = A.xy[2 * cur], qy = A.xy[2 * cur + 1];
+    const double d1 = dist2(qx, qy, A.xy[2 * c1], A.xy[2 * c1 + 1]);
+    const double d2 = dist2(qx, qy, A.xy[2 * c2], A.xy[2 * c2 + 1]);
+    return d2 > __dmul_rn(d1, 1.0 + 0x1.0p-40) ? c1 : -1;
+}
+
+// Partial rebuild: the two nearest remaining cities at tau0 as the remaining-city scan gives them
+// (FP32 squared distances; lane 0 holds d1 with its city y1 and the runner-up bound d2s, every
+// other lane FLT_MAX), from the extended list instead of a scan.
+__device__ __forceinline__ bool ext_nearest(const LbestArgs& A, int cur, const uint32_t* bits, int lane, float2 q32,
+                                            float& d1, float& d2s, int& y1) {
+    const int kx = A.kx, k = A.k;
+    const int e = lane < kx ? __ldg(A.ext + (size_t)cur * kx + lane) : -1;
+    const unsigned um = __ballot_sync(FULL, lane >= k && lane < kx && !is_visited(bits, e));
+    const unsigned more = um & (um - 1u);
+    const int r1 = __ffs(um) - 1;
+    if (um == 0u || (!more && r1 == kx - 1)) return false;
+    const int r2 = more ? __ffs(more) - 1 : kx - 1;
+    const int c1 = __shfl_sync(FULL, e, r1), c2 = __shfl_sync(FULL, e, r2);
+    d1 = FLT_MAX;
+    d2s = FLT_MAX;
+    y1 = 0x7fffffff;
+    if (lane == 0) {
+        const float2 p1 = A.xy32[c1], p2 = A.xy32[c2];
+        const float ax = __fsub_rn(p1.x, q32.x), ay = __fsub_rn(p1.y, q32.y);
+        const float bx = __fsub_rn(p2.x, q32.x), by = __fsub_rn(p2.y, q32.y);
+        d1 = __fadd_rn(__fmul_rn(ax, ax), __fmul_rn(ay, ay));
+        d2s = __fadd_rn(__fmul_rn(bx, bx), __fmul_rn(by, by));
+        y1 = c1;
+    }
+    return true;
+}
+
 // Exhausted step of a partial rebuild with every weight first estimated in FP32, each with a
 // relative error bound E (FP32 coordinates and distances, reciprocal, powers, tau).  If the best
 // estimate beats the second best by more than the bounds allow, it is the exact FP64 argmax and
 // is returned without any FP64 work; otherwise -1 (the caller then evaluates exactly).  The
 // remaining list is compacted on the way.
 __device__ int partial_choice_fast(const LbestArgs& A, int a, int cur, const uint32_t* bits, int& ucount, BoostSmem& sh,
-                                   int lane, const RankRow* pre) {
+                                   int lane, const RankRow* pre, unsigned long long& nfast) {
     int* ul = A.ulist + (size_t)a * A.ucap;
     float2* uxy = A.uxy + (size_t)a * A.ucap;
     const float2 q32 = A.xy32[cur];
@@ -804,7 +859,11 @@ __device__ int partial_choice_fast(const LbestArgs& A, int a, int cur, const uin
     // unboosted cities: the weight only falls with the distance, so keep the two nearest
     float d1 = FLT_MAX, d2s = FLT_MAX;
     int y1 = 0x7fffffff;
-    int cnt = 0;
+    int cnt = ucount;
+    if (A.kx && ext_nearest(A, cur, bits, lane, q32, d1, d2s, y1)) {
+        ++nfast;  // the list is compacted by a later scan
+    } else {
+    cnt = 0;
     for (int base = 0; base < ucount; base += 256) {
         int id[8];
         float2 p[8];
@@ -840,6 +899,7 @@ __device__ int partial_choice_fast(const LbestArgs& A, int a, int cur, const uin
             }
             cnt += __popc(b);
         }
+    }
     }
     if (d1 < FLT_MAX) {
         dmin = d1;
@@ -943,6 +1003,29 @@ __device__ __forceinline__ void scan_remaining(int* ul, float2* uxy, int& ucount
     ucount = cnt;
 }
 
+// Warp top-2 of the lanes' FP32 weight estimates, by reductions over the bit patterns of
+// non-negative floats (their order): the best estimate (ties: the lower city; one lane is taken as
+// its holder) and the best of all the other estimates; the winner is returned when it beats the
+// runner-up by more than the estimates' relative error bound E (FP32 coordinates and distances,
+// reciprocal, powers, tau; largest at the smallest squared distance dmin), else -1.
+__device__ __forceinline__ int top2_decide(const LbestArgs& A, int lane, float w1, int x1, float w2, float dmin) {
+    const unsigned wb = __float_as_uint(fmaxf(w1, 0.f));
+    const unsigned wmax = __reduce_max_sync(FULL, wb);
+    const unsigned xmin = __reduce_min_sync(FULL, wb == wmax ? (unsigned)x1 : 0xFFFFFFFFu);
+    const unsigned win = __ballot_sync(FULL, wb == wmax && (unsigned)x1 == xmin);
+    const float rest = lane == __ffs(win) - 1 ? w2 : fmaxf(w1, w2);
+    w2 = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(fmaxf(rest, 0.f))));
+    w1 = __uint_as_float(wmax);
+    x1 = (int)xmin;
+    dmin = __uint_as_float(__reduce_min_sync(FULL, __float_as_uint(dmin)));
+    if (!(dmin >= 1e-30f) || !(w1 > 0.f) || !(w1 <= FLT_MAX)) return -1;
+    const float eps_d = __fdiv_rn(__fmul_rn(1.1f, d2_bound(dmin, A.coord_r)), dmin);
+    const float E = __fmul_rn(1.25f, __fadd_rn(__fmul_rn(0.5f * (float)A.ib + 0.5f, eps_d),
+                                               __fmul_rn((float)(A.ib + A.ia + 4), 0x1.0p-22f)));
+    if (!(E < 0.25f)) return -1;
+    return __fmul_rn(w1, 1.f - E) > __fmul_rn(w2, 1.f + E) ? x1 : -1;
+}
+
 // FP32 estimates of the hashed cities (slots lane + 32 s, coordinates in hp) with their tau and of
 // the nearest remaining cities at tau0; the best estimate is returned when it wins by more than
 // the error bounds allow (the hash is emptied), else -1 (the hash is kept for hashed_exact).
@@ -968,30 +1051,9 @@ __device__ __forceinline__ int hashed_decision(const LbestArgs& A, BoostSmem& sh
         top2_push(__fmul_rn(A.tau0powf, weight_f32(1.f, d1, 0, A.ib)), y1, w1, x1, w2);
         if (d2s < FLT_MAX) w2 = fmaxf(w2, __fmul_rn(A.tau0powf, weight_f32(1.f, d2s, 0, A.ib)));
     }
-    // warp top-2 by reductions over the bit patterns of non-negative floats (their order): the
-    // best estimate (ties: the lower city; one lane is taken as its holder) and the best of all
-    // the other estimates
-    {
-        const unsigned wb = __float_as_uint(fmaxf(w1, 0.f));
-        const unsigned wmax = __reduce_max_sync(FULL, wb);
-        const unsigned xmin = __reduce_min_sync(FULL, wb == wmax ? (unsigned)x1 : 0xFFFFFFFFu);
-        const unsigned win = __ballot_sync(FULL, wb == wmax && (unsigned)x1 == xmin);
-        const float rest = lane == __ffs(win) - 1 ? w2 : fmaxf(w1, w2);
-        w2 = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(fmaxf(rest, 0.f))));
-        w1 = __uint_as_float(wmax);
-        x1 = (int)xmin;
-        dmin = __uint_as_float(__reduce_min_sync(FULL, __float_as_uint(dmin)));
-    }
-    if (!(dmin >= 1e-30f) || !(w1 > 0.f) || !(w1 <= FLT_MAX)) return -1;
-    const float eps_d = __fdiv_rn(__fmul_rn(1.1f, d2_bound(dmin, A.coord_r)), dmin);
-    const float E = __fmul_rn(1.25f, __fadd_rn(__fmul_rn(0.5f * (float)A.ib + 0.5f, eps_d),
-                                               __fmul_rn((float)(A.ib + A.ia + 4), 0x1.0p-22f)));
-    if (!(E < 0.25f)) return -1;
-    if (__fmul_rn(w1, 1.f - E) > __fmul_rn(w2, 1.f + E)) {
-        bhash_clear(sh, lane);
-        return x1;
-    }
-    return -1;
+    const int win = top2_decide(A, lane, w1, x1, w2, dmin);
+    if (win >= 0) bhash_clear(sh, lane);
+    return win;
 }
 
 // Exhausted step of a partial rebuild, FP32-screened as partial_choice_fast, with the boosted
@@ -1008,14 +1070,18 @@ __device__ __forceinline__ int hashed_decision(const LbestArgs& A, BoostSmem& sh
 // empty again); -1 when the estimates are too close (the hash is kept for hashed_exact); -2 when
 // the hash overflowed (emptied).
 __device__ int partial_choice_hashed(const LbestArgs& A, int a, int cur, const uint32_t* bits, int& ucount,
-                                     BoostSmem& sh, int lane, const RankRow& rr) {
+                                     BoostSmem& sh, int lane, const RankRow& rr, unsigned long long& nfast) {
     int* ul = A.ulist + (size_t)a * A.ucap;
     float2* uxy = A.uxy + (size_t)a * A.ucap;
     const int* irow = A.nb + (size_t)cur * A.m * 2;
     int id[8];
     float2 p[8];
-    load_remaining(ul, uxy, 0, ucount, lane, id, p);  // in flight while the hash is built
     const float2 q32 = A.xy32[cur];
+    float d1, d2s;
+    int y1;
+    // the nearest remaining cities from the extended list, else by a scan of the remaining list
+    const bool from_ext = A.kx && ext_nearest(A, cur, bits, lane, q32, d1, d2s, y1);
+    if (!from_ext) load_remaining(ul, uxy, 0, ucount, lane, id, p);  // in flight while the hash is built
     // 1a. entry e of the rank row sits in lane (e % 512) / 16 at byte (e / 512) * 16 + e % 16;
     //     bit 4 * word + byte of bm marks a non-candidate entry
     unsigned long long bm = 0;
@@ -1079,9 +1145,8 @@ __device__ int partial_choice_hashed(const LbestArgs& A, int a, int cur, const u
         bhash_clear(sh, lane);
         return -2;
     }
-    float d1, d2s;
-    int y1;
-    scan_remaining(ul, uxy, ucount, lane, q32, bits, id, p, d1, d2s, y1);
+    if (from_ext) ++nfast;
+    else scan_remaining(ul, uxy, ucount, lane, q32, bits, id, p, d1, d2s, y1);
     return hashed_decision(A, sh, lane, q32, hx, hp, d1, d2s, y1);
 }
 
@@ -1104,7 +1169,7 @@ __device__ void hashed_exact(const LbestArgs& A, BoostSmem& sh, int lane, double
 // staged: the candidate rows are staged (even k <= 16); the hashed step serves those colonies,
 // partial_choice_fast the others (measured faster for them).
 __device__ int exhausted_choice(const LbestArgs& A, int a, int cur, double u, bool partial, bool staged,
-                                int& ucount, const uint32_t* bits, BoostSmem& sh, int lane) {
+                                int& ucount, const uint32_t* bits, BoostSmem& sh, int lane, unsigned long long& nfast) {
     __syncwarp();  // the previous city's visited bit (set at the top of the step) is visible
     const double qx = A.xy[2 * cur], qy = A.xy[2 * cur + 1];
     const double tau0pow = powr(A.tau0, A.alpha);
@@ -1118,7 +1183,7 @@ __device__ int exhausted_choice(const LbestArgs& A, int a, int cur, double u, bo
         const bool pre = A.initialized && (A.m & 7) == 0 && A.m <= 1024;
         if (pre) load_rank_row(A, cur, lane, rr);
         if (partial && A.ia >= 0 && A.ib >= 0 && pre && staged) {
-            const int fast = partial_choice_hashed(A, a, cur, bits, ucount, sh, lane, rr);
+            const int fast = partial_choice_hashed(A, a, cur, bits, ucount, sh, lane, rr, nfast);
             if (fast >= 0) return fast;
             if (fast == -1) {  // near tie: exact weights of the near-nearest and of the hashed cities
                 remaining_argmax(A, a, cur, bits, ucount, lane, qx, qy, tau0pow, bw, bc);
@@ -1126,7 +1191,7 @@ __device__ int exhausted_choice(const LbestArgs& A, int a, int cur, double u, bo
                 decided = true;
             }
         } else if (partial && A.ia >= 0 && A.ib >= 0) {
-            const int fast = partial_choice_fast(A, a, cur, bits, ucount, sh, lane, pre ? &rr : nullptr);
+            const int fast = partial_choice_fast(A, a, cur, bits, ucount, sh, lane, pre ? &rr : nullptr, nfast);
             if (fast >= 0) return fast;
         }
         if (!decided) {
@@ -1362,7 +1427,7 @@ __device__ __forceinline__ void construct_ant(const LbestArgs& A, int a, int ite
     const int scan_lim = k <= 16 ? 16 : 32;  // Kogge-Stone levels needed for k lanes
     double my_u = 0.0;
     float my_uf = 0.f;
-    unsigned long long nfall = 0, nres = 0, nfb_m = 0, nfb_scan = 0;
+    unsigned long long nfall = 0, nres = 0, nfb_m = 0, nfb_scan = 0, nfast = 0;
     const CandW* rowp = A.candw + (size_t)cur * k;  // current row (global or a staged copy)
     int wb = 0;                                      // staging buffer written this step
     int pend = -1;                                   // chosen city whose visited bit is set next step
@@ -1483,12 +1548,19 @@ __device__ __forceinline__ void construct_ant(const LbestArgs& A, int a, int ite
             ++nfall;
             nfb_m += (unsigned long long)M;
             nfb_scan += (unsigned long long)(partial ? ucount : n - 1 - t);
-            if (!partial && A.fallback == 0) {  // the cities chosen so far leave the unvisited counts
-                counts_remove(A, a, seg, counted, t + 1, lane);
-                counted = t + 1;
+            j = -1;
+            if (A.kx && A.fallback == 0 && !partial && !A.initialized) {  // the extended list first
+                j = ext_full_choice(A, cur, bits, lane);
+                if (j >= 0) ++nfast;
             }
-            j = exhausted_choice(A, a, cur, __shfl_sync(FULL, my_u, t & 31), partial, staged, ucount, bits, boost,
-                                 lane);
+            if (j < 0) {
+                if (!partial && A.fallback == 0) {  // the cities chosen so far leave the unvisited counts
+                    counts_remove(A, a, seg, counted, t + 1, lane);
+                    counted = t + 1;
+                }
+                j = exhausted_choice(A, a, cur, __shfl_sync(FULL, my_u, t & 31), partial, staged, ucount, bits,
+                                     boost, lane, nfast);
+            }
             rowp = A.candw + (size_t)j * k;
         }
         wb ^= 1;
@@ -1533,6 +1605,7 @@ __device__ __forceinline__ void construct_ant(const LbestArgs& A, int a, int ite
         atomicAdd(&A.counters[CNT_FALLBACKS], nfall);
         atomicAdd(&A.counters[CNT_FB_REBUILT], nfb_m);
         atomicAdd(&A.counters[CNT_FB_SCANNED], nfb_scan);
+        atomicAdd(&A.counters[CNT_FB_FAST], nfast);
         atomicAdd(&A.counters[CNT_RESOLVES], nres);
         atomicAdd(&A.counters[partial ? CNT_PARTIAL : CNT_FULL], 1ull);
     }
@@ -1565,6 +1638,8 @@ void fill_lbest_args(const aco_instance* inst, int32_t iteration, LbestArgs& A) 
     A.selection = p.selection;
     A.ucap = inst->ucap; A.coord_r = inst->coord_r;
     A.ant0 = inst->ant0;
+    A.kx = inst->ext ? inst->kx : 0;
+    A.ext = inst->ext;
     const bool ia_ok = p.alpha >= 0 && p.alpha <= 16 && floor(p.alpha) == p.alpha;
     const bool ib_ok = p.beta >= 0 && p.beta <= 16 && floor(p.beta) == p.beta;
     A.ia = ia_ok ? (int)p.alpha : -1;
@@ -1775,7 +1850,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) persistent_batch_kernel(cons
 }
 
 // Persistent schedules: (warps per block, minimum resident blocks per SM, slots per pull).
-extern const int kPersistConfigs[ACO_PERSIST_CONFIGS][3] = {{4, 4, 1}, {4, 8, 1}, {8, 2, 2}, {2, 16, 1}};
+extern const int kPersistConfigs[ACO_PERSIST_CONFIGS][3] = {{1, 32, 1}, {2, 16, 1}, {4, 8, 1}, {4, 4, 1}};
 
 size_t persistent_smem_bytes(int smem_per_ant, int warps, int m_cap, int k) {
     const size_t c = (size_t)smem_per_ant * warps;
@@ -1791,10 +1866,10 @@ cudaError_t launch_persistent_batch(PersistArgs P, int config, int num_sms, cuda
     const size_t smem = persistent_smem_bytes(P.smem_per_ant, warps, P.m_cap, P.k);
     void (*kern)(PersistArgs) = nullptr;
     switch (config) {
-        case 0: kern = persistent_batch_kernel<4, 4>; break;
-        case 1: kern = persistent_batch_kernel<4, 8>; break;
-        case 2: kern = persistent_batch_kernel<8, 2>; break;
-        case 3: kern = persistent_batch_kernel<2, 16>; break;
+        case 0: kern = persistent_batch_kernel<1, 32>; break;
+        case 1: kern = persistent_batch_kernel<2, 16>; break;
+        case 2: kern = persistent_batch_kernel<4, 8>; break;
+        case 3: kern = persistent_batch_kernel<4, 4>; break;
         default: return cudaErrorInvalidValue;
     }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

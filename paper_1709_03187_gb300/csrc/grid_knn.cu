@@ -174,6 +174,25 @@ __global__ void dense_eta_kernel(const double* __restrict__ xy, int n, double be
     }
 }
 
+// Candidate lists, their screen entries and eta^beta from the first k entries of the extended
+// lists (the same (d^2, index) keys, so the same lists knn_kernel<false> writes).
+__global__ void cand_from_ext_kernel(const double* __restrict__ xy, int n, int k, int kx, double beta,
+                                     const int* __restrict__ ext, int* __restrict__ cand, CandW* __restrict__ candw,
+                                     double* __restrict__ etab, int* __restrict__ errflag) {
+    const long long total = (long long)n * k;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / k), r = (int)(e % k);
+        const int j = ext[(size_t)i * kx + r];
+        cand[e] = j;
+        candw[e].city = j;
+        const double d2 = dist2(xy[2 * i], xy[2 * i + 1], xy[2 * j], xy[2 * j + 1]);
+        if (d2 == 0.0) atomicOr(errflag, DEVERR_DUPLICATE);
+        const double v = eta_pow_from_d2(d2, beta);
+        if (!isfinite(v)) atomicOr(errflag, DEVERR_NONFINITE);
+        etab[e] = v;
+    }
+}
+
 __global__ void xy32_kernel(const double* __restrict__ xy, int n, float2* __restrict__ xy32) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         xy32[i] = make_float2(__double2float_rn(xy[2 * i]), __double2float_rn(xy[2 * i + 1]));
@@ -203,6 +222,18 @@ aco_status launch_build_grid_and_knn(aco_instance* inst) {
     if (st != ACO_OK) return st;
     const int warps_per_block = 8;
     const int kblocks = (int)fmin((double)inst->num_sms * 16, (double)ceil_div(n, warps_per_block));
+    if (inst->ext) {
+        // the kx nearest cities once; the candidate lists are their first k (the same keys)
+        knn_kernel<true><<<kblocks, 32 * warps_per_block, 0, s>>>(inst->xy, inst->grid_dev, inst->city_cell,
+                                                                  inst->cell_start, inst->cell_city, inst->cell_xy, n,
+                                                                  inst->kx, 0.0, inst->ext, nullptr, nullptr,
+                                                                  inst->errflag);
+        const long long total = (long long)n * inst->p.k;
+        cand_from_ext_kernel<<<(int)fmin((double)inst->num_sms * 8, (double)ceil_div(total, 256)), 256, 0, s>>>(
+            inst->xy, n, inst->p.k, inst->kx, inst->p.beta, inst->ext, inst->cand, inst->candw, inst->etab,
+            inst->errflag);
+        return check_launch(inst, "knn_kernel (extended lists)");
+    }
     knn_kernel<false><<<kblocks, 32 * warps_per_block, 0, s>>>(inst->xy, inst->grid_dev, inst->city_cell, inst->cell_start,
                                                        inst->cell_city, inst->cell_xy, n, inst->p.k, inst->p.beta,
                                                        inst->cand, inst->candw, inst->etab, inst->errflag);

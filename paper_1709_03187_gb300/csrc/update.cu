@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(256) rebuild_kernel(const __grid_constant__ Re
     const int m_cap = BATCH ? R.m_cap : m;
     unsigned long long* qs = sm;                                      // m
     unsigned long long* hist = sm + m_cap + (size_t)w * k * 32;      // [k][32]
+
     if (use_ants)
         for (int a = threadIdx.x; a < m; a += blockDim.x) qs[a] = R.q[a];
     __syncthreads();
