@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--ants", type=int, default=0, help="override m (profiling of smaller cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the short runs of the other forms")
     ap.add_argument("--cpu-sample", type=int, default=32, help="ants in the oracle's timed sample")
     return ap.parse_args()
 
@@ -309,6 +310,9 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload.startswith("lbest"):
         cpu = cpu_baseline_oracle(xy, params, it, args.cpu_sample)
     col.close()
+    secondary = None
+    if rank == 0 and world == 1 and not args.no_secondary and args.workload == "lbest200k" and not args.ants:
+        secondary = secondary_results()
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "decisions/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_max / args.steps * 1e3, 4), "higher_is_better": True,
@@ -334,11 +338,37 @@ def run_ours(args):
         "gpu_launches": 4 * args.steps,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "secondary": secondary,
     }
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def secondary_results():
+    """Short runs of the other forms of the hot path, reported beside the headline (after its timed
+    region): the dense Section 2 form (dense100, 50 timed iterations), the batched form against
+    per-instance launches on the first 64 of batch512's instances (16 of them timed one by one),
+    and the learned proposal's time to the plain form's quality at n = 20,000 on one seed, with
+    its training time beside it (the training runs once and serves every later instance)."""
+    import types
+
+    a = types.SimpleNamespace(steps=50, warmup=5, cpu_sample=16)
+    out = {}
+    d = run_dense(a, emit=False)
+    out["dense100"] = {kk: d[kk] for kk in ("value", "unit", "iterations_per_s", "ms_construct", "ms_update")}
+    out["dense100"]["cpu_oracle_decisions_per_s"] = d["cpu_baseline"]["value"]
+    b = run_batch(a, count=64, per_instance_sample=16, emit=False)
+    out["batch64"] = {kk: b[kk] for kk in ("workload", "batched_instances_per_s", "per_instance_instances_per_s",
+                                           "speedup", "schedule", "schedule_kind", "per_instance_sample")}
+    lr = run_learned(a, seeds=(1,), emit=False)
+    tr = lr["training"]
+    out["learned20k"] = {"ratio_learned_over_plain": lr["value"], "seed": lr["per_seed"],
+                         "training_gpu_ms": round(tr["plain_ms"] + tr["train_ms"], 1), "training": tr,
+                         "note": "ratio of GPU wall-clock to the plain form's final C_gbest; the training (plain "
+                                 "runs for labels, then Adam) is reported beside it, not inside it"}
+    return out
 
 
 def run_e2e(args, xy, params, stream, make_colony, world=1):
@@ -501,7 +531,7 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ batched form
-def run_batch(args):
+def run_batch(args, count=512, per_instance_sample=None, emit=True):
     """512 instances, n log-uniform in [50, 5000] (uniform cities), k = 20, m = min(n, 256),
     f = 1, 100 iterations each.  Batched: one launch per step over all colonies, CUDA-graph
     replay, autotuned schedule.  Per-instance: the same calls instance by instance; a stratified
@@ -512,8 +542,8 @@ def run_batch(args):
     from paper_1709_03187_gb300 import Batch, Colony
 
     torch.cuda.set_device(0)
-    count, iters = 512, 100
-    ns = aco_synth.batch_sizes(count, 50, 5000, 4)
+    iters = 100
+    ns = aco_synth.batch_sizes(512, 50, 5000, 4)[:count]
     xys = [aco_synth.uniform(int(n), 4000 + i) for i, n in enumerate(ns)]
     kw = dict(k=20, alpha=1.0, beta=2.0, tau0=1.0, max_mod_frac=1.0, seed=4)
     stream = torch.cuda.Stream()
@@ -528,7 +558,8 @@ def run_batch(args):
     best = b.best()
     b.close()
     order = np.argsort(ns)
-    sample = order[np.linspace(0, count - 1, args.cpu_sample if args.cpu_sample <= 64 else 24).astype(int)]
+    ns_sample = per_instance_sample or (args.cpu_sample if args.cpu_sample <= 64 else 24)
+    sample = order[np.linspace(0, count - 1, min(ns_sample, count)).astype(int)]
     t_inst = 0.0
     for i in sample:
         n = int(ns[i])
@@ -551,7 +582,11 @@ def run_batch(args):
            "schedule_kind": "persistent launch" if sched >= 8 else "four launches per iteration, CUDA graph",
            "schedule_warps_per_block": warps, "schedule_min_blocks": minb, "schedule_ants_per_pull": pull,
            "tune_ms": [round(float(x), 3) for x in tune_ms], "mean_gbest": float(np.mean(best))}
-    print(json.dumps(out))
+    if count != 512:
+        out["workload"] = out["workload"].replace("512 instances", f"the first {count} of its 512 instances")
+    if emit:
+        print(json.dumps(out))
+    return out
 
 
 # ------------------------------------------------------------------ learned proposal
@@ -589,7 +624,7 @@ def _colony_curve(xy, n, m, k, f, seed, iters, scorer=None, target=None):
     return ms, best, s0.elapsed_time(s1)
 
 
-def run_learned(args):
+def run_learned(args, seeds=(1, 2, 3), emit=True):
     """Learned proposal against the plain heuristic at n = 20,000 (clustered, 100 clusters,
     sigma = 0.01, k = 20, m = 512, f = 0.1).  Training: plain runs on 2,000 clustered instances of
     n = 1,000 (5 clusters, sigma = 0.01: the evaluation's 200 cities per cluster), m = 32, k = 20,
@@ -619,7 +654,7 @@ def run_learned(args):
     loss = loss.cpu().numpy()
     n, m, k, f, iters = 20_000, 512, 20, 0.1, 100
     rows = []
-    for s in (1, 2, 3):
+    for s in seeds:
         xy = aco_synth.clustered(n, 100, 0.01, 20_000 + s)
         # each arm twice (the runs are deterministic): the faster timing of each
         runs_p = [_colony_curve(xy, n, m, k, f, s, iters) for _ in range(2)]
@@ -638,7 +673,7 @@ def run_learned(args):
            "unit": "ratio", "higher_is_better": False,
            "workload": "learned20k: n=20,000 clustered (100 clusters, sigma=0.01), k=20, m=512, f=0.1, beta=2, plain "
                        "100 iterations vs learned (score exp(z)^beta) until it reaches the plain final C_gbest; "
-                       "3 seeds",
+                       f"seeds {list(seeds)}",
            "per_seed": rows,
            "training": {"instances": 2000, "n": 1000, "plain_iterations": 40, "m": 32,
                         "plain_ms": round(e[0].elapsed_time(e[1]), 1), "train_ms": round(e[1].elapsed_time(e[2]), 1),
@@ -646,7 +681,9 @@ def run_learned(args):
                         "loss_first": float(loss[:20].mean()), "loss_last": float(loss[-20:].mean()),
                         "train_instances_mean_gbest": float(np.mean(train_best)), "generate_s": round(t_gen, 1)}}
     sc.close()
-    print(json.dumps(out))
+    if emit:
+        print(json.dumps(out))
+    return out
 
 
 # ------------------------------------------------------------------ modification schedule
@@ -664,7 +701,7 @@ def run_schedule(args):
     torch.cuda.set_device(0)
     n, m, k, iters = 20_000, 512, 20, 100
     rows = []
-    for s in (1, 2, 3):
+    for s in seeds:
         xy = aco_synth.clustered(n, 100, 0.01, 20_000 + s)
         res = {}
         for name, sched, pp in (("fixed", lambda t: 0.1, 1.0), ("growing", linear_f_schedule(0.01, 0.1, 50), 1.0),
@@ -738,7 +775,7 @@ def run_ls(args):
 
 
 # ------------------------------------------------------------------ dense form (Section 2)
-def run_dense(args):
+def run_dense(args, emit=True):
     """The Section 2 form on its workload (dense100: n = 100 uniform cities, m = 100 ants; Eq. 1
     over every unvisited city, then Eq. 2 and Eq. 3-5 on the n x n matrix): CUDA-event time of the
     construction and of the update per iteration, decisions and iterations per second, the
@@ -800,7 +837,9 @@ def run_dense(args):
                                 "launches per iteration: launch- and latency-bound"},
            "cpu_baseline": {"value": round(dec_or / t_or, 1), "unit": "decisions/s", "cores": 1,
                             "kind": "oracle", "sample": "3 full iterations of the oracle's own dense colony"}}
-    print(json.dumps(out))
+    if emit:
+        print(json.dumps(out))
+    return out
 
 
 # ------------------------------------------------------------------ Independent Roulette

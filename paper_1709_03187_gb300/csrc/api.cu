@@ -56,10 +56,28 @@ static void free_all(aco_instance* inst) {
         if (p) cudaFree(p);
 }
 
+// Byte limit on an instance's device buffers from the environment variable ACO_DEVICE_BYTES_LIMIT
+// (unset or unparsable: none).  Creation fails with ACO_ERR_OOM, as it does when cudaMalloc
+// fails, once the buffers would exceed it: a way to exercise the out-of-memory path on purpose.
+static size_t device_bytes_limit() {
+    const char* v = getenv("ACO_DEVICE_BYTES_LIMIT");
+    if (!v || !*v) return (size_t)-1;
+    char* end = nullptr;
+    const unsigned long long x = strtoull(v, &end, 10);
+    return (end && *end == 0) ? (size_t)x : (size_t)-1;
+}
+
+// One device buffer of `count` elements; alloc = false only counts its bytes (the dry run that
+// checks the byte limit before anything touches the device).
 template <typename T>
-static bool dalloc(T** p, size_t count, size_t* total) {
+static bool dalloc(T** p, size_t count, size_t* total, bool alloc = true) {
     if (count == 0) count = 1;
     *total += count * sizeof(T);
+    if (!alloc) {
+        *p = nullptr;
+        return true;
+    }
+    if (*total > device_bytes_limit()) return false;
     return cudaMalloc((void**)p, count * sizeof(T)) == cudaSuccess;
 }
 
@@ -90,8 +108,76 @@ static bool params_ok(const aco_params* p, char* why, size_t wn) {
     return true;
 }
 
+// Every device buffer an instance allocates at creation (before the grid is known), or, with
+// alloc = false, only their bytes in *total.
+static bool plan_buffers(aco_instance* inst, const aco_params* p, size_t* total, bool alloc) {
+    const long long n = p->n, m = p->m, k = p->k;
+    bool ok = true;
+    ok &= dalloc(&inst->xy, 2 * n, total, alloc);
+    ok &= dalloc(&inst->grid_dev, 1, total, alloc);
+    ok &= dalloc(&inst->city_cell, n, total, alloc);
+    inst->ncells_cap = (int32_t)(n / 2 + 16);
+    ok &= dalloc(&inst->cell_start, inst->ncells_cap + 1, total, alloc);
+    ok &= dalloc(&inst->cell_fill, inst->ncells_cap, total, alloc);
+    ok &= dalloc(&inst->cell_city, n, total, alloc);
+    ok &= dalloc(&inst->cell_xy, 2 * n, total, alloc);
+    ok &= dalloc(&inst->counters, CNT_N, total, alloc);
+    ok &= dalloc(&inst->errflag, 1, total, alloc);
+    ok &= dalloc(&inst->clen, m, total, alloc);
+    ok &= dalloc(&inst->cfix, 2 * m, total, alloc);
+    ok &= dalloc(&inst->gbest, 1, total, alloc);
+    ok &= dalloc(&inst->gbest_ant, 1, total, alloc);
+    if (p->mode == ACO_MODE_LBEST_PARTIAL) {
+        ok &= dalloc(&inst->candw, n * k, total, alloc);
+        ok &= dalloc(&inst->cand, n * k, total, alloc);
+        ok &= dalloc(&inst->etab, n * k, total, alloc);
+        ok &= dalloc(&inst->W64, n * k, total, alloc);
+        ok &= dalloc(&inst->rowflag, n, total, alloc);
+        ok &= dalloc(&inst->lbest, m * n, total, alloc);
+        ok &= dalloc(&inst->nb, 2 * n * m, total, alloc);
+        ok &= dalloc(&inst->nbrank, 2 * n * m, total, alloc);
+        ok &= dalloc(&inst->q, m, total, alloc);
+        ok &= dalloc(&inst->seg, m * n, total, alloc);
+        ok &= dalloc(&inst->antit, m, total, alloc);
+        if (p->fallback == 1) ok &= dalloc(&inst->accq, m * n, total, alloc);
+        ok &= dalloc(&inst->bel, m * 2 * m, total, alloc);
+        ok &= dalloc(&inst->btx, m * 2 * m, total, alloc);
+        ok &= dalloc(&inst->btq, m * 2 * m, total, alloc);
+        ok &= dalloc(&inst->ghk, m * 2 * m, total, alloc);
+        ok &= dalloc(&inst->ghq, m * 2 * m, total, alloc);
+        long long fm = (long long)floor(p->max_mod_frac * (double)n);
+        long long pmin = n - fm;
+        if (pmin < 1) pmin = 1;
+        if (pmin > n - 1) pmin = n - 1;
+        inst->ucap = (int32_t)(n - pmin);
+        inst->f_cap = p->max_mod_frac;
+        inst->ls_window = 500;
+        ok &= dalloc(&inst->ulist, m * inst->ucap, total, alloc);
+        ok &= dalloc(&inst->uxy, m * inst->ucap, total, alloc);
+        ok &= dalloc(&inst->xy32, n, total, alloc);
+        ok &= dalloc(&inst->deg, n, total, alloc);
+        ok &= dalloc(&inst->rec_off, m, total, alloc);
+        ok &= dalloc(&inst->nrec, 1, total, alloc);
+        // extended neighbour lists speed up the exhausted-list rule
+        inst->kx = (int32_t)(n - 1 < ACO_KX ? n - 1 : ACO_KX);
+        if (inst->kx > k) ok &= dalloc(&inst->ext, n * inst->kx, total, alloc);
+        else inst->kx = 0;
+    } else {
+        ok &= dalloc(&inst->tau, n * n, total, alloc);
+        ok &= dalloc(&inst->etab_d, n * n, total, alloc);
+        ok &= dalloc(&inst->W64d, n * n, total, alloc);
+        ok &= dalloc(&inst->W32d, n * n, total, alloc);
+        ok &= dalloc(&inst->rowflag, n, total, alloc);
+        ok &= dalloc(&inst->tours, m * n, total, alloc);
+        ok &= dalloc(&inst->succ_d, m * n, total, alloc);
+        ok &= dalloc(&inst->pred_d, m * n, total, alloc);
+    }
+    return ok;
+}
+
 extern "C" aco_status aco_create_instance(const double* xy_dev, const aco_params* p, void* stream,
                                           aco_instance** out) {
+    ACO_RANGE("aco_create_instance");
     g_create_err[0] = 0;
     if (!out || !p || !xy_dev) {
         snprintf(g_create_err, sizeof(g_create_err), "null argument");
@@ -99,6 +185,17 @@ extern "C" aco_status aco_create_instance(const double* xy_dev, const aco_params
     }
     *out = nullptr;
     if (!params_ok(p, g_create_err, sizeof(g_create_err))) return ACO_ERR_INVALID_ARG;
+    {
+        aco_instance probe;
+        memset(&probe, 0, sizeof(probe));
+        size_t need = 0;
+        plan_buffers(&probe, p, &need, false);
+        if (need > device_bytes_limit()) {
+            snprintf(g_create_err, sizeof(g_create_err), "the buffers need %zu bytes, above ACO_DEVICE_BYTES_LIMIT",
+                     need);
+            return ACO_ERR_OOM;
+        }
+    }
     cudaPointerAttributes attr;
     if (cudaPointerGetAttributes(&attr, xy_dev) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
         cudaGetLastError();
@@ -114,68 +211,9 @@ extern "C" aco_status aco_create_instance(const double* xy_dev, const aco_params
     cudaGetDevice(&inst->device);
     cudaDeviceGetAttribute(&inst->num_sms, cudaDevAttrMultiProcessorCount, inst->device);
 
-    const long long n = p->n, m = p->m, k = p->k;
+    const long long n = p->n, m = p->m;
     size_t total = 0;
-    bool ok = true;
-    ok &= dalloc(&inst->xy, 2 * n, &total);
-    ok &= dalloc(&inst->grid_dev, 1, &total);
-    ok &= dalloc(&inst->city_cell, n, &total);
-    inst->ncells_cap = (int32_t)(n / 2 + 16);
-    ok &= dalloc(&inst->cell_start, inst->ncells_cap + 1, &total);
-    ok &= dalloc(&inst->cell_fill, inst->ncells_cap, &total);
-    ok &= dalloc(&inst->cell_city, n, &total);
-    ok &= dalloc(&inst->cell_xy, 2 * n, &total);
-    ok &= dalloc(&inst->counters, CNT_N, &total);
-    ok &= dalloc(&inst->errflag, 1, &total);
-    ok &= dalloc(&inst->clen, m, &total);
-    ok &= dalloc(&inst->cfix, 2 * m, &total);
-    ok &= dalloc(&inst->gbest, 1, &total);
-    ok &= dalloc(&inst->gbest_ant, 1, &total);
-    if (p->mode == ACO_MODE_LBEST_PARTIAL) {
-        ok &= dalloc(&inst->candw, n * k, &total);
-        ok &= dalloc(&inst->cand, n * k, &total);
-        ok &= dalloc(&inst->etab, n * k, &total);
-        ok &= dalloc(&inst->W64, n * k, &total);
-        ok &= dalloc(&inst->rowflag, n, &total);
-        ok &= dalloc(&inst->lbest, m * n, &total);
-        ok &= dalloc(&inst->nb, 2 * n * m, &total);
-        ok &= dalloc(&inst->nbrank, 2 * n * m, &total);
-        ok &= dalloc(&inst->q, m, &total);
-        ok &= dalloc(&inst->seg, m * n, &total);
-        ok &= dalloc(&inst->antit, m, &total);
-        if (p->fallback == 1) ok &= dalloc(&inst->accq, m * n, &total);
-        ok &= dalloc(&inst->bel, m * 2 * m, &total);
-        ok &= dalloc(&inst->btx, m * 2 * m, &total);
-        ok &= dalloc(&inst->btq, m * 2 * m, &total);
-        ok &= dalloc(&inst->ghk, m * 2 * m, &total);
-        ok &= dalloc(&inst->ghq, m * 2 * m, &total);
-        long long fm = (long long)floor(p->max_mod_frac * (double)n);
-        long long pmin = n - fm;
-        if (pmin < 1) pmin = 1;
-        if (pmin > n - 1) pmin = n - 1;
-        inst->ucap = (int32_t)(n - pmin);
-        inst->f_cap = p->max_mod_frac;
-        inst->ls_window = 500;
-        ok &= dalloc(&inst->ulist, m * inst->ucap, &total);
-        ok &= dalloc(&inst->uxy, m * inst->ucap, &total);
-        ok &= dalloc(&inst->xy32, n, &total);
-        ok &= dalloc(&inst->deg, n, &total);
-        ok &= dalloc(&inst->rec_off, m, &total);
-        ok &= dalloc(&inst->nrec, 1, &total);
-        // extended neighbour lists speed up the exhausted-list rule
-        inst->kx = (int32_t)(n - 1 < ACO_KX ? n - 1 : ACO_KX);
-        if (inst->kx > k) ok &= dalloc(&inst->ext, n * inst->kx, &total);
-        else inst->kx = 0;
-    } else {
-        ok &= dalloc(&inst->tau, n * n, &total);
-        ok &= dalloc(&inst->etab_d, n * n, &total);
-        ok &= dalloc(&inst->W64d, n * n, &total);
-        ok &= dalloc(&inst->W32d, n * n, &total);
-        ok &= dalloc(&inst->rowflag, n, &total);
-        ok &= dalloc(&inst->tours, m * n, &total);
-        ok &= dalloc(&inst->succ_d, m * n, &total);
-        ok &= dalloc(&inst->pred_d, m * n, &total);
-    }
+    bool ok = plan_buffers(inst, p, &total, true);
     if (!ok) {
         cudaGetLastError();
         snprintf(g_create_err, sizeof(g_create_err), "device allocation of %.3f GB failed", total / 1e9);
@@ -290,6 +328,7 @@ aco_status sync_and_check(aco_instance* inst, const char* what) {
 }
 
 extern "C" aco_status aco_build_candidates(aco_instance* inst, int32_t* cand_out_dev) {
+    ACO_RANGE("aco_build_candidates");
     if (!inst) return ACO_ERR_INVALID_ARG;
     aco_status st = launch_build_grid_and_knn(inst);
     if (st != ACO_OK) return st;
@@ -316,6 +355,7 @@ extern "C" aco_status aco_build_candidates(aco_instance* inst, int32_t* cand_out
 
 extern "C" aco_status aco_construct_tours(aco_instance* inst, int32_t iteration, int32_t* tours_out_dev,
                                           double* len_out_dev) {
+    ACO_RANGE("aco_construct_tours");
     if (!inst) return ACO_ERR_INVALID_ARG;
     if (!inst->cand_built) return set_err(inst, ACO_ERR_STATE, "construct_tours before build_candidates");
     if (iteration < 0) return set_err(inst, ACO_ERR_INVALID_ARG, "iteration must be >= 0");
@@ -336,6 +376,7 @@ extern "C" aco_status aco_construct_tours(aco_instance* inst, int32_t iteration,
 }
 
 extern "C" aco_status aco_update_pheromone(aco_instance* inst) {
+    ACO_RANGE("aco_update_pheromone");
     if (!inst) return ACO_ERR_INVALID_ARG;
     if (!inst->constructed) return set_err(inst, ACO_ERR_STATE, "update_pheromone without a construction");
     aco_status st = inst->p.mode == ACO_MODE_LBEST_PARTIAL ? launch_update_lbest(inst) : launch_update_dense(inst);
@@ -347,6 +388,7 @@ extern "C" aco_status aco_update_pheromone(aco_instance* inst) {
 }
 
 extern "C" aco_status aco_tour_lengths(aco_instance* inst, const int32_t* tours_dev, int32_t count, double* out_dev) {
+    ACO_RANGE("aco_tour_lengths");
     if (!inst || count < 0 || (count > 0 && (!tours_dev || !out_dev))) return ACO_ERR_INVALID_ARG;
     if (count == 0) return ACO_OK;
     return launch_tour_lengths(inst, tours_dev, count, out_dev);
@@ -354,6 +396,7 @@ extern "C" aco_status aco_tour_lengths(aco_instance* inst, const int32_t* tours_
 
 extern "C" aco_status aco_get_state(aco_instance* inst, int32_t* lbest_out_dev, double* clen_out_dev,
                                     double* tau_out_dev) {
+    ACO_RANGE("aco_get_state");
     if (!inst) return ACO_ERR_INVALID_ARG;
     const size_t n = inst->p.n, m = inst->p.m;
     cudaStream_t s = inst->stream;
@@ -371,6 +414,7 @@ extern "C" aco_status aco_get_state(aco_instance* inst, int32_t* lbest_out_dev, 
 aco_status launch_reweight(aco_instance* inst);
 
 extern "C" aco_status aco_set_async_share(aco_instance* inst, int32_t on) {
+    ACO_RANGE("aco_set_async_share");
     if (!inst) return ACO_ERR_INVALID_ARG;
     if (inst->p.mode != ACO_MODE_LBEST_PARTIAL) return set_err(inst, ACO_ERR_STATE, "set_async_share: LBEST mode only");
     if (inst->in_batch) return set_err(inst, ACO_ERR_STATE, "set_async_share: not for an instance of a batch");
@@ -398,6 +442,7 @@ extern "C" aco_status aco_set_async_share(aco_instance* inst, int32_t on) {
 }
 
 extern "C" aco_status aco_set_state(aco_instance* inst, const int32_t* lbest_dev, const double* tau_dev) {
+    ACO_RANGE("aco_set_state");
     if (!inst) return ACO_ERR_INVALID_ARG;
     if (!inst->cand_built) return set_err(inst, ACO_ERR_STATE, "set_state before build_candidates");
     if (inst->p.mode == ACO_MODE_LBEST_PARTIAL) {
@@ -419,6 +464,7 @@ extern "C" aco_status aco_set_state(aco_instance* inst, const int32_t* lbest_dev
 }
 
 extern "C" aco_status aco_get_stats(aco_instance* inst, aco_stats* out_host) {
+    ACO_RANGE("aco_get_stats");
     if (!inst || !out_host) return ACO_ERR_INVALID_ARG;
     aco_status st = sync_and_check(inst, "get_stats");
     if (st != ACO_OK) return st;

@@ -97,6 +97,7 @@ static void free_batch(aco_batch* b) {
 
 extern "C" aco_status aco_batch_create(const double* xy_dev, const int32_t* n_host, int32_t count, const aco_params* p,
                                        void* stream, aco_batch** out) {
+    ACO_RANGE("aco_batch_create");
     if (!xy_dev || !n_host || !p || !out || count < 1) return ACO_ERR_INVALID_ARG;
     *out = nullptr;
     if (p->mode != ACO_MODE_LBEST_PARTIAL) return ACO_ERR_INVALID_ARG;
@@ -182,6 +183,7 @@ extern "C" aco_status aco_batch_create(const double* xy_dev, const int32_t* n_ho
 }
 
 extern "C" aco_status aco_batch_build_candidates(aco_batch* b) {
+    ACO_RANGE("aco_batch_build_candidates");
     if (!b) return ACO_ERR_INVALID_ARG;
     for (aco_instance* i : b->inst) {
         aco_status st = aco_build_candidates(i, nullptr);
@@ -296,6 +298,7 @@ static aco_status check_status(aco_batch* b) {
 }
 
 extern "C" aco_status aco_batch_run(aco_batch* b, int32_t first_iteration, int32_t iterations, int32_t tune) {
+    ACO_RANGE("aco_batch_run");
     if (!b || iterations < 0 || first_iteration < 0) return ACO_ERR_INVALID_ARG;
     if (!b->built) return berr(b, ACO_ERR_STATE, "run before build_candidates");
     if (b->failed) return berr(b, ACO_ERR_STATE, "the batch failed earlier (barrier wait ran out)");
@@ -368,6 +371,7 @@ extern "C" aco_status aco_batch_run(aco_batch* b, int32_t first_iteration, int32
 }
 
 extern "C" aco_status aco_batch_get_state(aco_batch* b, int32_t* lbest_out_dev, double* clen_out_dev) {
+    ACO_RANGE("aco_batch_get_state");
     if (!b) return ACO_ERR_INVALID_ARG;
     aco_status st = check_status(b);
     if (st != ACO_OK) return st;
@@ -380,6 +384,7 @@ extern "C" aco_status aco_batch_get_state(aco_batch* b, int32_t* lbest_out_dev, 
 }
 
 extern "C" aco_status aco_batch_get_best(aco_batch* b, double* best_len_host) {
+    ACO_RANGE("aco_batch_get_best");
     if (!b || !best_len_host) return ACO_ERR_INVALID_ARG;
     aco_status st = check_status(b);
     if (st != ACO_OK) return st;

@@ -12,6 +12,7 @@
 //    purpose); u = 53 bits / 2^53; integers in [0, r) by the multiply-shift (x * r) >> 32.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/aco.h"
@@ -393,3 +394,10 @@ aco_status launch_set_lbest(aco_instance* inst, const int32_t* lbest);
 aco_status launch_step_probs(aco_instance* inst, int32_t city, const uint32_t* bits, float* probs, int32_t* exhausted);
 
 static inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// An NVTX range over one ABI call: a named span on a profiler's timeline, nearly free without one.
+struct AcoRange {
+    explicit AcoRange(const char* name) { nvtxRangePushA(name); }
+    ~AcoRange() { nvtxRangePop(); }
+};
+#define ACO_RANGE(name) AcoRange aco_range_(name)

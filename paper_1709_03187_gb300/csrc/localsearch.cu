@@ -257,6 +257,7 @@ aco_status launch_local_search(aco_instance* inst, int32_t iteration) {
 }
 
 extern "C" aco_status aco_set_local_search(aco_instance* inst, double p, int32_t window) {
+    ACO_RANGE("aco_set_local_search");
     if (!inst) return ACO_ERR_INVALID_ARG;
     if (inst->p.mode != ACO_MODE_LBEST_PARTIAL) return set_err(inst, ACO_ERR_STATE, "set_local_search: LBEST mode only");
     if (inst->constructed) return set_err(inst, ACO_ERR_STATE, "set_local_search: tours constructed, update pending");

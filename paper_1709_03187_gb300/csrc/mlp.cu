@@ -514,6 +514,7 @@ static aco_status mlp_launch_ok(aco_mlp* h, const char* what) {
 extern "C" const char* aco_mlp_last_error(const aco_mlp* h) { return h ? h->err : ""; }
 
 extern "C" aco_status aco_mlp_create(const float* w_host, int64_t max_rows, void* stream, aco_mlp** out) {
+    ACO_RANGE("aco_mlp_create");
     if (!out || !w_host || max_rows < 16 || max_rows > (1LL << 30)) return ACO_ERR_INVALID_ARG;
     *out = nullptr;
     for (int e = 0; e < MLP_NW; ++e)
@@ -589,6 +590,7 @@ extern "C" aco_status aco_mlp_get_weights(aco_mlp* h, float* w_host) {
 
 extern "C" aco_status aco_mlp_forward(aco_mlp* h, const uint16_t* X_dev, int64_t rows, float* z_dev,
                                       float* score_dev, float beta) {
+    ACO_RANGE("aco_mlp_forward");
     if (!h || !X_dev || rows < 0 || (!z_dev && !score_dev) || !isfinite(beta)) return ACO_ERR_INVALID_ARG;
     if (rows == 0) return ACO_OK;
     mlp_forward_kernel<<<blocks_for(rows, 64), 128, 0, h->stream>>>(weights_of(h), (const bf16*)X_dev, rows, z_dev,
@@ -626,6 +628,7 @@ static aco_status mlp_backward(aco_mlp* h, const bf16* X, const uint32_t* target
 
 extern "C" aco_status aco_mlp_backward(aco_mlp* h, const uint16_t* X_dev, const uint32_t* target_dev, int32_t cities,
                                        int32_t k, float scale, float* grad_dev, float* loss_dev) {
+    ACO_RANGE("aco_mlp_backward");
     if (!h || !X_dev || !target_dev || cities < 1 || k < 1 || k > 32 || !isfinite(scale)) return ACO_ERR_INVALID_ARG;
     if ((long long)cities * k > h->max_rows) return ACO_ERR_INVALID_ARG;
     aco_status st = mlp_backward(h, (const bf16*)X_dev, target_dev, cities, k, scale, loss_dev);
@@ -644,12 +647,14 @@ static aco_status mlp_adam(aco_mlp* h, const float* grad, float lr) {
 }
 
 extern "C" aco_status aco_mlp_adam(aco_mlp* h, const float* grad_dev, float lr) {
+    ACO_RANGE("aco_mlp_adam");
     if (!h || !(lr >= 0.f) || !isfinite(lr)) return ACO_ERR_INVALID_ARG;
     return mlp_adam(h, grad_dev ? grad_dev : h->grad, lr);
 }
 
 extern "C" aco_status aco_mlp_train(aco_mlp* h, const uint16_t* X_dev, const uint32_t* target_dev, int32_t cities,
                                     int32_t k, int32_t batch_cities, int32_t steps, float lr, float* loss_dev) {
+    ACO_RANGE("aco_mlp_train");
     if (!h || !X_dev || !target_dev || cities < 1 || k < 1 || k > 32 || batch_cities < 1 || steps < 0 ||
         !(lr >= 0.f) || !isfinite(lr))
         return ACO_ERR_INVALID_ARG;
@@ -671,6 +676,7 @@ extern "C" aco_status aco_mlp_train(aco_mlp* h, const uint16_t* X_dev, const uin
 
 // ---------------------------------------------------------------- instance side
 extern "C" aco_status aco_edge_features(aco_instance* inst, int32_t degree_ants, uint16_t* X_dev) {
+    ACO_RANGE("aco_edge_features");
     if (!inst || !X_dev) return ACO_ERR_INVALID_ARG;
     if (inst->p.mode != ACO_MODE_LBEST_PARTIAL || !inst->cand_built || !inst->initialized)
         return set_err(inst, ACO_ERR_STATE, "edge_features: needs candidate lists and l_best tours");
@@ -683,6 +689,7 @@ extern "C" aco_status aco_edge_features(aco_instance* inst, int32_t degree_ants,
 }
 
 extern "C" aco_status aco_tour_labels(aco_instance* inst, uint32_t* target_dev) {
+    ACO_RANGE("aco_tour_labels");
     if (!inst || !target_dev) return ACO_ERR_INVALID_ARG;
     if (inst->p.mode != ACO_MODE_LBEST_PARTIAL || !inst->initialized)
         return set_err(inst, ACO_ERR_STATE, "tour_labels: needs l_best tours");
@@ -693,6 +700,7 @@ extern "C" aco_status aco_tour_labels(aco_instance* inst, uint32_t* target_dev) 
 }
 
 extern "C" aco_status aco_set_edge_scores(aco_instance* inst, const float* score_dev) {
+    ACO_RANGE("aco_set_edge_scores");
     if (!inst) return ACO_ERR_INVALID_ARG;
     if (inst->p.mode != ACO_MODE_LBEST_PARTIAL || !inst->cand_built)
         return set_err(inst, ACO_ERR_STATE, "set_edge_scores: needs candidate lists");

@@ -99,6 +99,7 @@ static aco_status scratch_for_current_device(void** ptr, int* num_sms, int* devi
 
 extern "C" aco_status aco_build_candidates_noalloc(const double* xy_dev, int32_t n, int32_t k, int32_t* cand_out_dev,
                                                    void* stream) {
+    ACO_RANGE("aco_build_candidates_noalloc");
     if (!xy_dev || !cand_out_dev) return ACO_ERR_INVALID_ARG;
     if (n < 2 || n > ACO_NOALLOC_MAX_N) return ACO_ERR_INVALID_ARG;  // beyond the fixed scratch
     if (k < 1 || k > ACO_MAX_K || k > n - 1) return ACO_ERR_INVALID_ARG;

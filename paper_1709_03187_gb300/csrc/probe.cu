@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(512) probe_copy_kernel(const int4* __restrict_
 
 extern "C" aco_status aco_probe_bandwidth(void* buf_dev, int64_t bytes, int32_t mode, int32_t reps, void* stream,
                                           float* ms_out) {
+    ACO_RANGE("aco_probe_bandwidth");
     if (!buf_dev || !ms_out || reps < 1 || (mode != 0 && mode != 1)) return ACO_ERR_INVALID_ARG;
     if (bytes < 4096 || (bytes & 31) || (reinterpret_cast<uintptr_t>(buf_dev) & 15)) return ACO_ERR_INVALID_ARG;
     int dev = 0, sms = 1;

@@ -136,6 +136,7 @@ extern "C" aco_status aco_set_ant_range(aco_instance* inst, int32_t ant_begin, i
 }
 
 extern "C" aco_status aco_export_commits(aco_instance* inst, int32_t* buf_dev, int64_t cap_words, int64_t* words_out) {
+    ACO_RANGE("aco_export_commits");
     if (!inst || !buf_dev || !words_out || cap_words < 4) return ACO_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(buf_dev) & 7) return set_err(inst, ACO_ERR_INVALID_ARG, "export_commits: buffer not 8-byte aligned");
     if (inst->p.mode != ACO_MODE_LBEST_PARTIAL) return set_err(inst, ACO_ERR_STATE, "export_commits: LBEST mode only");
@@ -161,6 +162,7 @@ extern "C" aco_status aco_export_commits(aco_instance* inst, int32_t* buf_dev, i
 
 extern "C" aco_status aco_import_commits(aco_instance* inst, const int32_t* bufs_dev, int32_t count,
                                          int64_t stride_words) {
+    ACO_RANGE("aco_import_commits");
     if (!inst || !bufs_dev || count < 1 || stride_words < 4) return ACO_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(bufs_dev) & 7 || (stride_words & 1))
         return set_err(inst, ACO_ERR_INVALID_ARG, "import_commits: buffers must be 8-byte aligned, stride even");

@@ -63,3 +63,28 @@ def test_status_strings_without_gpu():
     lib.aco_status_string.restype = ctypes.c_char_p
     assert lib.aco_status_string(0) == b"ok"
     assert lib.aco_status_string(1) == b"invalid argument"
+
+
+def test_device_byte_limit_gives_oom_before_any_device_call():
+    """ACO_DEVICE_BYTES_LIMIT below an instance's buffers: aco_create_instance returns ACO_ERR_OOM
+    from its dry run, before it touches the device (so this runs without a GPU)."""
+    import sys
+
+    code = r'''
+import ctypes, sys
+sys.path.insert(0, sys.argv[1])
+from paper_1709_03187_gb300 import build
+from paper_1709_03187_gb300._ffi import Params
+lib = ctypes.CDLL(build.build())
+lib.aco_last_error.restype = ctypes.c_char_p
+p = Params(1, 200000, 1024, 16, 1.0, 2.0, 0.1, 1.0, 0.01, 1.0, 3, 0, 0)
+h = ctypes.c_void_p()
+dummy = ctypes.c_void_p(0x1000)
+st = lib.aco_create_instance(dummy, ctypes.byref(p), None, ctypes.byref(h))
+print(st, lib.aco_last_error(None).decode())
+'''
+    env = dict(os.environ, ACO_DEVICE_BYTES_LIMIT="1000000")
+    r = subprocess.run([sys.executable, "-c", code, ROOT], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    status, msg = r.stdout.split(" ", 1)
+    assert int(status) == 2 and "ACO_DEVICE_BYTES_LIMIT" in msg  # ACO_ERR_OOM
