@@ -33,10 +33,10 @@ import aco_synth  # noqa: E402
 
 METRIC = "city decisions/s and ACO iterations/s at n=200K on 1 GB300; % of mem roofline"
 # DRAM bytes (read + write) per decision of construct_lbest_kernel from one ncu capture of the
-# 200,000-city workload at m = 256 (58.0 MB for 251,025 decisions), valid for the code it was
+# 200,000-city workload at m = 256 (62.95 MB for 266,770 decisions), valid for the code it was
 # taken on: code_sha1 hashes construct.cu without its comments and blank lines, and the bench
 # reports null traffic once the code changes.
-CONSTRUCT_TRAFFIC = {"code_sha1_12": "d08a52df3a73", "bytes_per_decision": 57963776.0 / 251025.5}
+CONSTRUCT_TRAFFIC = {"code_sha1_12": "33d915d38744", "bytes_per_decision": 62951680.0 / 266769.67}
 L2_FLUSH_BYTES = 512 << 20  # > 126 MB L2
 
 
