@@ -28,16 +28,20 @@ def exchange_records(local: torch.Tensor, words: int, group=None, world: int | N
     import torch.distributed as dist
 
     world = world or dist.get_world_size(group)
-    size = torch.tensor([words], dtype=torch.int64, device=local.device)
+    # a backend without device collectives (gloo) exchanges through host memory
+    dev = local.device
+    via_host = dev.type == "cuda" and dist.get_backend(group) == "gloo"
+    cdev = torch.device("cpu") if via_host else dev
+    size = torch.tensor([words], dtype=torch.int64, device=cdev)
     sizes = [torch.zeros_like(size) for _ in range(world)]
     dist.all_gather(sizes, size, group=group)
     stride = max(int(s.item()) for s in sizes)
     stride += stride & 1
-    send = torch.zeros(stride, dtype=torch.int32, device=local.device)
-    send[:words] = local[:words]
-    recv = [torch.empty(stride, dtype=torch.int32, device=local.device) for _ in range(world)]
+    send = torch.zeros(stride, dtype=torch.int32, device=cdev)
+    send[:words] = local[:words].to(cdev)
+    recv = [torch.empty(stride, dtype=torch.int32, device=cdev) for _ in range(world)]
     dist.all_gather(recv, send, group=group)
-    return torch.stack(recv)
+    return torch.stack(recv).to(dev)
 
 
 class ShardedColony:
