@@ -324,10 +324,12 @@ typedef struct aco_mlp aco_mlp; /* opaque: weights, optimiser state and training
  * device memory per row).  stream: cudaStream_t for all of this network's work (NULL = legacy
  * default stream).  Allocates everything.  Synchronises. */
 aco_status aco_mlp_create(const float* w_host, int64_t max_rows, void* stream, aco_mlp** out);
-/* The FP32 weights (ACO_MLP_WEIGHTS floats).  Synchronises. */
+/* The FP32 weights (ACO_MLP_WEIGHTS floats).  Synchronises.  ACO_ERR_TIMEOUT if a forward pass on
+ * this handle gave up waiting for a tensor-core MMA (2 s; its unfinished rows were written NaN). */
 aco_status aco_mlp_get_weights(aco_mlp* h, float* w_host);
 /* z_dev and/or score_dev = exp(beta z) (rows floats each; either may be NULL, not both) for rows of
- * BF16 features X_dev (rows * 16 BF16 bit patterns).  No row limit.  Enqueued. */
+ * BF16 features X_dev (rows * 16 BF16 bit patterns, 4-byte aligned).  No row limit.  On the tcgen05
+ * tensor cores: 128-row tiles, accumulators in tensor memory.  Enqueued. */
 aco_status aco_mlp_forward(aco_mlp* h, const uint16_t* X_dev, int64_t rows, float* z_dev, float* score_dev,
                            float beta);
 /* Gradient of scale * (summed loss over `cities` cities of k rows each, k <= 32) with respect to

@@ -7,8 +7,10 @@
 //   h2 = relu(W2 h1)     W2: 64 x 64
 //   h2[63] = 1           (constant unit: w3[63] is the output bias)
 //   z  = w3 . h2         score = exp(z)
-// BF16 weights and activations, FP32 accumulation on the tensor cores (mma m16n8k16), the
-// hidden activations rounded to BF16 between layers.
+// BF16 weights and activations, FP32 accumulation on the tensor cores, the hidden activations
+// rounded to BF16 between layers.  The forward pass runs on the fifth-generation tensor cores
+// (tcgen05 MMAs with accumulators in tensor memory, umma.cuh); the backward products use the warp
+// MMA (mma.sync m16n8k16).
 //
 // Training objective: for every city, the softmax of z over its k candidate edges against the
 // best tour's edges among them (cross-entropy; each of the city's best-tour neighbours that is a
@@ -26,6 +28,7 @@
 #include <new>
 
 #include "common.cuh"
+#include "umma.cuh"
 
 #define FULL 0xffffffffu
 #define MLP_IN 16
@@ -76,107 +79,165 @@ __device__ void load_weights(MlpSmem& sh, const MlpWeights& w) {
 
 __device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
-// Forward of 16 rows starting at r0 (rows >= R are zero inputs).  Returns z for rows g and g+8
-// (g = lane >> 2) in lanes with t == 0; optionally stores h1, h2 (BF16) for the backward pass.
-__device__ void forward16(const MlpSmem& sh, const bf16* __restrict__ X, long long r0, long long R, int lane, bf16* h1out,
-                          bf16* h2out, float& z_lo, float& z_hi) {
-    const int g = lane >> 2, t = lane & 3;
-    const long long ra = r0 + g, rb = r0 + g + 8;
-    uint32_t a[4];
-    a[0] = ra < R ? ld32(X + (size_t)ra * MLP_IN + 2 * t) : 0u;
-    a[1] = rb < R ? ld32(X + (size_t)rb * MLP_IN + 2 * t) : 0u;
-    a[2] = ra < R ? ld32(X + (size_t)ra * MLP_IN + 8 + 2 * t) : 0u;
-    a[3] = rb < R ? ld32(X + (size_t)rb * MLP_IN + 8 + 2 * t) : 0u;
-    // layer 1: 8 output tiles of 8 units
-    float h1[8][4];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        h1[j][0] = h1[j][1] = h1[j][2] = h1[j][3] = 0.f;
-        const uint32_t b[2] = {ld32(&sh.W1[(8 * j + g) * MLP_IN + 2 * t]), ld32(&sh.W1[(8 * j + g) * MLP_IN + 8 + 2 * t])};
-        mma_bf16(h1[j], a, b);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int col = 8 * j + 2 * t + (e & 1);
-            float v = fmaxf(h1[j][e], 0.f);
-            if (col == MLP_H - 1) v = 1.f;
-            h1[j][e] = bf16_round(v);
-        }
-    }
-    if (h1out) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            if (ra < R) *reinterpret_cast<uint32_t*>(h1out + (size_t)ra * MLP_H + 8 * j + 2 * t) = pack_bf16(h1[j][0], h1[j][1]);
-            if (rb < R) *reinterpret_cast<uint32_t*>(h1out + (size_t)rb * MLP_H + 8 * j + 2 * t) = pack_bf16(h1[j][2], h1[j][3]);
-        }
-    }
-    // layer 2: A fragments from the layer-1 accumulators (k-step s = tiles 2s, 2s+1)
-    float h2[8][4];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) h2[j][0] = h2[j][1] = h2[j][2] = h2[j][3] = 0.f;
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        const uint32_t as[4] = {pack_bf16(h1[2 * s][0], h1[2 * s][1]), pack_bf16(h1[2 * s][2], h1[2 * s][3]),
-                                pack_bf16(h1[2 * s + 1][0], h1[2 * s + 1][1]),
-                                pack_bf16(h1[2 * s + 1][2], h1[2 * s + 1][3])};
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const uint32_t b[2] = {ld32(&sh.W2[(8 * j + g) * MLP_H + 16 * s + 2 * t]),
-                                   ld32(&sh.W2[(8 * j + g) * MLP_H + 16 * s + 8 + 2 * t])};
-            mma_bf16(h2[j], as, b);
-        }
-    }
-    float zl = 0.f, zh = 0.f;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int col = 8 * j + 2 * t + (e & 1);
-            float v = fmaxf(h2[j][e], 0.f);
-            if (col == MLP_H - 1) v = 1.f;
-            v = bf16_round(v);
-            h2[j][e] = v;
-            if (e < 2) zl = __fmaf_rn(v, sh.w3[col], zl);
-            else zh = __fmaf_rn(v, sh.w3[col], zh);
-        }
-    }
-    if (h2out) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            if (ra < R) *reinterpret_cast<uint32_t*>(h2out + (size_t)ra * MLP_H + 8 * j + 2 * t) = pack_bf16(h2[j][0], h2[j][1]);
-            if (rb < R) *reinterpret_cast<uint32_t*>(h2out + (size_t)rb * MLP_H + 8 * j + 2 * t) = pack_bf16(h2[j][2], h2[j][3]);
-        }
-    }
-    // layer 3: reduce the four partial dot products of each row
-    zl += __shfl_xor_sync(FULL, zl, 1);
-    zl += __shfl_xor_sync(FULL, zl, 2);
-    zh += __shfl_xor_sync(FULL, zh, 1);
-    zh += __shfl_xor_sync(FULL, zh, 2);
-    z_lo = zl;
-    z_hi = zh;
+// ---------------------------------------------------------------- forward on the tensor cores
+// One CTA of 128 threads works through 128-row tiles; thread t owns row t of the tile.  Layer 1 is
+// one tcgen05 MMA (M 128, N 64, K 16) of the feature rows by W1; layer 2 four MMAs (K = 64 in steps
+// of 16) of the BF16 h1 tile by W2.  The FP32 accumulators live in tensor memory (columns 0..63
+// layer 1, 64..127 layer 2) and come back to registers one row per thread for the epilogues: ReLU,
+// the constant unit, BF16 rounding and z = w3 . h2 summed in FP32 in unit order.
+#define TC_COLS 128u               // tensor-memory columns per CTA
+#define TC_SMEM (64 * 1024)        // dynamic shared memory per CTA; also keeps 3 CTAs at most on an SM
+#define TC_MAX_CTAS_PER_SM 4       // 512 tensor-memory columns / TC_COLS: more would wait in tcgen05.alloc
+#define TC_WAIT_NS 2000000000ull   // a wait for an MMA gives up after 2 s
+// shared-memory map (byte offsets; the base is 1024-byte aligned)
+#define TC_A1 0          // feature tile, 128 x 16 BF16
+#define TC_A2 4096       // h1 tile, 128 x 64 BF16
+#define TC_W1 20480      // W1, 64 x 16
+#define TC_W2 22528      // W2, 64 x 64
+#define TC_W3 30720      // w3 as FP32
+#define TC_BAR 30976     // mbarrier of the MMA completions
+#define TC_SLOT 30984    // tensor-memory base address written by tcgen05.alloc
+
+// Byte offset of 16-byte chunk `kg` of row `row` in a K-major tile of `kgroups` chunks per row.
+__device__ __forceinline__ uint32_t kmajor_off(int row, int kg, int kgroups) {
+    return (uint32_t)((row >> 3) * (128 * kgroups) + kg * 128 + (row & 7) * 16);
 }
 
-// z and/or score = exp(beta z) (beta z clamped to [-60, 60]), optionally h1 and h2, for R rows;
-// 4 warps per block, 16 rows per warp per step.
-__global__ void __launch_bounds__(128) mlp_forward_kernel(MlpWeights w, const bf16* __restrict__ X, long long R,
-                                                          float* __restrict__ z, float* __restrict__ score, float beta,
-                                                          bf16* __restrict__ h1, bf16* __restrict__ h2) {
-    __shared__ MlpSmem sh;
-    load_weights(sh, w);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    for (long long r0 = (blockIdx.x * 4LL + warp) * 16; r0 < R; r0 += gridDim.x * 64LL) {
-        float zl, zh;
-        forward16(sh, X, r0, R, lane, h1, h2, zl, zh);
-        if (t == 0) {
-            if (r0 + g < R) {
-                if (z) z[r0 + g] = zl;
-                if (score) score[r0 + g] = __expf(fminf(fmaxf(beta * zl, -60.f), 60.f));
-            }
-            if (r0 + g + 8 < R) {
-                if (z) z[r0 + g + 8] = zh;
-                if (score) score[r0 + g + 8] = __expf(fminf(fmaxf(beta * zh, -60.f), 60.f));
+// z and/or score = exp(beta z) (beta z clamped to [-60, 60]), optionally h1 and h2 (BF16), for R
+// rows.  A wait that gives up sets *status and writes NaN to the z and score rows this CTA has
+// not finished.
+__global__ void __launch_bounds__(128, 1)
+    mlp_forward_tc_kernel(MlpWeights w, const bf16* __restrict__ X, long long R, float* __restrict__ z,
+                          float* __restrict__ score, float beta, bf16* __restrict__ h1out, bf16* __restrict__ h2out,
+                          int* __restrict__ status) {
+    extern __shared__ __align__(1024) uint8_t tc_smem[];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tc_smem + TC_BAR);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(tc_smem + TC_SLOT);
+    float* w3s = reinterpret_cast<float*>(tc_smem + TC_W3);
+    // weights into the K-major operand layout (16-byte chunks of rows)
+    for (int c = tid; c < MLP_H * 2; c += 128)
+        *reinterpret_cast<uint4*>(tc_smem + TC_W1 + kmajor_off(c >> 1, c & 1, 2)) =
+            *reinterpret_cast<const uint4*>(w.W1 + (size_t)(c >> 1) * MLP_IN + 8 * (c & 1));
+    for (int c = tid; c < MLP_H * 8; c += 128)
+        *reinterpret_cast<uint4*>(tc_smem + TC_W2 + kmajor_off(c >> 3, c & 7, 8)) =
+            *reinterpret_cast<const uint4*>(w.W2 + (size_t)(c >> 3) * MLP_H + 8 * (c & 7));
+    if (tid < MLP_H) w3s[tid] = __bfloat162float(w.w3[tid]);
+    if (tid == 0) umma::mbar_init(bar, 1);
+    if (warp == 0) umma::tmem_alloc(slot, TC_COLS);
+    umma::fence_async_smem();
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *slot;
+    const uint32_t lanes = (uint32_t)(32 * warp) << 16;  // this warp's quarter of the lanes
+    constexpr uint32_t idesc = umma::IdescBf16<128, MLP_H>::value;
+    const uint32_t a1 = umma::smem_addr(tc_smem + TC_A1), a2 = umma::smem_addr(tc_smem + TC_A2);
+    const uint32_t b1 = umma::smem_addr(tc_smem + TC_W1), b2 = umma::smem_addr(tc_smem + TC_W2);
+    uint32_t phase = 0;
+    bool failed = false;
+    const long long tiles = (R + 127) / 128;
+    long long tile = blockIdx.x;
+    for (; tile < tiles; tile += gridDim.x) {
+        const long long row = tile * 128 + tid;
+        uint32_t xv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) xv[i] = row < R ? ld32(X + (size_t)row * MLP_IN + 2 * i) : 0u;
+        *reinterpret_cast<uint4*>(tc_smem + TC_A1 + kmajor_off(tid, 0, 2)) = make_uint4(xv[0], xv[1], xv[2], xv[3]);
+        *reinterpret_cast<uint4*>(tc_smem + TC_A1 + kmajor_off(tid, 1, 2)) = make_uint4(xv[4], xv[5], xv[6], xv[7]);
+        umma::fence_async_smem();
+        umma::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            umma::fence_after_sync();
+            umma::mma_bf16(tmem, umma::smem_desc(a1, 128, 256), umma::smem_desc(b1, 128, 256), idesc, 0u);
+            umma::commit(bar);
+        }
+        bool ok = umma::mbar_wait(bar, phase, TC_WAIT_NS);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        umma::fence_after_sync();
+        // layer-1 epilogue: h1 = bf16(relu(.)), unit 63 = 1, into the h1 tile (and out)
+        uint32_t hp[32];
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            float acc[32];
+            umma::tmem_ld32(tmem + lanes + 32u * half, acc);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int c = 32 * half + 2 * i;
+                const float v0 = fmaxf(acc[2 * i], 0.f);
+                const float v1 = c + 1 == MLP_H - 1 ? 1.f : fmaxf(acc[2 * i + 1], 0.f);
+                hp[16 * half + i] = pack_bf16(v0, v1);
             }
         }
+#pragma unroll
+        for (int kg = 0; kg < 8; ++kg) {
+            const uint4 v = make_uint4(hp[4 * kg], hp[4 * kg + 1], hp[4 * kg + 2], hp[4 * kg + 3]);
+            *reinterpret_cast<uint4*>(tc_smem + TC_A2 + kmajor_off(tid, kg, 8)) = v;
+            if (h1out && row < R) *reinterpret_cast<uint4*>(h1out + (size_t)row * MLP_H + 8 * kg) = v;
+        }
+        umma::fence_async_smem();
+        umma::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            umma::fence_after_sync();
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                umma::mma_bf16(tmem + MLP_H, umma::smem_desc(a2 + 256u * s, 128, 1024),
+                               umma::smem_desc(b2 + 256u * s, 128, 1024), idesc, s > 0 ? 1u : 0u);
+            umma::commit(bar);
+        }
+        ok = umma::mbar_wait(bar, phase, TC_WAIT_NS);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        umma::fence_after_sync();
+        // layer-2 epilogue and layer 3
+        float zr = 0.f;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            float acc[32];
+            umma::tmem_ld32(tmem + lanes + MLP_H + 32u * half, acc);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const int c = 32 * half + i;
+                acc[i] = c == MLP_H - 1 ? 1.f : bf16_round(fmaxf(acc[i], 0.f));
+                zr = __fmaf_rn(acc[i], w3s[c], zr);
+            }
+            if (h2out && row < R) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    *reinterpret_cast<uint4*>(h2out + (size_t)row * MLP_H + 32 * half + 8 * q) =
+                        make_uint4(pack_bf16(acc[8 * q], acc[8 * q + 1]), pack_bf16(acc[8 * q + 2], acc[8 * q + 3]),
+                                   pack_bf16(acc[8 * q + 4], acc[8 * q + 5]), pack_bf16(acc[8 * q + 6], acc[8 * q + 7]));
+            }
+        }
+        if (row < R) {
+            if (z) z[row] = zr;
+            if (score) score[row] = __expf(fminf(fmaxf(beta * zr, -60.f), 60.f));
+        }
+    }
+    if (failed) {
+        if (tid == 0) atomicExch(status, 1);
+        for (; tile < tiles; tile += gridDim.x) {
+            const long long row = tile * 128 + tid;
+            if (row < R) {
+                if (z) z[row] = __int_as_float(0x7fc00000);
+                if (score) score[row] = __int_as_float(0x7fc00000);
+            }
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        umma::fence_after_sync();
+        umma::tmem_dealloc(tmem, TC_COLS);
     }
 }
 
@@ -477,6 +538,8 @@ struct aco_mlp {
     bf16* dh2;
     bf16* dzm;      // max_rows * 16
     float* partial; // blocks * 4096
+    int* status;    // set by a forward whose wait for an MMA gave up
+    int tc_grid;    // CTAs of the forward: resident CTAs per SM x SMs
     char err[256];
 };
 
@@ -494,7 +557,7 @@ static void host_mask(uint8_t* mk) {
 
 static void free_mlp(aco_mlp* h) {
     void* ptrs[] = {h->w, h->m1, h->m2, h->grad, h->mask, h->wb, h->z, h->dz, h->closs,
-                    h->h1, h->h2, h->dh1, h->dh2, h->dzm, h->partial};
+                    h->h1, h->h2, h->dh1, h->dh2, h->dzm, h->partial, h->status};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -512,6 +575,34 @@ static aco_status mlp_launch_ok(aco_mlp* h, const char* what) {
 }
 
 extern "C" const char* aco_mlp_last_error(const aco_mlp* h) { return h ? h->err : ""; }
+
+// The forward's launch shape: its shared memory admits at most TC_MAX_CTAS_PER_SM CTAs per SM, so
+// their tensor-memory allocations always fit and tcgen05.alloc never waits; refused otherwise.
+static aco_status setup_forward_tc(aco_mlp* h) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp_forward_tc_kernel, 128, TC_SMEM);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        snprintf(h->err, sizeof(h->err), "forward setup: %s", cudaGetErrorString(e));
+        return ACO_ERR_CUDA;
+    }
+    if (occ < 1 || occ > TC_MAX_CTAS_PER_SM) {
+        snprintf(h->err, sizeof(h->err), "forward setup: %d resident CTAs per SM (1..%d needed)", occ, TC_MAX_CTAS_PER_SM);
+        return ACO_ERR_CUDA;
+    }
+    h->tc_grid = occ * sms;
+    return ACO_OK;
+}
+
+static void launch_forward(aco_mlp* h, const bf16* X, long long rows, float* z, float* score, float beta, bf16* h1,
+                           bf16* h2) {
+    const long long tiles = (rows + 127) / 128;
+    const int grid = (int)(tiles < h->tc_grid ? tiles : h->tc_grid);
+    mlp_forward_tc_kernel<<<grid, 128, TC_SMEM, h->stream>>>(weights_of(h), X, rows, z, score, beta, h1, h2, h->status);
+}
 
 extern "C" aco_status aco_mlp_create(const float* w_host, int64_t max_rows, void* stream, aco_mlp** out) {
     ACO_RANGE("aco_mlp_create");
@@ -541,6 +632,7 @@ extern "C" aco_status aco_mlp_create(const float* w_host, int64_t max_rows, void
     ok &= cudaMalloc(&h->dh2, sizeof(bf16) * MLP_H * max_rows) == cudaSuccess;
     ok &= cudaMalloc(&h->dzm, sizeof(bf16) * 16 * max_rows) == cudaSuccess;
     ok &= cudaMalloc(&h->partial, sizeof(float) * MLP_H * MLP_H * blocks) == cudaSuccess;
+    ok &= cudaMalloc(&h->status, sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_mlp(h);
@@ -556,11 +648,13 @@ extern "C" aco_status aco_mlp_create(const float* w_host, int64_t max_rows, void
     cudaMemsetAsync(h->m1, 0, sizeof(float) * MLP_NW, h->stream);
     cudaMemsetAsync(h->m2, 0, sizeof(float) * MLP_NW, h->stream);
     cudaMemsetAsync(h->grad, 0, sizeof(float) * MLP_NW, h->stream);
+    cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
     // BF16 copies: an Adam step with zero learning rate leaves the masters and refreshes them
     mlp_adam_kernel<<<blocks_for(MLP_NW, 256), 256, 0, h->stream>>>(h->w, h->m1, h->m2, h->grad, h->mask, MLP_NW, 0.f,
                                                                     0.9f, 0.999f, 1e-8f, 1.f, 1.f, h->wb);
     aco_status st = mlp_launch_ok(h, "create");
     if (st == ACO_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) st = ACO_ERR_CUDA;
+    if (st == ACO_OK) st = setup_forward_tc(h);
     if (st != ACO_OK) {
         free_mlp(h);
         delete h;
@@ -579,11 +673,17 @@ extern "C" void aco_mlp_destroy(aco_mlp* h) {
 
 extern "C" aco_status aco_mlp_get_weights(aco_mlp* h, float* w_host) {
     if (!h || !w_host) return ACO_ERR_INVALID_ARG;
+    int failed = 0;
     cudaError_t e = cudaMemcpyAsync(w_host, h->w, sizeof(float) * MLP_NW, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&failed, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         snprintf(h->err, sizeof(h->err), "get_weights: %s", cudaGetErrorString(e));
         return ACO_ERR_CUDA;
+    }
+    if (failed) {
+        snprintf(h->err, sizeof(h->err), "a forward pass gave up waiting for a tensor-core MMA");
+        return ACO_ERR_TIMEOUT;
     }
     return ACO_OK;
 }
@@ -593,9 +693,8 @@ extern "C" aco_status aco_mlp_forward(aco_mlp* h, const uint16_t* X_dev, int64_t
     ACO_RANGE("aco_mlp_forward");
     if (!h || !X_dev || rows < 0 || (!z_dev && !score_dev) || !isfinite(beta)) return ACO_ERR_INVALID_ARG;
     if (rows == 0) return ACO_OK;
-    mlp_forward_kernel<<<blocks_for(rows, 64), 128, 0, h->stream>>>(weights_of(h), (const bf16*)X_dev, rows, z_dev,
-                                                                   score_dev, beta, nullptr, nullptr);
-    return mlp_launch_ok(h, "mlp_forward_kernel");
+    launch_forward(h, (const bf16*)X_dev, rows, z_dev, score_dev, beta, nullptr, nullptr);
+    return mlp_launch_ok(h, "mlp_forward_tc_kernel");
 }
 
 // forward with stored activations, loss, backward: gradient of scale * (summed loss) into
@@ -605,7 +704,7 @@ static aco_status mlp_backward(aco_mlp* h, const bf16* X, const uint32_t* target
     const int rows = cities * k;
     cudaStream_t s = h->stream;
     const MlpWeights w = weights_of(h);
-    mlp_forward_kernel<<<blocks_for(rows, 64), 128, 0, s>>>(w, X, rows, h->z, nullptr, 1.f, h->h1, h->h2);
+    launch_forward(h, X, rows, h->z, nullptr, 1.f, h->h1, h->h2);
     mlp_loss_kernel<<<blocks_for(cities, 8), 256, 0, s>>>(h->z, target, cities, k, h->dz, h->closs);
     if (loss_dev) sum_kernel<<<1, 1024, 0, s>>>(h->closs, cities, scale, loss_dev);
     // the row gradient kernels take dz * scale: fold the scale into dz once
