@@ -320,12 +320,13 @@ aco_status aco_batch_instance(aco_batch* b, int32_t i, aco_instance** out);
 typedef struct aco_mlp aco_mlp; /* opaque: weights, optimiser state and training scratch */
 
 /* w_host: ACO_MLP_WEIGHTS initial FP32 weights (finite).  max_rows: the most candidate-edge rows
- * one aco_mlp_backward call or one aco_mlp_train batch may hold (16 .. 2^30; about 600 bytes of
+ * one aco_mlp_backward call or one aco_mlp_train batch may hold (16 .. 2^30; about 350 bytes of
  * device memory per row).  stream: cudaStream_t for all of this network's work (NULL = legacy
  * default stream).  Allocates everything.  Synchronises. */
 aco_status aco_mlp_create(const float* w_host, int64_t max_rows, void* stream, aco_mlp** out);
-/* The FP32 weights (ACO_MLP_WEIGHTS floats).  Synchronises.  ACO_ERR_TIMEOUT if a forward pass on
- * this handle gave up waiting for a tensor-core MMA (2 s; its unfinished rows were written NaN). */
+/* The FP32 weights (ACO_MLP_WEIGHTS floats).  Synchronises.  ACO_ERR_TIMEOUT if a forward or
+ * backward pass on this handle gave up waiting for a tensor-core MMA (2 s; its unfinished rows or
+ * gradient blocks were written NaN). */
 aco_status aco_mlp_get_weights(aco_mlp* h, float* w_host);
 /* z_dev and/or score_dev = exp(beta z) (rows floats each; either may be NULL, not both) for rows of
  * BF16 features X_dev (rows * 16 BF16 bit patterns, 4-byte aligned).  No row limit.  On the tcgen05

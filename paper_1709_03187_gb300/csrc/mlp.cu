@@ -7,18 +7,17 @@
 //   h2 = relu(W2 h1)     W2: 64 x 64
 //   h2[63] = 1           (constant unit: w3[63] is the output bias)
 //   z  = w3 . h2         score = exp(z)
-// BF16 weights and activations, FP32 accumulation on the tensor cores, the hidden activations
-// rounded to BF16 between layers.  The forward pass runs on the fifth-generation tensor cores
-// (tcgen05 MMAs with accumulators in tensor memory, umma.cuh); the backward products use the warp
-// MMA (mma.sync m16n8k16).
+// BF16 weights and activations, FP32 accumulation on the fifth-generation tensor cores (tcgen05
+// MMAs with accumulators in tensor memory, umma.cuh), the hidden activations rounded to BF16
+// between layers.
 //
 // Training objective: for every city, the softmax of z over its k candidate edges against the
 // best tour's edges among them (cross-entropy; each of the city's best-tour neighbours that is a
 // candidate carries equal target mass).  Gradients:
 //   dz = softmax(z) - y;  dh2 = dz w3 * [h2 > 0];  dh1 = dh2 W2 * [h1 > 0]  (constant units 0)
 //   dW2 = dh2^T h1;  dW1 = dh1^T x;  dw3 = dz^T h2
-// The weight gradients are split-K over blocks with per-block partial sums and a fixed-order
-// reduction, so a training step is deterministic.  Adam on FP32 master weights.
+// The weight gradients are split over blocks of MLP_RPB rows with per-block partial sums and a
+// fixed-order reduction, so a training step is deterministic.  Adam on FP32 master weights.
 #include <cuda_bf16.h>
 #include <float.h>
 #include <math.h>
@@ -33,6 +32,8 @@
 #define FULL 0xffffffffu
 #define MLP_IN 16
 #define MLP_H 64
+#define MLP_NW (MLP_H * MLP_IN + MLP_H * MLP_H + MLP_H)  // W1 | W2 | w3
+#define MLP_RPB 256  // rows per block of the weight gradients (summed in FP32, then the blocks in order)
 
 typedef __nv_bfloat16 bf16;
 
@@ -43,39 +44,11 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
-// D = A(16x16 bf16, row) * B(16x8 bf16, col) + C (fp32)
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 struct MlpWeights {  // BF16 copies used by the kernels
     const bf16* W1;  // [64][16]
     const bf16* W2;  // [64][64]
     const bf16* w3;  // [64]
 };
-
-// Stage the BF16 weights in shared memory (W2 also transposed for the backward pass).
-struct MlpSmem {
-    bf16 W1[MLP_H * MLP_IN];
-    bf16 W2[MLP_H * MLP_H];
-    bf16 W2T[MLP_H * MLP_H];
-    float w3[MLP_H];
-};
-
-__device__ void load_weights(MlpSmem& sh, const MlpWeights& w) {
-    for (int i = threadIdx.x; i < MLP_H * MLP_IN; i += blockDim.x) sh.W1[i] = w.W1[i];
-    for (int i = threadIdx.x; i < MLP_H * MLP_H; i += blockDim.x) {
-        sh.W2[i] = w.W2[i];
-        const int r = i / MLP_H, c = i % MLP_H;
-        sh.W2T[c * MLP_H + r] = w.W2[i];
-    }
-    for (int i = threadIdx.x; i < MLP_H; i += blockDim.x) sh.w3[i] = __bfloat162float(w.w3[i]);
-    __syncthreads();
-}
 
 __device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
@@ -241,6 +214,212 @@ __global__ void __launch_bounds__(128, 1)
     }
 }
 
+// ---------------------------------------------------------------- backward on the tensor cores
+// One CTA per block of MLP_RPB = 256 rows: two 128-row sub-tiles, thread t owning row t of each.
+// Per sub-tile: dh2 = dz w3 [h2 > 0] in registers; dh1 = dh2 W2 [h1 > 0] by four tcgen05 MMAs
+// (M 128, N 64, K 16; B = W2 transposed, K-major); then a chain of eight MMAs over the sub-tile's
+// rows accumulates
+//     D[128 x 144] += [dh2 | dh1]^T [h1 | x | h2]
+// with both operands MN-major (the rows are the contraction index): D[u][0..63] = dW2 row u,
+// D[64 + u][64..79] = dW1 row u, and because unit 63 of dh2 is always zero (the constant unit) that
+// row of the A operand carries dz instead, so that D[63][80..143] = dw3.  The block's gradient goes
+// out as one partial vector in the layout W1 | W2 | w3, reduced over the blocks in order by
+// mlp_reduce_kernel.
+#define TCB_COLS 256u               // tensor-memory columns per CTA: dh1 (64) and D (144)
+#define TCB_SMEM (96 * 1024)        // dynamic shared memory per CTA; also keeps 2 CTAs at most on an SM
+#define TCB_MAX_CTAS_PER_SM 2       // 512 tensor-memory columns / TCB_COLS
+#define TCB_N 144                   // columns of D: h1 | x | h2
+#define TCB_W2T 0                   // W2 transposed, 64 x 64 K-major (8 KB)
+#define TCB_AH 8192                 // dh2 tile, 128 x 64 K-major (16 KB)
+#define TCB_AW 24576                // [dh2 | dh1], 16 unit groups x 16 row groups, MN-major (32 KB)
+#define TCB_BW 57344                // [h1 | x | h2], 18 column groups x 16 row groups, MN-major (36 KB)
+#define TCB_W3 94208                // w3 as FP32
+#define TCB_BAR 94464
+#define TCB_SLOT 94472
+
+// Byte offset of the 16-byte chunk of M/N group g (8 values) in row r (along K) of an MN-major
+// tile of 128 rows: 16 K groups of 128 bytes per M/N group.
+__device__ __forceinline__ uint32_t mnmajor_off(int r, int g) {
+    return (uint32_t)(g * 2048 + (r >> 3) * 128 + (r & 7) * 16);
+}
+
+__device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
+__device__ __forceinline__ uint32_t word_of(const uint4& v, int i) {
+    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// Per block of MLP_RPB rows the gradient of sum(scale * loss) into partial[block][MLP_NW];
+// dz: softmax - y per row (unscaled); h1, h2: the forward's BF16 activations.  A wait that gives
+// up sets *status and writes NaN into the block's partial vector.
+__global__ void __launch_bounds__(128, 1)
+    mlp_backward_tc_kernel(MlpWeights w, const bf16* __restrict__ X, const float* __restrict__ dz, float scale, int R,
+                           const bf16* __restrict__ h1, const bf16* __restrict__ h2, float* __restrict__ partial,
+                           int* __restrict__ status) {
+    extern __shared__ __align__(1024) uint8_t tcb_smem[];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tcb_smem + TCB_BAR);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(tcb_smem + TCB_SLOT);
+    float* w3s = reinterpret_cast<float*>(tcb_smem + TCB_W3);
+    // B of dh1 = dh2 W2: B[n][k] = W2[k][n] (n an h1 unit, k an h2 unit), K-major
+    for (int e = tid; e < MLP_H * MLP_H; e += 128) {
+        const int k = e >> 6, n = e & 63;
+        *reinterpret_cast<bf16*>(tcb_smem + TCB_W2T + kmajor_off(n, k >> 3, 8) + (k & 7) * 2) = w.W2[e];
+    }
+    if (tid < MLP_H) w3s[tid] = __bfloat162float(w.w3[tid]);
+    if (tid == 0) umma::mbar_init(bar, 1);
+    if (warp == 0) umma::tmem_alloc(slot, TCB_COLS);
+    umma::fence_async_smem();
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *slot;
+    const uint32_t dh = tmem, dd = tmem + MLP_H;         // dh1 accumulator, gradient accumulator
+    const uint32_t lanes = (uint32_t)(32 * warp) << 16;
+    constexpr uint32_t idesc_h = umma::IdescBf16<128, MLP_H>::value;
+    constexpr uint32_t idesc_w = umma::IdescBf16<128, TCB_N, true, true>::value;
+    const uint32_t ah = umma::smem_addr(tcb_smem + TCB_AH), w2t = umma::smem_addr(tcb_smem + TCB_W2T);
+    const uint32_t aw = umma::smem_addr(tcb_smem + TCB_AW), bw = umma::smem_addr(tcb_smem + TCB_BW);
+    uint32_t phase = 0;
+    bool failed = false;
+    const long long rbeg = (long long)blockIdx.x * MLP_RPB;
+    for (int sub = 0; sub < 2 && !failed; ++sub) {
+        const long long row = rbeg + 128 * sub + tid;
+        const bool live = row < R;
+        const float d = live ? dz[row] * scale : 0.f;
+        uint4 h1v[8], h2v[8], xv[2];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            h1v[q] = live ? *reinterpret_cast<const uint4*>(h1 + (size_t)row * MLP_H + 8 * q) : make_uint4(0, 0, 0, 0);
+            h2v[q] = live ? *reinterpret_cast<const uint4*>(h2 + (size_t)row * MLP_H + 8 * q) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            uint32_t x4[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) x4[i] = live ? ld32(X + (size_t)row * MLP_IN + 8 * q + 2 * i) : 0u;
+            xv[q] = make_uint4(x4[0], x4[1], x4[2], x4[3]);
+        }
+        // dh2 = dz w3 where h2 > 0 (the constant unit 63 gets 0), BF16 pairs
+        uint32_t dp[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const uint32_t hw = word_of(h2v[i >> 2], i & 3);
+            const int c = 2 * i;
+            const float a = bf16_lo(hw) > 0.f ? d * w3s[c] : 0.f;
+            const float b = (c + 1 != MLP_H - 1 && bf16_hi(hw) > 0.f) ? d * w3s[c + 1] : 0.f;
+            dp[i] = pack_bf16(a, b);
+        }
+        const uint32_t dzb = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(d));
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            const uint4 v = make_uint4(dp[4 * g], dp[4 * g + 1], dp[4 * g + 2], dp[4 * g + 3]);
+            *reinterpret_cast<uint4*>(tcb_smem + TCB_AH + kmajor_off(tid, g, 8)) = v;
+            // the A operand of the gradient: unit 63 carries dz
+            const uint4 u = g == 7 ? make_uint4(v.x, v.y, v.z, (v.w & 0xffffu) | (dzb << 16)) : v;
+            *reinterpret_cast<uint4*>(tcb_smem + TCB_AW + mnmajor_off(tid, g)) = u;
+            *reinterpret_cast<uint4*>(tcb_smem + TCB_BW + mnmajor_off(tid, g)) = h1v[g];
+            *reinterpret_cast<uint4*>(tcb_smem + TCB_BW + mnmajor_off(tid, 10 + g)) = h2v[g];
+        }
+        *reinterpret_cast<uint4*>(tcb_smem + TCB_BW + mnmajor_off(tid, 8)) = xv[0];
+        *reinterpret_cast<uint4*>(tcb_smem + TCB_BW + mnmajor_off(tid, 9)) = xv[1];
+        umma::fence_async_smem();
+        umma::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            umma::fence_after_sync();
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                umma::mma_bf16(dh, umma::smem_desc(ah + 256u * s, 128, 1024), umma::smem_desc(w2t + 256u * s, 128, 1024),
+                               idesc_h, s > 0 ? 1u : 0u);
+            umma::commit(bar);
+        }
+        bool ok = umma::mbar_wait(bar, phase, TC_WAIT_NS);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        umma::fence_after_sync();
+        // dh1 = (dh2 W2) where h1 > 0 (unit 63 gets 0), BF16, into units 64..127 of the A operand
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            float acc[32];
+            umma::tmem_ld32(dh + lanes + 32u * half, acc);
+            uint32_t hp[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int c = 32 * half + 2 * i;
+                const uint32_t hw = word_of(h1v[c >> 3], (c >> 1) & 3);
+                const float a = bf16_lo(hw) > 0.f ? acc[2 * i] : 0.f;
+                const float b = (c + 1 != MLP_H - 1 && bf16_hi(hw) > 0.f) ? acc[2 * i + 1] : 0.f;
+                hp[i] = pack_bf16(a, b);
+            }
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+                *reinterpret_cast<uint4*>(tcb_smem + TCB_AW + mnmajor_off(tid, 8 + 4 * half + g)) =
+                    make_uint4(hp[4 * g], hp[4 * g + 1], hp[4 * g + 2], hp[4 * g + 3]);
+        }
+        umma::fence_async_smem();
+        umma::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            umma::fence_after_sync();
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+                umma::mma_bf16(dd, umma::smem_desc(aw + 256u * s, 128, 2048), umma::smem_desc(bw + 256u * s, 128, 2048),
+                               idesc_w, (sub > 0 || s > 0) ? 1u : 0u);
+            umma::commit(bar);
+        }
+        ok = umma::mbar_wait(bar, phase, TC_WAIT_NS);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        umma::fence_after_sync();
+    }
+    float* out = partial + (size_t)blockIdx.x * MLP_NW;
+    if (!failed) {
+        // thread t holds row t of D
+        if (warp < 2) {
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                float acc[32];
+                umma::tmem_ld32(dd + lanes + 32u * half, acc);
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    out[MLP_H * MLP_IN + tid * MLP_H + 32 * half + i] = tid == MLP_H - 1 ? 0.f : acc[i];
+            }
+            if (warp == 1) {
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    float acc[32];
+                    umma::tmem_ld32(dd + lanes + 80u + 32u * half, acc);
+                    if (tid == MLP_H - 1) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) out[MLP_H * MLP_IN + MLP_H * MLP_H + 32 * half + i] = acc[i];
+                    }
+                }
+            }
+        } else {
+            float acc[32];
+            umma::tmem_ld32(dd + lanes + 64u, acc);
+#pragma unroll
+            for (int i = 0; i < MLP_IN; ++i) out[(tid - MLP_H) * MLP_IN + i] = acc[i];
+        }
+    } else {
+        if (tid == 0) atomicExch(status, 1);
+        for (int e = tid; e < MLP_NW; e += 128) out[e] = __int_as_float(0x7fc00000);
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        umma::fence_after_sync();
+        umma::tmem_dealloc(tmem, TCB_COLS);
+    }
+}
+
 // Softmax cross-entropy per city over its k consecutive rows.  target: per city a bitmask of
 // the candidate ranks that are best-tour neighbours (cities with no such rank are skipped).
 // dz[row] = softmax - y; loss per city into city_loss (0 when skipped).
@@ -265,137 +444,6 @@ __global__ void mlp_loss_kernel(const float* __restrict__ z, const uint32_t* __r
     }
 }
 
-// Backward over rows: dh2 = dz w3 [h2 > 0], dh1 = dh2 W2 [h1 > 0] (constant units get 0).
-// Also writes dz as a BF16 [R][16] matrix (column 0) for the dw3 reduction.
-__global__ void __launch_bounds__(128) mlp_backward_rows_kernel(MlpWeights w, const float* __restrict__ dz, int R,
-                                                                const bf16* __restrict__ h1,
-                                                                const bf16* __restrict__ h2, bf16* __restrict__ dh1,
-                                                                bf16* __restrict__ dh2, bf16* __restrict__ dzm) {
-    __shared__ MlpSmem sh;
-    load_weights(sh, w);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    for (int r0 = (blockIdx.x * 4 + warp) * 16; r0 < R; r0 += gridDim.x * 64) {
-        const int ra = r0 + g, rb = r0 + g + 8;
-        const float dza = ra < R ? dz[ra] : 0.f, dzb = rb < R ? dz[rb] : 0.f;
-        // dh2 in A-fragment layout: k-step s covers columns 16s..16s+15
-        uint32_t a[4][4];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-#pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {  // columns 16s + 8hh + 2t, +1
-                const int col = 16 * s + 8 * hh + 2 * t;
-                float v[4];
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const float ha = ra < R ? __bfloat162float(h2[(size_t)ra * MLP_H + col + e]) : 0.f;
-                    const float hb = rb < R ? __bfloat162float(h2[(size_t)rb * MLP_H + col + e]) : 0.f;
-                    const bool live = col + e != MLP_H - 1;
-                    v[e] = (live && ha > 0.f) ? dza * sh.w3[col + e] : 0.f;
-                    v[2 + e] = (live && hb > 0.f) ? dzb * sh.w3[col + e] : 0.f;
-                }
-                a[s][2 * hh] = pack_bf16(v[0], v[1]);
-                a[s][2 * hh + 1] = pack_bf16(v[2], v[3]);
-                if (ra < R) *reinterpret_cast<uint32_t*>(dh2 + (size_t)ra * MLP_H + col) = a[s][2 * hh];
-                if (rb < R) *reinterpret_cast<uint32_t*>(dh2 + (size_t)rb * MLP_H + col) = a[s][2 * hh + 1];
-            }
-        }
-        // dh1 = dh2 W2: B(k = h2 unit, n = h1 unit) = W2[k][n] = W2T[n][k]
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            float d[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                const uint32_t b[2] = {ld32(&sh.W2T[(8 * j + g) * MLP_H + 16 * s + 2 * t]),
-                                       ld32(&sh.W2T[(8 * j + g) * MLP_H + 16 * s + 8 + 2 * t])};
-                mma_bf16(d, a[s], b);
-            }
-            const int col = 8 * j + 2 * t;
-            float v[4];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const float ha = ra < R ? __bfloat162float(h1[(size_t)ra * MLP_H + col + e]) : 0.f;
-                const float hb = rb < R ? __bfloat162float(h1[(size_t)rb * MLP_H + col + e]) : 0.f;
-                const bool live = col + e != MLP_H - 1;
-                v[e] = (live && ha > 0.f) ? d[e] : 0.f;
-                v[2 + e] = (live && hb > 0.f) ? d[2 + e] : 0.f;
-            }
-            if (ra < R) *reinterpret_cast<uint32_t*>(dh1 + (size_t)ra * MLP_H + col) = pack_bf16(v[0], v[1]);
-            if (rb < R) *reinterpret_cast<uint32_t*>(dh1 + (size_t)rb * MLP_H + col) = pack_bf16(v[2], v[3]);
-        }
-        if (t == 0) {
-            if (ra < R) dzm[(size_t)ra * 16] = __float2bfloat16_rn(dza);
-            if (rb < R) dzm[(size_t)rb * 16] = __float2bfloat16_rn(dzb);
-        }
-    }
-}
-
-// Split-K partial products C_b = P^T Q over the rows of block b: P [R][MP], Q [R][NQ] (BF16),
-// MP in {16, 64}, NQ in {16, 64}.  Rows in 16-row steps; partial[b][MP][NQ] in FP32.
-// Each warp owns output tiles (16 rows of C) x (8 columns); fragments are assembled from
-// shared-memory copies of the row step.
-template <int MP, int NQ>
-__global__ void __launch_bounds__(128) mlp_wgrad_kernel(const bf16* __restrict__ P, const bf16* __restrict__ Q, int R,
-                                                        int rows_per_block, float* __restrict__ partial) {
-    constexpr int MT = MP / 16, NT = NQ / 8, TILES = MT * NT, TPW = (TILES + 3) / 4;
-    __shared__ bf16 Ps[16][MP];
-    __shared__ bf16 Qs[16][NQ];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    float acc[TPW][4];
-#pragma unroll
-    for (int i = 0; i < TPW; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
-    const int rbeg = blockIdx.x * rows_per_block, rend = min(R, rbeg + rows_per_block);
-    for (int r0 = rbeg; r0 < rend; r0 += 16) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < 16 * MP; i += blockDim.x) {
-            const int rr = i / MP, cc = i % MP;
-            Ps[rr][cc] = r0 + rr < rend ? P[(size_t)(r0 + rr) * MP + cc] : __float2bfloat16_rn(0.f);
-        }
-        for (int i = threadIdx.x; i < 16 * NQ; i += blockDim.x) {
-            const int rr = i / NQ, cc = i % NQ;
-            Qs[rr][cc] = r0 + rr < rend ? Q[(size_t)(r0 + rr) * NQ + cc] : __float2bfloat16_rn(0.f);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < TPW; ++i) {
-            const int tile = warp * TPW + i;
-            if (tile >= TILES) break;
-            const int mt = tile / NT, nt = tile % NT;
-            // A = P^T (m = C row, k = data row): a0 (m g, k 2t..2t+1), a1 (m g+8), a2 (k +8), a3
-            const int m0 = 16 * mt;
-            uint32_t a[4];
-            a[0] = pack_bf16(__bfloat162float(Ps[2 * t][m0 + g]), __bfloat162float(Ps[2 * t + 1][m0 + g]));
-            a[1] = pack_bf16(__bfloat162float(Ps[2 * t][m0 + g + 8]), __bfloat162float(Ps[2 * t + 1][m0 + g + 8]));
-            a[2] = pack_bf16(__bfloat162float(Ps[2 * t + 8][m0 + g]), __bfloat162float(Ps[2 * t + 9][m0 + g]));
-            a[3] = pack_bf16(__bfloat162float(Ps[2 * t + 8][m0 + g + 8]), __bfloat162float(Ps[2 * t + 9][m0 + g + 8]));
-            // B = Q (k = data row, n = C column): b0 (k 2t..2t+1, n g), b1 (k +8)
-            const int n0 = 8 * nt;
-            uint32_t b[2];
-            b[0] = pack_bf16(__bfloat162float(Qs[2 * t][n0 + g]), __bfloat162float(Qs[2 * t + 1][n0 + g]));
-            b[1] = pack_bf16(__bfloat162float(Qs[2 * t + 8][n0 + g]), __bfloat162float(Qs[2 * t + 9][n0 + g]));
-            mma_bf16(acc[i], a, b);
-        }
-    }
-    float* out = partial + (size_t)blockIdx.x * MP * NQ;
-#pragma unroll
-    for (int i = 0; i < TPW; ++i) {
-        const int tile = warp * TPW + i;
-        if (tile >= TILES) break;
-        const int mt = tile / NT, nt = tile % NT;
-        const int m = 16 * mt + g, n = 8 * nt + 2 * t;
-        out[(size_t)m * NQ + n] = acc[i][0];
-        out[(size_t)m * NQ + n + 1] = acc[i][1];
-        out[(size_t)(m + 8) * NQ + n] = acc[i][2];
-        out[(size_t)(m + 8) * NQ + n + 1] = acc[i][3];
-    }
-}
-
-__global__ void mlp_scale_kernel(float* __restrict__ v, int count, float scale) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) v[e] *= scale;
-}
-
-// grad[e] = sum over blocks (in block order) of partial[b * stride + e] * scale, e < elems.
 __global__ void mlp_reduce_kernel(const float* __restrict__ partial, int blocks, int stride, int elems, float scale,
                                   float* __restrict__ grad) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < elems; e += gridDim.x * blockDim.x) {
@@ -516,8 +564,6 @@ __global__ void sum_kernel(const float* __restrict__ v, int count, float scale, 
 }
 
 // ---------------------------------------------------------------- the network handle
-#define MLP_NW (MLP_H * MLP_IN + MLP_H * MLP_H + MLP_H)
-#define MLP_RPB 256  // rows per block of the split-K weight gradients
 
 struct aco_mlp {
     cudaStream_t stream;
@@ -534,11 +580,8 @@ struct aco_mlp {
     float* closs;   // max_rows (per city, cities <= rows)
     bf16* h1;       // max_rows * 64
     bf16* h2;
-    bf16* dh1;
-    bf16* dh2;
-    bf16* dzm;      // max_rows * 16
-    float* partial; // blocks * 4096
-    int* status;    // set by a forward whose wait for an MMA gave up
+    float* partial; // blocks * MLP_NW: per block of MLP_RPB rows its part of the gradient
+    int* status;    // set by a forward or backward whose wait for an MMA gave up
     int tc_grid;    // CTAs of the forward: resident CTAs per SM x SMs
     char err[256];
 };
@@ -557,7 +600,7 @@ static void host_mask(uint8_t* mk) {
 
 static void free_mlp(aco_mlp* h) {
     void* ptrs[] = {h->w, h->m1, h->m2, h->grad, h->mask, h->wb, h->z, h->dz, h->closs,
-                    h->h1, h->h2, h->dh1, h->dh2, h->dzm, h->partial, h->status};
+                    h->h1, h->h2, h->partial, h->status};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -576,25 +619,39 @@ static aco_status mlp_launch_ok(aco_mlp* h, const char* what) {
 
 extern "C" const char* aco_mlp_last_error(const aco_mlp* h) { return h ? h->err : ""; }
 
-// The forward's launch shape: its shared memory admits at most TC_MAX_CTAS_PER_SM CTAs per SM, so
-// their tensor-memory allocations always fit and tcgen05.alloc never waits; refused otherwise.
-static aco_status setup_forward_tc(aco_mlp* h) {
-    int dev = 0, sms = 0, occ = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp_forward_tc_kernel, 128, TC_SMEM);
+// Launch shapes of the tensor-core kernels: their shared memory admits so few CTAs per SM that the
+// CTAs' tensor-memory allocations (512 columns per SM) always fit and tcgen05.alloc never waits;
+// refused otherwise.  Returns the forward's grid in h->tc_grid.
+static aco_status setup_tc_kernel(aco_mlp* h, const void* kernel, int smem, int max_per_sm, const char* name,
+                                  int* occ_out) {
+    int occ = 0;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 128, smem);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        snprintf(h->err, sizeof(h->err), "forward setup: %s", cudaGetErrorString(e));
+        snprintf(h->err, sizeof(h->err), "%s setup: %s", name, cudaGetErrorString(e));
         return ACO_ERR_CUDA;
     }
-    if (occ < 1 || occ > TC_MAX_CTAS_PER_SM) {
-        snprintf(h->err, sizeof(h->err), "forward setup: %d resident CTAs per SM (1..%d needed)", occ, TC_MAX_CTAS_PER_SM);
+    if (occ < 1 || occ > max_per_sm) {
+        snprintf(h->err, sizeof(h->err), "%s setup: %d resident CTAs per SM (1..%d needed)", name, occ, max_per_sm);
         return ACO_ERR_CUDA;
     }
-    h->tc_grid = occ * sms;
+    *occ_out = occ;
     return ACO_OK;
+}
+
+static aco_status setup_forward_tc(aco_mlp* h) {
+    int dev = 0, sms = 0, occ = 0, occ_b = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        snprintf(h->err, sizeof(h->err), "tensor-core setup: no device");
+        return ACO_ERR_CUDA;
+    }
+    aco_status st = setup_tc_kernel(h, (const void*)mlp_forward_tc_kernel, TC_SMEM, TC_MAX_CTAS_PER_SM, "forward", &occ);
+    if (st == ACO_OK)
+        st = setup_tc_kernel(h, (const void*)mlp_backward_tc_kernel, TCB_SMEM, TCB_MAX_CTAS_PER_SM, "backward", &occ_b);
+    h->tc_grid = occ * sms;
+    return st;
 }
 
 static void launch_forward(aco_mlp* h, const bf16* X, long long rows, float* z, float* score, float beta, bf16* h1,
@@ -628,10 +685,7 @@ extern "C" aco_status aco_mlp_create(const float* w_host, int64_t max_rows, void
     ok &= cudaMalloc(&h->closs, sizeof(float) * max_rows) == cudaSuccess;
     ok &= cudaMalloc(&h->h1, sizeof(bf16) * MLP_H * max_rows) == cudaSuccess;
     ok &= cudaMalloc(&h->h2, sizeof(bf16) * MLP_H * max_rows) == cudaSuccess;
-    ok &= cudaMalloc(&h->dh1, sizeof(bf16) * MLP_H * max_rows) == cudaSuccess;
-    ok &= cudaMalloc(&h->dh2, sizeof(bf16) * MLP_H * max_rows) == cudaSuccess;
-    ok &= cudaMalloc(&h->dzm, sizeof(bf16) * 16 * max_rows) == cudaSuccess;
-    ok &= cudaMalloc(&h->partial, sizeof(float) * MLP_H * MLP_H * blocks) == cudaSuccess;
+    ok &= cudaMalloc(&h->partial, sizeof(float) * MLP_NW * blocks) == cudaSuccess;
     ok &= cudaMalloc(&h->status, sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -682,7 +736,7 @@ extern "C" aco_status aco_mlp_get_weights(aco_mlp* h, float* w_host) {
         return ACO_ERR_CUDA;
     }
     if (failed) {
-        snprintf(h->err, sizeof(h->err), "a forward pass gave up waiting for a tensor-core MMA");
+        snprintf(h->err, sizeof(h->err), "a forward or backward pass gave up waiting for a tensor-core MMA");
         return ACO_ERR_TIMEOUT;
     }
     return ACO_OK;
@@ -703,25 +757,13 @@ static aco_status mlp_backward(aco_mlp* h, const bf16* X, const uint32_t* target
                                float* loss_dev) {
     const int rows = cities * k;
     cudaStream_t s = h->stream;
-    const MlpWeights w = weights_of(h);
     launch_forward(h, X, rows, h->z, nullptr, 1.f, h->h1, h->h2);
     mlp_loss_kernel<<<blocks_for(cities, 8), 256, 0, s>>>(h->z, target, cities, k, h->dz, h->closs);
     if (loss_dev) sum_kernel<<<1, 1024, 0, s>>>(h->closs, cities, scale, loss_dev);
-    // the row gradient kernels take dz * scale: fold the scale into dz once
-    cudaMemsetAsync(h->dzm, 0, sizeof(bf16) * (size_t)rows * 16, s);
-    mlp_scale_kernel<<<blocks_for(rows, 256), 256, 0, s>>>(h->dz, rows, scale);
-    mlp_backward_rows_kernel<<<blocks_for(rows, 64), 128, 0, s>>>(w, h->dz, rows, h->h1, h->h2, h->dh1, h->dh2,
-                                                                   h->dzm);
     const int blocks = (rows + MLP_RPB - 1) / MLP_RPB;
-    float* gW1 = h->grad;
-    float* gW2 = h->grad + MLP_H * MLP_IN;
-    float* gw3 = h->grad + MLP_H * MLP_IN + MLP_H * MLP_H;
-    mlp_wgrad_kernel<64, 64><<<blocks, 128, 0, s>>>(h->dh2, h->h1, rows, MLP_RPB, h->partial);  // dW2 = dh2^T h1
-    mlp_reduce_kernel<<<16, 256, 0, s>>>(h->partial, blocks, MLP_H * MLP_H, MLP_H * MLP_H, 1.f, gW2);
-    mlp_wgrad_kernel<64, 16><<<blocks, 128, 0, s>>>(h->dh1, X, rows, MLP_RPB, h->partial);      // dW1 = dh1^T x
-    mlp_reduce_kernel<<<4, 256, 0, s>>>(h->partial, blocks, MLP_H * MLP_IN, MLP_H * MLP_IN, 1.f, gW1);
-    mlp_wgrad_kernel<16, 64><<<blocks, 128, 0, s>>>(h->dzm, h->h2, rows, MLP_RPB, h->partial);  // dw3 = dz^T h2
-    mlp_reduce_kernel<<<1, 64, 0, s>>>(h->partial, blocks, 16 * MLP_H, MLP_H, 1.f, gw3);  // row 0 of dzm^T h2
+    mlp_backward_tc_kernel<<<blocks, 128, TCB_SMEM, s>>>(weights_of(h), X, h->dz, scale, rows, h->h1, h->h2,
+                                                         h->partial, h->status);
+    mlp_reduce_kernel<<<blocks_for(MLP_NW, 256), 256, 0, s>>>(h->partial, blocks, MLP_NW, MLP_NW, 1.f, h->grad);
     return mlp_launch_ok(h, "mlp backward");
 }
 

@@ -2,10 +2,11 @@
 // edge-scoring network: tensor-memory allocation, BF16 MMAs with FP32 accumulators in tensor
 // memory, their completion through an mbarrier, and the read-back of accumulator rows.
 //
-// Operands sit in shared memory in the canonical K-major layout without swizzle: a core matrix is
-// 8 rows x 16 bytes (8 BF16 of K), stored as 128 contiguous bytes; the core matrix of row group g
-// and K group c starts at byte g * SBO + c * LBO.  Every tile here uses LBO = 128 (K groups of one
-// row group adjacent) and SBO = 128 * (K groups per row).
+// Operands sit in shared memory in the canonical layouts without swizzle, in core matrices of 128
+// contiguous bytes.  K-major: a core matrix is 8 rows (of M or N) x 16 bytes (8 BF16 along K).
+// MN-major: 8 rows along K x 16 bytes (8 BF16 along M or N).  Either way the core matrix of M/N
+// group g and K group c starts at byte g * SBO + c * LBO; every tile here uses LBO = 128 (the K
+// groups of one M/N group adjacent) and SBO = 128 * (K groups in the tile).
 //
 // Accumulator layout for M = 128 with one CTA: row i of D in tensor-memory lane i, column j of D in
 // column (base + j).  Warp w of the CTA reads lanes 32w .. 32w + 31.
@@ -32,12 +33,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 }
 
 // Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9 and 10-12 =
-// 1), both K-major (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-template <int M, int N>
+// 1), A and B K-major (bits 15, 16 = 0) or MN-major (= 1), N >> 3 in bits 17-22, M >> 4 in bits
+// 24-28.
+template <int M, int N, bool A_MN = false, bool B_MN = false>
 struct IdescBf16 {
     static_assert(M == 128, "one-CTA tiles of 128 rows");
     static_assert(N % 16 == 0 && N >= 16 && N <= 256, "N for M = 128");
-    static constexpr uint32_t value = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+    static constexpr uint32_t value = (1u << 4) | (1u << 7) | (1u << 10) | ((A_MN ? 1u : 0u) << 15) |
+                                      ((B_MN ? 1u : 0u) << 16) | ((uint32_t)(N >> 3) << 17) |
                                       ((uint32_t)(M >> 4) << 24);
 };
 
