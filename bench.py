@@ -700,6 +700,7 @@ def run_schedule(args):
 
     torch.cuda.set_device(0)
     n, m, k, iters = 20_000, 512, 20, 100
+    seeds = (1, 2, 3)
     rows = []
     for s in seeds:
         xy = aco_synth.clustered(n, 100, 0.01, 20_000 + s)

@@ -41,3 +41,30 @@ def test_construct_byte_model():
     # the 200,000-city line: about 1e6 decisions, 6e4 exhausted steps with M about 1,000
     assert 0.9e9 < b.construct_bytes_model(10 ** 6, 6 * 10 ** 4, 6 * 10 ** 7, 16, 1024) < 1.1e9
     assert b.construct_bytes_layout(1, 16, 0) == 8 * 16 + 4 + 40
+
+
+def test_every_name_read_is_bound_somewhere():
+    """A coarse lint of the scripts that only run on a GPU machine: every name the module reads is
+    bound somewhere in it (an assignment, argument, import, function or class) or is a builtin, so
+    a workload cannot fail on a NameError there."""
+    import ast
+    import builtins
+    import pathlib
+
+    root = pathlib.Path(__file__).resolve().parent.parent
+    for rel in ("bench.py", "__graft_entry__.py"):
+        tree = ast.parse((root / rel).read_text())
+        bound = set(dir(builtins)) | {"__file__", "__name__"}
+        for node in ast.walk(tree):
+            if isinstance(node, (ast.FunctionDef, ast.AsyncFunctionDef, ast.ClassDef)):
+                bound.add(node.name)
+            elif isinstance(node, ast.arg):
+                bound.add(node.arg)
+            elif isinstance(node, (ast.Import, ast.ImportFrom)):
+                bound.update((a.asname or a.name).split(".")[0] for a in node.names)
+            elif isinstance(node, ast.Name) and isinstance(node.ctx, (ast.Store, ast.Del)):
+                bound.add(node.id)
+            elif isinstance(node, ast.ExceptHandler) and node.name:
+                bound.add(node.name)
+        used = {n.id for n in ast.walk(tree) if isinstance(n, ast.Name) and isinstance(n.ctx, ast.Load)}
+        assert not used - bound, (rel, sorted(used - bound))
