@@ -283,10 +283,11 @@ void aco_batch_destroy(aco_batch* b);
  * xy_dev: n*2 FP64 device coordinates; cand_out_dev: n*k int32 device output (row i = the k
  * nearest other cities of city i, key (d^2, index) ascending).  n <= 65536 (larger n returns
  * ACO_ERR_INVALID_ARG), 1 <= k <= min(32, n-1).  The first call on a device (and the first after
- * the device's context was reset) looks up the array's device address (make that call before any
- * stream capture).  All calls share the array and it keeps the last call's contents; calls that
- * overlap on the GPU race and must be serialised by the caller.  Synchronises the stream;
- * coincident or non-finite cities give ACO_ERR_INVALID_ARG. */
+ * the device's context was reset) looks up the array's device address.  All calls share the array
+ * and it keeps the last call's contents; calls that overlap on the GPU race and must be serialised
+ * by the caller.  Synchronises the stream, so it cannot be captured in a CUDA graph: on a stream
+ * that is capturing it returns ACO_ERR_INVALID_ARG and enqueues nothing.  Coincident or non-finite
+ * cities give ACO_ERR_INVALID_ARG. */
 aco_status aco_build_candidates_noalloc(const double* xy_dev, int32_t n, int32_t k, int32_t* cand_out_dev,
                                         void* stream);
 

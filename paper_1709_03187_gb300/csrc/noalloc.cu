@@ -104,6 +104,13 @@ extern "C" aco_status aco_build_candidates_noalloc(const double* xy_dev, int32_t
     if (n < 2 || n > ACO_NOALLOC_MAX_N) return ACO_ERR_INVALID_ARG;  // beyond the fixed scratch
     if (k < 1 || k > ACO_MAX_K || k > n - 1) return ACO_ERR_INVALID_ARG;
     if (knn_scratch_bytes(n) > ACO_NOALLOC_SCRATCH_BYTES) return ACO_ERR_INVALID_ARG;
+    // the call reads its error flag back and synchronises: it cannot be part of a captured graph
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return ACO_ERR_CUDA;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return ACO_ERR_INVALID_ARG;
     void* scratch = nullptr;
     int sms = 1, dev = 0;
     aco_status st = scratch_for_current_device(&scratch, &sms, &dev);

@@ -206,3 +206,21 @@ def test_bad_scores_are_rejected_and_leave_the_scores_in_use():
         ref.iterate(it)
     assert np.array_equal(col.state()[0].cpu().numpy(), ref.lbest)
     col.close()
+
+
+def test_forward_many_tiles_per_cta_and_ragged_tail():
+    """Enough rows that every CTA of the tensor-core forward loops over several 128-row tiles, and
+    a last tile of 77 rows: every row within the a-priori bound against the FP64 network."""
+    require_gpu()
+    from paper_1709_03187_gb300 import EdgeScorer
+
+    rows = 3 * 456 * 128 + 77
+    w = aco_synth.mlp_weights(33)
+    X = _features(rows, 12)
+    sc = EdgeScorer(w, max_rows=1 << 12)
+    z = sc.forward(_to_dev_bf16(X), z=True, score=False).cpu().numpy().astype(np.float64)
+    wo = _oracle_weights(w)
+    zo = mlp.forward(wo, X)[0]
+    bound = mlp.z_error_bound(wo, X)
+    assert np.all(np.abs(z - zo) <= 1.05 * bound + 1e-6), np.max(np.abs(z - zo) - bound)
+    sc.close()

@@ -71,3 +71,33 @@ def test_noalloc_rejects_what_its_array_cannot_hold():
     good = torch.empty((500, 8), dtype=torch.int32, device="cuda")
     aco_build_candidates_noalloc(torch.from_numpy(xy).cuda(), 500, 8, good)
     assert torch.equal(good, _regular(xy, 8))
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """The call synchronises and reads its error flag back, so it cannot be captured in a CUDA
+    graph: on a capturing stream it returns ACO_ERR_INVALID_ARG, enqueues nothing and leaves the
+    capture intact; afterwards the stream takes it normally."""
+    require_gpu()
+    from paper_1709_03187_gb300 import AcoError, aco_build_candidates_noalloc
+
+    xy = aco_synth.uniform(500, 4)
+    dev = torch.from_numpy(xy).cuda()
+    out = torch.full((500, 8), -7, dtype=torch.int32, device="cuda")
+    side = torch.zeros(4, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    status = None
+    with torch.cuda.graph(g, stream=s):
+        side.add_(1.0)
+        try:
+            aco_build_candidates_noalloc(dev, 500, 8, out, stream=s)
+        except AcoError as e:
+            status = e.status
+    assert status == 1
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(side, torch.ones(4, device="cuda"))
+    assert bool((out == -7).all())  # nothing ran
+    aco_build_candidates_noalloc(dev, 500, 8, out, stream=s)
+    s.synchronize()
+    assert torch.equal(out, _regular(xy, 8))
