@@ -1171,8 +1171,6 @@ __device__ void hashed_exact(const LbestArgs& A, BoostSmem& sh, int lane, double
 __device__ int exhausted_choice(const LbestArgs& A, int a, int cur, double u, bool partial, bool staged,
                                 int& ucount, const uint32_t* bits, BoostSmem& sh, int lane, unsigned long long& nfast) {
     __syncwarp();  // the previous city's visited bit (set at the top of the step) is visible
-    const double qx = A.xy[2 * cur], qy = A.xy[2 * cur + 1];
-    const double tau0pow = powr(A.tau0, A.alpha);
     int choice = -1;
     bool decided = false;
     if (A.fallback == 0) {
@@ -1182,17 +1180,23 @@ __device__ int exhausted_choice(const LbestArgs& A, int a, int cur, double u, bo
         RankRow rr;
         const bool pre = A.initialized && (A.m & 7) == 0 && A.m <= 1024;
         if (pre) load_rank_row(A, cur, lane, rr);
+        bool hashed_tie = false;
         if (partial && A.ia >= 0 && A.ib >= 0 && pre && staged) {
             const int fast = partial_choice_hashed(A, a, cur, bits, ucount, sh, lane, rr, nfast);
             if (fast >= 0) return fast;
-            if (fast == -1) {  // near tie: exact weights of the near-nearest and of the hashed cities
-                remaining_argmax(A, a, cur, bits, ucount, lane, qx, qy, tau0pow, bw, bc);
-                hashed_exact(A, sh, lane, qx, qy, tau0pow, bw, bc);
-                decided = true;
-            }
+            hashed_tie = fast == -1;
         } else if (partial && A.ia >= 0 && A.ib >= 0) {
             const int fast = partial_choice_fast(A, a, cur, bits, ucount, sh, lane, pre ? &rr : nullptr, nfast);
             if (fast >= 0) return fast;
+        }
+        // the FP64 paths (the FP32 screens above settle almost every step without them, so the
+        // coordinates and the FP64 power are taken only here)
+        const double qx = A.xy[2 * cur], qy = A.xy[2 * cur + 1];
+        const double tau0pow = powr(A.tau0, A.alpha);
+        if (hashed_tie) {  // near tie: exact weights of the near-nearest and of the hashed cities
+            remaining_argmax(A, a, cur, bits, ucount, lane, qx, qy, tau0pow, bw, bc);
+            hashed_exact(A, sh, lane, qx, qy, tau0pow, bw, bc);
+            decided = true;
         }
         if (!decided) {
             if (partial) remaining_argmax(A, a, cur, bits, ucount, lane, qx, qy, tau0pow, bw, bc);
@@ -1208,7 +1212,8 @@ __device__ int exhausted_choice(const LbestArgs& A, int a, int cur, double u, bo
         choice = bc;
         if (bw < 0.0) choice = -1;
     } else {
-        choice = wheel_all_unvisited(A, a, cur, u, bits, lane, qx, qy, tau0pow);
+        const double qx = A.xy[2 * cur], qy = A.xy[2 * cur + 1];
+        choice = wheel_all_unvisited(A, a, cur, u, bits, lane, qx, qy, powr(A.tau0, A.alpha));
     }
     if (choice < 0 || choice >= A.n) {
         if (lane == 0) atomicOr(A.errflag, DEVERR_NO_CHOICE);
