@@ -1120,10 +1120,11 @@ __device__ int partial_choice_hashed(const LbestArgs& A, int a, int cur, const u
             unsigned hs = bhash_slot(x8[h]);
             bool done = false;
             for (int pr = 0; pr < BHASH && !done; ++pr) {
-                const int old = atomicCAS(&sh.hkey[hs], -1, x8[h]);
+                // a slot that already holds the city takes a plain add; an empty one is claimed
+                int old = *reinterpret_cast<volatile int*>(&sh.hkey[hs]);
+                if (old == -1) old = atomicCAS(&sh.hkey[hs], -1, x8[h]);
                 if (old == -1 || old == x8[h]) {
                     atomicAdd(&sh.hq[hs], q8[h]);
-                    if (old == -1 && atomicAdd(&sh.hcount, 1) >= BHASH_MAX) over = true;
                     done = true;
                 }
                 hs = (hs + 1) & (BHASH - 1);
@@ -1132,15 +1133,18 @@ __device__ int partial_choice_hashed(const LbestArgs& A, int a, int cur, const u
         }
     }
     __syncwarp();
-    const bool overflow = __any_sync(FULL, over);
-    // 2. coordinates of the hashed cities (four slots per lane) requested before the scan
+    // 2. coordinates of the hashed cities (four slots per lane) requested before the scan; the
+    //    number of distinct cities decides the overflow
     int hx[BHASH / 32];
     float2 hp[BHASH / 32];
+    int distinct = 0;
 #pragma unroll
     for (int s4 = 0; s4 < BHASH / 32; ++s4) {
         hx[s4] = sh.hkey[lane + 32 * s4];
         hp[s4] = hx[s4] >= 0 ? A.xy32[hx[s4]] : make_float2(0.f, 0.f);
+        distinct += __popc(__ballot_sync(FULL, hx[s4] >= 0));
     }
+    const bool overflow = __any_sync(FULL, over) || distinct > BHASH_MAX;
     if (overflow) {
         bhash_clear(sh, lane);
         return -2;
