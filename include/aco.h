@@ -330,7 +330,8 @@ aco_status aco_mlp_create(const float* w_host, int64_t max_rows, void* stream, a
  * gradient blocks were written NaN). */
 aco_status aco_mlp_get_weights(aco_mlp* h, float* w_host);
 /* z_dev and/or score_dev = exp(beta z) (rows floats each; either may be NULL, not both) for rows of
- * BF16 features X_dev (rows * 16 BF16 bit patterns, 4-byte aligned).  No row limit.  On the tcgen05
+ * BF16 features X_dev (rows * 16 BF16 bit patterns).  Every pointer 4-byte aligned (else
+ * ACO_ERR_INVALID_ARG), as for aco_mlp_backward and aco_mlp_train.  No row limit.  On the tcgen05
  * tensor cores: 128-row tiles, accumulators in tensor memory.  Enqueued. */
 aco_status aco_mlp_forward(aco_mlp* h, const uint16_t* X_dev, int64_t rows, float* z_dev, float* score_dev,
                            float beta);

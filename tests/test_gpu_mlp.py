@@ -224,3 +224,22 @@ def test_forward_many_tiles_per_cta_and_ragged_tail():
     bound = mlp.z_error_bound(wo, X)
     assert np.all(np.abs(z - zo) <= 1.05 * bound + 1e-6), np.max(np.abs(z - zo) - bound)
     sc.close()
+
+
+def test_misaligned_features_are_refused():
+    """The kernels read features in 4-byte words: a feature pointer at an odd BF16 offset is
+    refused with ACO_ERR_INVALID_ARG before anything is enqueued."""
+    require_gpu()
+    from paper_1709_03187_gb300 import AcoError, EdgeScorer, _ffi
+
+    w = aco_synth.mlp_weights(3)
+    sc = EdgeScorer(w, max_rows=64)
+    flat = _to_dev_bf16(_features(33, 2)).reshape(-1)
+    odd = flat[1:1 + 32 * IN]  # starts 2 bytes into the buffer
+    z = torch.empty(32, dtype=torch.float32, device="cuda")
+    with pytest.raises(AcoError) as e:
+        _ffi.aco_mlp_forward(sc._h, odd, 32, z, None, 1.0)
+    assert e.value.status == 1
+    zz = sc.forward(flat[: 32 * IN].reshape(32, IN), z=True)  # the aligned view still works
+    assert bool(torch.isfinite(zz).all())
+    sc.close()
