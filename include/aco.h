@@ -12,6 +12,9 @@
  * Conventions (every entry point):
  *  - Pointers named *_dev are CUDA device pointers on the instance's device; *_host are host
  *    pointers.  The caller owns every buffer it passes; the library copies what it keeps.
+ *  - A device buffer is aligned to its element type (4 bytes for int32, float and BF16 pairs, 8
+ *    for FP64; the feature matrix of aco_edge_features 16); a misaligned one gives
+ *    ACO_ERR_INVALID_ARG before anything is enqueued.
  *  - All work is enqueued on the instance's stream.  Only the calls documented as
  *    synchronising wait for the device.
  *  - All device memory is allocated by aco_create_instance; no later call allocates.
@@ -330,8 +333,7 @@ aco_status aco_mlp_create(const float* w_host, int64_t max_rows, void* stream, a
  * gradient blocks were written NaN). */
 aco_status aco_mlp_get_weights(aco_mlp* h, float* w_host);
 /* z_dev and/or score_dev = exp(beta z) (rows floats each; either may be NULL, not both) for rows of
- * BF16 features X_dev (rows * 16 BF16 bit patterns).  Every pointer 4-byte aligned (else
- * ACO_ERR_INVALID_ARG), as for aco_mlp_backward and aco_mlp_train.  No row limit.  On the tcgen05
+ * BF16 features X_dev (rows * 16 BF16 bit patterns).  No row limit.  On the tcgen05
  * tensor cores: 128-row tiles, accumulators in tensor memory.  Enqueued. */
 aco_status aco_mlp_forward(aco_mlp* h, const uint16_t* X_dev, int64_t rows, float* z_dev, float* score_dev,
                            float beta);

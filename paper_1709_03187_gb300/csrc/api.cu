@@ -184,6 +184,10 @@ extern "C" aco_status aco_create_instance(const double* xy_dev, const aco_params
         return ACO_ERR_INVALID_ARG;
     }
     *out = nullptr;
+    if (aco_misaligned(xy_dev, 8)) {
+        snprintf(g_create_err, sizeof(g_create_err), "xy_dev not 8-byte aligned");
+        return ACO_ERR_INVALID_ARG;
+    }
     if (!params_ok(p, g_create_err, sizeof(g_create_err))) return ACO_ERR_INVALID_ARG;
     {
         aco_instance probe;
@@ -330,6 +334,7 @@ aco_status sync_and_check(aco_instance* inst, const char* what) {
 extern "C" aco_status aco_build_candidates(aco_instance* inst, int32_t* cand_out_dev) {
     ACO_RANGE("aco_build_candidates");
     if (!inst) return ACO_ERR_INVALID_ARG;
+    if (aco_misaligned(cand_out_dev, 4)) return set_err(inst, ACO_ERR_INVALID_ARG, "cand_out_dev not 4-byte aligned");
     aco_status st = launch_build_grid_and_knn(inst);
     if (st != ACO_OK) return st;
     if (inst->p.mode == ACO_MODE_LBEST_PARTIAL) {
@@ -359,6 +364,8 @@ extern "C" aco_status aco_construct_tours(aco_instance* inst, int32_t iteration,
     if (!inst) return ACO_ERR_INVALID_ARG;
     if (!inst->cand_built) return set_err(inst, ACO_ERR_STATE, "construct_tours before build_candidates");
     if (iteration < 0) return set_err(inst, ACO_ERR_INVALID_ARG, "iteration must be >= 0");
+    if (aco_misaligned(tours_out_dev, 4) || aco_misaligned(len_out_dev, 8))
+        return set_err(inst, ACO_ERR_INVALID_ARG, "construct_tours: output not aligned to its element type");
     aco_status st = inst->p.mode == ACO_MODE_LBEST_PARTIAL ? launch_construct_lbest(inst, iteration)
                                                            : launch_construct_dense(inst, iteration);
     if (st != ACO_OK) return st;
@@ -390,6 +397,8 @@ extern "C" aco_status aco_update_pheromone(aco_instance* inst) {
 extern "C" aco_status aco_tour_lengths(aco_instance* inst, const int32_t* tours_dev, int32_t count, double* out_dev) {
     ACO_RANGE("aco_tour_lengths");
     if (!inst || count < 0 || (count > 0 && (!tours_dev || !out_dev))) return ACO_ERR_INVALID_ARG;
+    if (aco_misaligned(tours_dev, 4) || aco_misaligned(out_dev, 8))
+        return set_err(inst, ACO_ERR_INVALID_ARG, "tour_lengths: buffer not aligned to its element type");
     if (count == 0) return ACO_OK;
     return launch_tour_lengths(inst, tours_dev, count, out_dev);
 }
@@ -398,6 +407,8 @@ extern "C" aco_status aco_get_state(aco_instance* inst, int32_t* lbest_out_dev, 
                                     double* tau_out_dev) {
     ACO_RANGE("aco_get_state");
     if (!inst) return ACO_ERR_INVALID_ARG;
+    if (aco_misaligned(lbest_out_dev, 4) || aco_misaligned(clen_out_dev, 8) || aco_misaligned(tau_out_dev, 8))
+        return set_err(inst, ACO_ERR_INVALID_ARG, "get_state: output not aligned to its element type");
     const size_t n = inst->p.n, m = inst->p.m;
     cudaStream_t s = inst->stream;
     if (inst->p.mode == ACO_MODE_LBEST_PARTIAL) {
@@ -444,6 +455,8 @@ extern "C" aco_status aco_set_async_share(aco_instance* inst, int32_t on) {
 extern "C" aco_status aco_set_state(aco_instance* inst, const int32_t* lbest_dev, const double* tau_dev) {
     ACO_RANGE("aco_set_state");
     if (!inst) return ACO_ERR_INVALID_ARG;
+    if (aco_misaligned(lbest_dev, 4) || aco_misaligned(tau_dev, 8))
+        return set_err(inst, ACO_ERR_INVALID_ARG, "set_state: input not aligned to its element type");
     if (!inst->cand_built) return set_err(inst, ACO_ERR_STATE, "set_state before build_candidates");
     if (inst->p.mode == ACO_MODE_LBEST_PARTIAL) {
         if (!lbest_dev) return set_err(inst, ACO_ERR_INVALID_ARG, "lbest_dev is required");
@@ -496,6 +509,8 @@ extern "C" aco_status aco_get_stats(aco_instance* inst, aco_stats* out_host) {
 extern "C" aco_status aco_step_probs(aco_instance* inst, int32_t city, const uint32_t* visited_bits_dev,
                                      float* probs_out_dev, int32_t* exhausted_out_dev) {
     if (!inst || !visited_bits_dev || !probs_out_dev || !exhausted_out_dev) return ACO_ERR_INVALID_ARG;
+    if (aco_misaligned(visited_bits_dev, 4) || aco_misaligned(probs_out_dev, 4) || aco_misaligned(exhausted_out_dev, 4))
+        return set_err(inst, ACO_ERR_INVALID_ARG, "step_probs: buffer not 4-byte aligned");
     if (city < 0 || city >= inst->p.n) return set_err(inst, ACO_ERR_INVALID_ARG, "city out of range");
     if (!inst->cand_built) return set_err(inst, ACO_ERR_STATE, "step_probs before build_candidates");
     return launch_step_probs(inst, city, visited_bits_dev, probs_out_dev, exhausted_out_dev);

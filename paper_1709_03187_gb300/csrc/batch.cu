@@ -100,6 +100,7 @@ extern "C" aco_status aco_batch_create(const double* xy_dev, const int32_t* n_ho
     ACO_RANGE("aco_batch_create");
     if (!xy_dev || !n_host || !p || !out || count < 1) return ACO_ERR_INVALID_ARG;
     *out = nullptr;
+    if (aco_misaligned(xy_dev, 8)) return ACO_ERR_INVALID_ARG;
     if (p->mode != ACO_MODE_LBEST_PARTIAL) return ACO_ERR_INVALID_ARG;
     aco_batch* b = new (std::nothrow) aco_batch();
     if (!b) return ACO_ERR_OOM;
@@ -372,7 +373,7 @@ extern "C" aco_status aco_batch_run(aco_batch* b, int32_t first_iteration, int32
 
 extern "C" aco_status aco_batch_get_state(aco_batch* b, int32_t* lbest_out_dev, double* clen_out_dev) {
     ACO_RANGE("aco_batch_get_state");
-    if (!b) return ACO_ERR_INVALID_ARG;
+    if (!b || aco_misaligned(lbest_out_dev, 4) || aco_misaligned(clen_out_dev, 8)) return ACO_ERR_INVALID_ARG;
     aco_status st = check_status(b);
     if (st != ACO_OK) return st;
     for (int i = 0; i < b->count; ++i) {

@@ -373,6 +373,9 @@ struct aco_instance {
 };
 
 // ------------------------------------------------------------------ host helpers
+// A caller's buffer is read and written by kernels in units of its element type (or wider):
+// true when a non-null pointer is not aligned to `to` bytes.
+static inline bool aco_misaligned(const void* p, uintptr_t to) { return p && ((uintptr_t)p & (to - 1)) != 0; }
 aco_status set_err(aco_instance* inst, aco_status s, const char* fmt, ...);
 aco_status check_launch(aco_instance* inst, const char* what);
 aco_status sync_and_check(aco_instance* inst, const char* what);

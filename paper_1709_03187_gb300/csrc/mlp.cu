@@ -619,9 +619,6 @@ static aco_status mlp_launch_ok(aco_mlp* h, const char* what) {
 
 extern "C" const char* aco_mlp_last_error(const aco_mlp* h) { return h ? h->err : ""; }
 
-// The kernels read features and targets in 4-byte words (a feature row is 16 BF16 values).
-static bool misaligned(const void* p, uintptr_t to) { return p && ((uintptr_t)p & (to - 1)) != 0; }
-
 // Launch shapes of the tensor-core kernels: their shared memory admits so few CTAs per SM that the
 // CTAs' tensor-memory allocations (512 columns per SM) always fit and tcgen05.alloc never waits;
 // refused otherwise.  Returns the forward's grid in h->tc_grid.
@@ -749,7 +746,7 @@ extern "C" aco_status aco_mlp_forward(aco_mlp* h, const uint16_t* X_dev, int64_t
                                       float* score_dev, float beta) {
     ACO_RANGE("aco_mlp_forward");
     if (!h || !X_dev || rows < 0 || (!z_dev && !score_dev) || !isfinite(beta)) return ACO_ERR_INVALID_ARG;
-    if (misaligned(X_dev, 4) || misaligned(z_dev, 4) || misaligned(score_dev, 4)) return ACO_ERR_INVALID_ARG;
+    if (aco_misaligned(X_dev, 4) || aco_misaligned(z_dev, 4) || aco_misaligned(score_dev, 4)) return ACO_ERR_INVALID_ARG;
     if (rows == 0) return ACO_OK;
     launch_forward(h, (const bf16*)X_dev, rows, z_dev, score_dev, beta, nullptr, nullptr);
     return mlp_launch_ok(h, "mlp_forward_tc_kernel");
@@ -775,7 +772,7 @@ extern "C" aco_status aco_mlp_backward(aco_mlp* h, const uint16_t* X_dev, const 
                                        int32_t k, float scale, float* grad_dev, float* loss_dev) {
     ACO_RANGE("aco_mlp_backward");
     if (!h || !X_dev || !target_dev || cities < 1 || k < 1 || k > 32 || !isfinite(scale)) return ACO_ERR_INVALID_ARG;
-    if (misaligned(X_dev, 4) || misaligned(target_dev, 4) || misaligned(grad_dev, 4) || misaligned(loss_dev, 4))
+    if (aco_misaligned(X_dev, 4) || aco_misaligned(target_dev, 4) || aco_misaligned(grad_dev, 4) || aco_misaligned(loss_dev, 4))
         return ACO_ERR_INVALID_ARG;
     if ((long long)cities * k > h->max_rows) return ACO_ERR_INVALID_ARG;
     aco_status st = mlp_backward(h, (const bf16*)X_dev, target_dev, cities, k, scale, loss_dev);
@@ -805,7 +802,7 @@ extern "C" aco_status aco_mlp_train(aco_mlp* h, const uint16_t* X_dev, const uin
     if (!h || !X_dev || !target_dev || cities < 1 || k < 1 || k > 32 || batch_cities < 1 || steps < 0 ||
         !(lr >= 0.f) || !isfinite(lr))
         return ACO_ERR_INVALID_ARG;
-    if (misaligned(X_dev, 4) || misaligned(target_dev, 4) || misaligned(loss_dev, 4)) return ACO_ERR_INVALID_ARG;
+    if (aco_misaligned(X_dev, 4) || aco_misaligned(target_dev, 4) || aco_misaligned(loss_dev, 4)) return ACO_ERR_INVALID_ARG;
     if ((long long)batch_cities * k > h->max_rows) return ACO_ERR_INVALID_ARG;
     const bf16* X = (const bf16*)X_dev;
     const int nb = (cities + batch_cities - 1) / batch_cities;
@@ -826,6 +823,8 @@ extern "C" aco_status aco_mlp_train(aco_mlp* h, const uint16_t* X_dev, const uin
 extern "C" aco_status aco_edge_features(aco_instance* inst, int32_t degree_ants, uint16_t* X_dev) {
     ACO_RANGE("aco_edge_features");
     if (!inst || !X_dev) return ACO_ERR_INVALID_ARG;
+    // a feature row (16 BF16 values) is written as two 16-byte words
+    if (aco_misaligned(X_dev, 16)) return set_err(inst, ACO_ERR_INVALID_ARG, "edge_features: X_dev not 16-byte aligned");
     if (inst->p.mode != ACO_MODE_LBEST_PARTIAL || !inst->cand_built || !inst->initialized)
         return set_err(inst, ACO_ERR_STATE, "edge_features: needs candidate lists and l_best tours");
     if (degree_ants < 1 || degree_ants > 16 || degree_ants > inst->p.m)
@@ -839,6 +838,7 @@ extern "C" aco_status aco_edge_features(aco_instance* inst, int32_t degree_ants,
 extern "C" aco_status aco_tour_labels(aco_instance* inst, uint32_t* target_dev) {
     ACO_RANGE("aco_tour_labels");
     if (!inst || !target_dev) return ACO_ERR_INVALID_ARG;
+    if (aco_misaligned(target_dev, 4)) return set_err(inst, ACO_ERR_INVALID_ARG, "tour_labels: target_dev not 4-byte aligned");
     if (inst->p.mode != ACO_MODE_LBEST_PARTIAL || !inst->initialized)
         return set_err(inst, ACO_ERR_STATE, "tour_labels: needs l_best tours");
     if (inst->p.k > 32) return set_err(inst, ACO_ERR_INVALID_ARG, "tour_labels: k > 32");
@@ -850,6 +850,7 @@ extern "C" aco_status aco_tour_labels(aco_instance* inst, uint32_t* target_dev) 
 extern "C" aco_status aco_set_edge_scores(aco_instance* inst, const float* score_dev) {
     ACO_RANGE("aco_set_edge_scores");
     if (!inst) return ACO_ERR_INVALID_ARG;
+    if (aco_misaligned(score_dev, 4)) return set_err(inst, ACO_ERR_INVALID_ARG, "set_edge_scores: score_dev not 4-byte aligned");
     if (inst->p.mode != ACO_MODE_LBEST_PARTIAL || !inst->cand_built)
         return set_err(inst, ACO_ERR_STATE, "set_edge_scores: needs candidate lists");
     if (inst->constructed) return set_err(inst, ACO_ERR_STATE, "set_edge_scores: tours constructed, update pending");

@@ -101,6 +101,7 @@ extern "C" aco_status aco_build_candidates_noalloc(const double* xy_dev, int32_t
                                                    void* stream) {
     ACO_RANGE("aco_build_candidates_noalloc");
     if (!xy_dev || !cand_out_dev) return ACO_ERR_INVALID_ARG;
+    if (aco_misaligned(xy_dev, 8) || aco_misaligned(cand_out_dev, 4)) return ACO_ERR_INVALID_ARG;
     if (n < 2 || n > ACO_NOALLOC_MAX_N) return ACO_ERR_INVALID_ARG;  // beyond the fixed scratch
     if (k < 1 || k > ACO_MAX_K || k > n - 1) return ACO_ERR_INVALID_ARG;
     if (knn_scratch_bytes(n) > ACO_NOALLOC_SCRATCH_BYTES) return ACO_ERR_INVALID_ARG;
