@@ -24,9 +24,11 @@
 
 #define FULL 0xffffffffu
 
-// One warp per ant.  Batched colonies: block b is ant slot b, naming (instance, ant).
-template <bool BATCH>
-__global__ void __launch_bounds__(32) commit_kernel(const __grid_constant__ CommitArgs Cp,
+// One block of NT threads per ant (a warp for the batched colonies, where block b is ant slot b,
+// naming (instance, ant); a wider block for a single colony, so that the longest rebuilt segment
+// is spread over more threads).
+template <bool BATCH, int NT>
+__global__ void __launch_bounds__(NT) commit_kernel(const __grid_constant__ CommitArgs Cp,
                                                     const CommitArgs* __restrict__ batch, const int2* __restrict__ slot,
                                                     int slots) {
     int a = blockIdx.x, inst = 0;
@@ -37,7 +39,7 @@ __global__ void __launch_bounds__(32) commit_kernel(const __grid_constant__ Comm
         a = sa.y;
     }
     const CommitArgs& C = BATCH ? batch[inst] : Cp;
-    commit_ant(C, a, threadIdx.x);
+    commit_ant<NT>(C, a, threadIdx.x);
 }
 
 // One block per colony: C_gbest, its ant, and the per-ant deposit weights.  keep_prev: fold in
@@ -259,7 +261,7 @@ cudaError_t launch_update_batch(const CommitArgs* cargs, const int2* slot, int s
                                 int count, const RebuildArgs* rargs, const int4* blockmap, int rblocks, int m_cap,
                                 int k, cudaStream_t s) {
     CommitArgs c0{};
-    commit_kernel<true><<<slots, 32, 0, s>>>(c0, cargs, slot, slots);
+    commit_kernel<true, 32><<<slots, 32, 0, s>>>(c0, cargs, slot, slots);
     GbestArgs g0{};
     gbest_q_kernel<true><<<count, 256, 0, s>>>(g0, gargs);
     RebuildArgs r0{};
@@ -289,7 +291,7 @@ aco_status launch_update_lbest(aco_instance* inst) {
     const aco_params& p = inst->p;
     CommitArgs C;
     fill_commit_args(inst, C);
-    commit_kernel<false><<<p.m, 32, 0, inst->stream>>>(C, nullptr, nullptr, 0);
+    commit_kernel<false, 256><<<p.m, 256, 0, inst->stream>>>(C, nullptr, nullptr, 0);
     aco_status st = check_launch(inst, "commit_kernel");
     if (st != ACO_OK) return st;
     GbestArgs G;

@@ -23,6 +23,15 @@ __device__ __forceinline__ void set_neighbours(int* __restrict__ nb, uint8_t* __
 // Algorithm 1's replacement for ant a (one warp): when the new tour is strictly shorter than the
 // ant's l_best it becomes the l_best: the rebuilt positions (or the whole tour), the neighbour
 // entries of the cities they touch, the length and its exact fixed-point value.
+// NT threads take the ant (a warp, or a whole block when NT > 32); thread `lane` of them.  Every
+// thread reads C_lbest before the first synchronisation and thread 0 writes it after the last.
+template <int NT>
+__device__ __forceinline__ void group_sync() {
+    if (NT == 32) __syncwarp();
+    else __syncthreads();
+}
+
+template <int NT = 32>
 __device__ __forceinline__ void commit_ant(const CommitArgs& C, int a, int lane) {
     const int n = C.n, m = C.m, k = C.k;
     const AntIter it = C.antit[a];
@@ -30,17 +39,17 @@ __device__ __forceinline__ void commit_ant(const CommitArgs& C, int a, int lane)
     int* L = C.lbest + (size_t)a * n;
     const int* S = C.seg + (size_t)a * n;
     if (it.s < 0) {
-        for (int t = lane; t < n; t += 32) L[t] = S[t];
-        __syncwarp();
-        for (int t = lane; t < n; t += 32)
+        for (int t = lane; t < n; t += NT) L[t] = S[t];
+        group_sync<NT>();
+        for (int t = lane; t < n; t += NT)
             set_neighbours(C.nb, C.nbrank, C.cand, m, k, a, S[t], S[t + 1 == n ? 0 : t + 1], S[t == 0 ? n - 1 : t - 1]);
     } else {
         const int e = L[(it.s + it.P - 1) % n];
         const int start = L[it.s];
         const int M = it.M;
-        __syncwarp();
-        for (int t = lane; t < M; t += 32) L[(it.s + it.P + t) % n] = S[t];
-        for (int t = lane; t < M; t += 32) {
+        group_sync<NT>();
+        for (int t = lane; t < M; t += NT) L[(it.s + it.P + t) % n] = S[t];
+        for (int t = lane; t < M; t += NT) {
             const int pc = t == 0 ? e : S[t - 1];
             const int sc = t == M - 1 ? start : S[t + 1];
             set_neighbours(C.nb, C.nbrank, C.cand, m, k, a, S[t], sc, pc);
