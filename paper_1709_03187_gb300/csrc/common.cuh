@@ -79,6 +79,14 @@ __device__ __forceinline__ double powr(double x, double e) {
     return pow(x, e);
 }
 
+// x^t for a small integer t: the same products as powr (its first factor 1.0 * x is x exactly).
+__device__ __forceinline__ double pow_int(double x, int t) {
+    if (t == 0) return 1.0;
+    double p = x;
+    for (int i = 1; i < t; ++i) p = __dmul_rn(p, x);
+    return p;
+}
+
 __device__ __forceinline__ double eta_pow_from_d2(double d2, double beta) {
     const double eta = __ddiv_rn(1.0, __dsqrt_rn(d2));
     return powr(eta, beta);
@@ -255,6 +263,7 @@ struct GbestArgs {
 struct RebuildArgs {
     int n, m, k;
     double tau0, alpha;
+    int ia;  // alpha as a small integer (0 .. 64), else -1
     int use_ants;
     int m_cap;  // shared-memory slots for per-ant weights (largest m of a batch)
     const uint8_t* nbrank;

@@ -234,6 +234,7 @@ void fill_gbest_args(const aco_instance* inst, int keep_prev, GbestArgs& G) {
 void fill_rebuild_args(const aco_instance* inst, int use_ants, RebuildArgs& R) {
     const aco_params& p = inst->p;
     R.n = p.n; R.m = p.m; R.k = p.k; R.tau0 = p.tau0; R.alpha = p.alpha; R.use_ants = use_ants; R.m_cap = p.m;
+    R.ia = (p.alpha >= 0.0 && p.alpha <= 64.0 && floor(p.alpha) == p.alpha) ? (int)p.alpha : -1;
     R.nbrank = inst->nbrank; R.q = inst->q; R.etab = inst->etab; R.candw = inst->candw; R.W64 = inst->W64;
     R.rowflag = inst->rowflag; R.errflag = inst->errflag;
     R.Qt = inst->Qt;

@@ -110,9 +110,11 @@ __device__ __forceinline__ void finish_row(const RebuildArgs& R, int i, unsigned
     if (lane < k) {
         const size_t e = (size_t)i * k + lane;
         const double tau = __dadd_rn(R.tau0, __dmul_rn(__ull2double_rn(Q), 0x1.0p-32));
-        const double wv = __dmul_rn(powr(tau, R.alpha), eta);
+        const double wv = __dmul_rn(R.ia >= 0 ? pow_int(tau, R.ia) : powr(tau, R.alpha), eta);
         w32 = __double2float_rn(wv);
-        if (!isfinite(wv)) atomicOr(R.errflag, DEVERR_NONFINITE);
+        // not finite: all exponent bits set (tested on the bit pattern, off the FP64 pipe)
+        if ((__double_as_longlong(wv) & 0x7ff0000000000000LL) == 0x7ff0000000000000LL)
+            atomicOr(R.errflag, DEVERR_NONFINITE);
         flag = !(w32 >= FLT_MIN && w32 <= FLT_MAX);
         R.W64[e] = wv;
         if (R.Qt) R.Qt[e] = Q;
