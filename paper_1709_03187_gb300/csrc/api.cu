@@ -51,7 +51,7 @@ static void free_all(aco_instance* inst) {
                     inst->tours, inst->succ_d, inst->pred_d, inst->counters, inst->errflag, inst->xy32,
                     inst->ulist, inst->uxy, inst->bel, inst->btx, inst->btq, inst->deg, inst->ghk, inst->ghq,
                     inst->ls_buf, inst->ls_sel, inst->ls_imp, inst->fcnt, inst->ccnt, inst->csize, inst->Qt,
-                    inst->rec_off, inst->nrec, inst->ext};
+                    inst->rec_off, inst->nrec, inst->ext, inst->far};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -162,6 +162,9 @@ static bool plan_buffers(aco_instance* inst, const aco_params* p, size_t* total,
         inst->kx = (int32_t)(n - 1 < ACO_KX ? n - 1 : ACO_KX);
         if (inst->kx > k) ok &= dalloc(&inst->ext, n * inst->kx, total, alloc);
         else inst->kx = 0;
+        // large colonies also keep the 128 nearest: the initial tours' exhausted steps find the
+        // nearest unvisited city there far more often than in the 32 nearest
+        if (inst->kx > k && n > ACO_FAR_MIN_N) ok &= dalloc(&inst->far, n * ACO_KF, total, alloc);
     } else {
         ok &= dalloc(&inst->tau, n * n, total, alloc);
         ok &= dalloc(&inst->etab_d, n * n, total, alloc);

@@ -30,6 +30,8 @@ enum : uint32_t { PURPOSE_WHEEL = 0, PURPOSE_START = 1, PURPOSE_KEEP = 2, PURPOS
 #define ACO_LS_MAX_ANTS 8     // ants improved by local search per iteration, at most
 #define ACO_LS_MAX_PASSES 16  // windowed 2-opt passes, at most
 #define ACO_KX 32             // extended neighbour list: the 32 nearest cities (candidates first)
+#define ACO_KF 128            // far list of large colonies: the 128 nearest cities (the extended list first)
+#define ACO_FAR_MIN_N 8192    // colonies with more cities keep the far list
 
 struct Draw4 { uint32_t x0, x1, x2, x3; };
 
@@ -366,6 +368,7 @@ struct aco_instance {
     int32_t* nrec;         // 1: imported records
     int32_t kx;            // extended list length min(ACO_KX, n - 1) (0 = no extended list)
     int32_t* ext;          // n*kx: the kx nearest other cities, key (d^2, index); its first k are the candidates
+    int32_t* far;          // n*ACO_KF when n > ACO_FAR_MIN_N: the ACO_KF nearest, key (d^2, index); ext is its prefix
 
     // dense mode
     double* tau;           // n*n

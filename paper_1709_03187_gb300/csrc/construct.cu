@@ -46,6 +46,7 @@ struct LbestArgs {
     int ant0;       // first ant of the launch (a rank's share of a sharded colony)
     int kx;         // extended list length (0 = none)
     const int* __restrict__ ext;                 // n*kx nearest cities (candidates first)
+    const int* __restrict__ far;                 // n*ACO_KF nearest cities, or null
     float coord_r;  // max |coordinate| (FP32 screen error bound)
     int ia, ib;     // alpha, beta as small integers (0..16) for the FP32 screen, else -1
     float tau0f, tau0powf;  // tau0 and tau0^alpha in FP32
@@ -801,16 +802,45 @@ __device__ int wheel_all_unvisited(const LbestArgs& A, int a, int cur, double u,
 // Full construction before any pheromone (initial tours, tau = tau0 everywhere): the nearest
 // unvisited city wins unless the runner-up lies within 2^-40 of it (a possible tie of the rounded
 // weights), compared exactly in FP64.
+static_assert(ACO_KF == 128, "the far list is read as four slots of 32 lanes");
+
 __device__ int ext_full_choice(const LbestArgs& A, int cur, const uint32_t* bits, int lane) {
     __syncwarp();  // the previous city's visited bit is visible
     const int kx = A.kx, k = A.k;
-    const int e = lane < kx ? __ldg(A.ext + (size_t)cur * kx + lane) : -1;
-    const unsigned um = __ballot_sync(FULL, lane >= k && lane < kx && !is_visited(bits, e));
-    const unsigned more = um & (um - 1u);
-    const int r1 = __ffs(um) - 1;
-    if (um == 0u || (!more && r1 == kx - 1)) return -1;
-    const int r2 = more ? __ffs(more) - 1 : kx - 1;
-    const int c1 = __shfl_sync(FULL, e, r1), c2 = __shfl_sync(FULL, e, r2);
+    int c1, c2;
+    if (A.far) {
+        // the 128 nearest, entry p in lane p % 32 of slot p / 32: the first two unvisited
+        // entries of rank >= k in list order (the last entry bounds every unlisted city)
+        int e[ACO_KF / 32], r1 = -1, r2 = -1;
+#pragma unroll
+        for (int s = 0; s < ACO_KF / 32; ++s) e[s] = __ldg(A.far + (size_t)cur * ACO_KF + 32 * s + lane);
+#pragma unroll
+        for (int s = 0; s < ACO_KF / 32; ++s) {
+            unsigned u = __ballot_sync(FULL, 32 * s + lane >= k && !is_visited(bits, e[s]));
+            while (u && r2 < 0) {
+                const int p = 32 * s + __ffs(u) - 1;
+                u &= u - 1u;
+                if (r1 < 0) r1 = p;
+                else r2 = p;
+            }
+        }
+        if (r1 < 0 || (r2 < 0 && r1 == ACO_KF - 1)) return -1;
+        if (r2 < 0) r2 = ACO_KF - 1;
+        const int s1 = r1 >> 5, s2 = r2 >> 5;
+        const int v1 = s1 == 0 ? e[0] : s1 == 1 ? e[1] : s1 == 2 ? e[2] : e[3];
+        const int v2 = s2 == 0 ? e[0] : s2 == 1 ? e[1] : s2 == 2 ? e[2] : e[3];
+        c1 = __shfl_sync(FULL, v1, r1 & 31);
+        c2 = __shfl_sync(FULL, v2, r2 & 31);
+    } else {
+        const int e = lane < kx ? __ldg(A.ext + (size_t)cur * kx + lane) : -1;
+        const unsigned um = __ballot_sync(FULL, lane >= k && lane < kx && !is_visited(bits, e));
+        const unsigned more = um & (um - 1u);
+        const int r1 = __ffs(um) - 1;
+        if (um == 0u || (!more && r1 == kx - 1)) return -1;
+        const int r2 = more ? __ffs(more) - 1 : kx - 1;
+        c1 = __shfl_sync(FULL, e, r1);
+        c2 = __shfl_sync(FULL, e, r2);
+    }
     const double qx = A.xy[2 * cur], qy = A.xy[2 * cur + 1];
     const double d1 = dist2(qx, qy, A.xy[2 * c1], A.xy[2 * c1 + 1]);
     const double d2 = dist2(qx, qy, A.xy[2 * c2], A.xy[2 * c2 + 1]);
@@ -1649,6 +1679,7 @@ void fill_lbest_args(const aco_instance* inst, int32_t iteration, LbestArgs& A) 
     A.ant0 = inst->ant0;
     A.kx = inst->ext ? inst->kx : 0;
     A.ext = inst->ext;
+    A.far = inst->far;
     const bool ia_ok = p.alpha >= 0 && p.alpha <= 16 && floor(p.alpha) == p.alpha;
     const bool ib_ok = p.beta >= 0 && p.beta <= 16 && floor(p.beta) == p.beta;
     A.ia = ia_ok ? (int)p.alpha : -1;

@@ -81,7 +81,9 @@ __device__ __forceinline__ int ring_cell(const GridDesc& g, int cx, int cy, int 
     return y * g.gx + x;
 }
 
-__device__ __forceinline__ bool key_less(double da, int ja, double db, int jb) {
+// (d^2, index) order on the bit patterns of non-negative FP64 squared distances (the same order
+// as the values), so that the comparisons run on the integer units.
+__device__ __forceinline__ bool key_less_u(unsigned long long da, int ja, unsigned long long db, int jb) {
     return da < db || (da == db && ja < jb);
 }
 
@@ -100,9 +102,11 @@ __global__ void __launch_bounds__(256) knn_kernel(const double* __restrict__ xy,
         const double qx = xy[2 * i], qy = xy[2 * i + 1];
         const int cell = city_cell[i];
         const int cx = cell % g.gx, cy = cell / g.gx;
-        double ld = DBL_MAX;  // this lane's list entry (lanes < k), sorted ascending
+        // this lane's list entry (lanes < k), sorted ascending; keys are the bit patterns of the
+        // non-negative FP64 squared distances (the same order), compared on the integer units
+        unsigned long long ld = ~0ull;
         int lj = 0x7fffffff;
-        double kd = DBL_MAX;
+        unsigned long long kd = ~0ull;
         int kj = 0x7fffffff;
         for (int r = 0;; ++r) {
             const int ncell = r == 0 ? 1 : 8 * r;
@@ -113,25 +117,26 @@ __global__ void __launch_bounds__(256) knn_kernel(const double* __restrict__ xy,
                     if (c >= 0) { pb = cell_start[c]; pe = cell_start[c + 1]; }
                 }
                 while (__any_sync(FULL, pb < pe)) {
-                    double d2 = DBL_MAX;
+                    unsigned long long d2 = ~0ull;
                     int j = 0x7fffffff;
                     bool cand_ok = false;
                     if (pb < pe) {
                         j = cell_city[pb];
-                        d2 = dist2(qx, qy, cell_xy[2 * pb], cell_xy[2 * pb + 1]);
-                        cand_ok = (j != i) && key_less(d2, j, kd, kj);
+                        d2 = (unsigned long long)__double_as_longlong(
+                            dist2(qx, qy, cell_xy[2 * pb], cell_xy[2 * pb + 1]));
+                        cand_ok = (j != i) && key_less_u(d2, j, kd, kj);
                         ++pb;
                     }
                     unsigned pend = __ballot_sync(FULL, cand_ok);
                     while (pend) {
                         const int src = __ffs(pend) - 1;
                         pend &= pend - 1;
-                        const double cd = __shfl_sync(FULL, d2, src);
+                        const unsigned long long cd = __shfl_sync(FULL, d2, src);
                         const int cj = __shfl_sync(FULL, j, src);
-                        if (key_less(cd, cj, kd, kj)) {
-                            const bool before = lane < k && key_less(ld, lj, cd, cj);
+                        if (key_less_u(cd, cj, kd, kj)) {
+                            const bool before = lane < k && key_less_u(ld, lj, cd, cj);
                             const int pos = __popc(__ballot_sync(FULL, before));
-                            const double ud = __shfl_up_sync(FULL, ld, 1);
+                            const unsigned long long ud = __shfl_up_sync(FULL, ld, 1);
                             const int uj = __shfl_up_sync(FULL, lj, 1);
                             if (lane == pos) { ld = cd; lj = cj; }
                             else if (lane > pos) { ld = ud; lj = uj; }
@@ -142,15 +147,17 @@ __global__ void __launch_bounds__(256) knn_kernel(const double* __restrict__ xy,
                 }
             }
             const double lb = ring_lower_bound(g, qx, qy, cx, cy, r);
-            if (lb < 0.0) break;                       // every cell scanned
-            if (kd < __dmul_rn(lb, lb)) break;        // nothing unscanned can enter the list
+            if (lb < 0.0) break;  // every cell scanned
+            // nothing unscanned can enter the list
+            if (kd != ~0ull && __longlong_as_double((long long)kd) < __dmul_rn(lb, lb)) break;
         }
         if (lane < k) {
+            const double ldd = __longlong_as_double((long long)ld);
             cand[(size_t)i * k + lane] = lj;
-            if (ld == 0.0) atomicOr(errflag, DEVERR_DUPLICATE);
+            if (ldd == 0.0) atomicOr(errflag, DEVERR_DUPLICATE);
             if (!LISTS_ONLY) {
                 candw[(size_t)i * k + lane].city = lj;
-                const double e = eta_pow_from_d2(ld, beta);
+                const double e = eta_pow_from_d2(ldd, beta);
                 if (!isfinite(e)) atomicOr(errflag, DEVERR_NONFINITE);
                 etab[(size_t)i * k + lane] = e;
             }
@@ -159,6 +166,113 @@ __global__ void __launch_bounds__(256) knn_kernel(const double* __restrict__ xy,
 }
 
 // Dense mode: eta^beta for every ordered pair and tau = tau0.
+// The ACO_KF nearest other cities of every city, key (d^2, index) ascending, one warp per query
+// city, by the same ring scan as knn_kernel; the sorted list is spread over the lanes, entry p in
+// lane p % 32 of slot p / 32, and an entry that enters it shifts the later ones up by one.
+__global__ void __launch_bounds__(256) knn_far_kernel(const double* __restrict__ xy, const GridDesc* __restrict__ gd,
+                                                      const int* __restrict__ city_cell,
+                                                      const int* __restrict__ cell_start,
+                                                      const int* __restrict__ cell_city,
+                                                      const double* __restrict__ cell_xy, int n,
+                                                      int* __restrict__ far) {
+    constexpr int S = ACO_KF / 32;
+    const GridDesc g = *gd;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nwarps) {
+        const double qx = xy[2 * i], qy = xy[2 * i + 1];
+        const int cell = city_cell[i];
+        const int cx = cell % g.gx, cy = cell / g.gx;
+        // keys are the bit patterns of the non-negative FP64 squared distances, which order as
+        // the values do, so the comparisons run on the integer units
+        unsigned long long ld[S];
+        int lj[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            ld[s] = ~0ull;
+            lj[s] = 0x7fffffff;
+        }
+        unsigned long long kd = ~0ull;  // the last entry of the list
+        int kj = 0x7fffffff;
+        for (int r = 0;; ++r) {
+            const int ncell = r == 0 ? 1 : 8 * r;
+            for (int c0 = 0; c0 < ncell; c0 += 32) {
+                int pb = 0, pe = 0;
+                if (c0 + lane < ncell) {
+                    const int c = ring_cell(g, cx, cy, r, c0 + lane);
+                    if (c >= 0) { pb = cell_start[c]; pe = cell_start[c + 1]; }
+                }
+                while (__any_sync(FULL, pb < pe)) {
+                    unsigned long long d2 = ~0ull;
+                    int j = 0x7fffffff;
+                    bool cand_ok = false;
+                    if (pb < pe) {
+                        j = cell_city[pb];
+                        d2 = (unsigned long long)__double_as_longlong(
+                            dist2(qx, qy, cell_xy[2 * pb], cell_xy[2 * pb + 1]));
+                        cand_ok = (j != i) && key_less_u(d2, j, kd, kj);
+                        ++pb;
+                    }
+                    unsigned pend = __ballot_sync(FULL, cand_ok);
+                    while (pend) {
+                        const int src = __ffs(pend) - 1;
+                        pend &= pend - 1;
+                        const unsigned long long cd = __shfl_sync(FULL, d2, src);
+                        const int cj = __shfl_sync(FULL, j, src);
+                        if (!key_less_u(cd, cj, kd, kj)) continue;
+                        int pos = 0;
+#pragma unroll
+                        for (int s = 0; s < S; ++s)
+                            pos += __popc(__ballot_sync(FULL, key_less_u(ld[s], lj[s], cd, cj)));
+                        // the entry before each position, read before any entry moves
+                        unsigned long long ud[S];
+                        int uj[S];
+#pragma unroll
+                        for (int s = 0; s < S; ++s) {
+                            ud[s] = __shfl_up_sync(FULL, ld[s], 1);
+                            uj[s] = __shfl_up_sync(FULL, lj[s], 1);
+                            if (s > 0) {
+                                const unsigned long long pd = __shfl_sync(FULL, ld[s - 1], 31);
+                                const int pj = __shfl_sync(FULL, lj[s - 1], 31);
+                                if (lane == 0) {
+                                    ud[s] = pd;
+                                    uj[s] = pj;
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int s = 0; s < S; ++s) {
+                            const int p = 32 * s + lane;
+                            if (p == pos) {
+                                ld[s] = cd;
+                                lj[s] = cj;
+                            } else if (p > pos) {
+                                ld[s] = ud[s];
+                                lj[s] = uj[s];
+                            }
+                        }
+                        kd = __shfl_sync(FULL, ld[S - 1], 31);
+                        kj = __shfl_sync(FULL, lj[S - 1], 31);
+                    }
+                }
+            }
+            const double lb = ring_lower_bound(g, qx, qy, cx, cy, r);
+            if (lb < 0.0) break;  // every cell scanned
+            // nothing unscanned can enter the list
+            if (kd != ~0ull && __longlong_as_double((long long)kd) < __dmul_rn(lb, lb)) break;
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) far[(size_t)i * ACO_KF + 32 * s + lane] = lj[s];
+    }
+}
+
+// The extended lists as the prefix of the far lists.
+__global__ void ext_from_far_kernel(const int* __restrict__ far, int n, int kx, int* __restrict__ ext) {
+    const long long total = (long long)n * kx;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x)
+        ext[e] = far[(e / kx) * ACO_KF + e % kx];
+}
+
 __global__ void dense_eta_kernel(const double* __restrict__ xy, int n, double beta, double tau0,
                                  double* __restrict__ etab_d, double* __restrict__ tau, int* __restrict__ errflag) {
     const long long total = (long long)n * n;
@@ -223,11 +337,21 @@ aco_status launch_build_grid_and_knn(aco_instance* inst) {
     const int warps_per_block = 8;
     const int kblocks = (int)fmin((double)inst->num_sms * 16, (double)ceil_div(n, warps_per_block));
     if (inst->ext) {
-        // the kx nearest cities once; the candidate lists are their first k (the same keys)
-        knn_kernel<true><<<kblocks, 32 * warps_per_block, 0, s>>>(inst->xy, inst->grid_dev, inst->city_cell,
-                                                                  inst->cell_start, inst->cell_city, inst->cell_xy, n,
-                                                                  inst->kx, 0.0, inst->ext, nullptr, nullptr,
-                                                                  inst->errflag);
+        // the kx nearest cities once (as the prefix of the far lists when the colony keeps them);
+        // the candidate lists are their first k (the same keys)
+        if (inst->far) {
+            knn_far_kernel<<<kblocks, 32 * warps_per_block, 0, s>>>(inst->xy, inst->grid_dev, inst->city_cell,
+                                                                   inst->cell_start, inst->cell_city, inst->cell_xy, n,
+                                                                   inst->far);
+            const long long te = (long long)n * inst->kx;
+            ext_from_far_kernel<<<(int)fmin((double)inst->num_sms * 8, (double)ceil_div(te, 256)), 256, 0, s>>>(
+                inst->far, n, inst->kx, inst->ext);
+        } else {
+            knn_kernel<true><<<kblocks, 32 * warps_per_block, 0, s>>>(inst->xy, inst->grid_dev, inst->city_cell,
+                                                                      inst->cell_start, inst->cell_city, inst->cell_xy,
+                                                                      n, inst->kx, 0.0, inst->ext, nullptr, nullptr,
+                                                                      inst->errflag);
+        }
         const long long total = (long long)n * inst->p.k;
         cand_from_ext_kernel<<<(int)fmin((double)inst->num_sms * 8, (double)ceil_div(total, 256)), 256, 0, s>>>(
             inst->xy, n, inst->p.k, inst->kx, inst->p.beta, inst->ext, inst->cand, inst->candw, inst->etab,

@@ -28,7 +28,9 @@ def _lbest_kw(n, m, k, f=0.3, seed=3, p_partial=1.0, fallback=0, alpha=1.0, beta
 
 # ------------------------------------------------------------------ candidate lists
 @pytest.mark.parametrize("gen,n,k", [("uniform", 3000, 16), ("clustered", 5000, 20), ("mixed", 4000, 12),
-                                     ("lattice", 400, 8), ("uniform", 5, 4), ("uniform", 33, 32)])
+                                     ("lattice", 400, 8), ("uniform", 5, 4), ("uniform", 33, 32),
+                                     # above 8,192 cities the lists are the prefix of the 128-nearest lists
+                                     ("clustered", 9000, 32), ("lattice", 10000, 16)])
 def test_candidate_lists_bit_exact(gen, n, k):
     if gen == "uniform":
         xy = aco_synth.uniform(n, 11)
@@ -37,7 +39,7 @@ def test_candidate_lists_bit_exact(gen, n, k):
     elif gen == "mixed":
         xy = aco_synth.mixed(n, 20, 0.02, 13)
     else:
-        g = np.arange(20, dtype=np.float64)
+        g = np.arange(int(round(n ** 0.5)), dtype=np.float64)
         xy = np.ascontiguousarray(np.stack(np.meshgrid(g, g), -1).reshape(-1, 2))
     col, ref = pair(xy, **_lbest_kw(n, 2, k))
     cand = col.build_candidates(return_lists=True).cpu().numpy()
@@ -126,6 +128,8 @@ def test_dense_probabilities_within_1e5():
     (90, 5, 2, 1.0, 6, 0.5, 1),      # two candidates, the Eq. 1 wheel over all unvisited
     (600, 1032, 8, 0.3, 4, 1.0, 0),  # m > 1024: rebuild weights from shared memory, rank rows in blocks
     (300, 1030, 6, 0.5, 3, 1.0, 0),  # m > 1024 and not a multiple of 8: the scalar rank-row paths
+    (12000, 8, 16, 0.05, 3, 1.0, 0),  # above 8,192 cities: initial tours read the 128-nearest lists
+    (10000, 6, 20, 0.05, 2, 1.0, 0),
 ])
 def test_partialaco_iterations_bit_exact(n, m, k, f, iters, p_partial, fallback):
     xy = aco_synth.clustered(n, max(1, n // 50), 0.02, n + m)
@@ -213,3 +217,21 @@ def test_call_order_and_arguments():
     col.tour_lengths(torch.from_numpy(bad))  # out-of-range index: skipped, flagged on the device
     with pytest.raises(AcoError):
         col.stats()
+
+
+def test_lattice_initial_tours_above_the_far_list_size():
+    """A 100 x 100 lattice (exact distance ties everywhere) above 8,192 cities: the initial tours,
+    whose exhausted steps read the 128-nearest lists ordered by (d^2, index), and one PartialACO
+    iteration, bit for bit against the oracle."""
+    g = np.arange(100, dtype=np.float64)
+    xy = np.ascontiguousarray(np.stack(np.meshgrid(g, g), -1).reshape(-1, 2))
+    n = xy.shape[0]
+    col, ref = pair(xy, **_lbest_kw(n, 4, 8, f=0.05, seed=5))
+    col.build_candidates()
+    for it in range(2):
+        tours, _ = col.construct(it, return_tours=True, return_lengths=True)
+        ref.construct(it)
+        d = first_divergence(tours.cpu().numpy(), ref.newtours)
+        assert d is None, f"iteration {it}: first differing (ant, position) {d}"
+        col.update()
+        ref.update()
