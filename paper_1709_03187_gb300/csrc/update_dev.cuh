@@ -11,13 +11,11 @@
 __device__ __forceinline__ void set_neighbours(int* __restrict__ nb, uint8_t* __restrict__ nbrank,
                                                const int* __restrict__ cand, int m, int k, int a, int c, int succ,
                                                int pred) {
-    const size_t e = ((size_t)c * m + a) * 2;
-    nb[e] = succ;
-    nb[e + 1] = pred;
+    const size_t e = ((size_t)c * m + a) * 2;  // even: the pair is 8-byte (ids) and 2-byte (ranks) aligned
+    *reinterpret_cast<int2*>(nb + e) = make_int2(succ, pred);
     uint8_t rs, rp;
     ranks_of(cand, k, c, succ, pred, rs, rp);
-    nbrank[e] = rs;
-    nbrank[e + 1] = rp;
+    *reinterpret_cast<uint16_t*>(nbrank + e) = (uint16_t)(rs | (rp << 8));
 }
 
 // Algorithm 1's replacement for ant a (one warp): when the new tour is strictly shorter than the
