@@ -30,8 +30,8 @@
 template <bool BATCH, int NT>
 __global__ void __launch_bounds__(NT) commit_kernel(const __grid_constant__ CommitArgs Cp,
                                                     const CommitArgs* __restrict__ batch, const int2* __restrict__ slot,
-                                                    int slots) {
-    int a = blockIdx.x, inst = 0;
+                                                    int slots, int ant0) {
+    int a = ant0 + (int)blockIdx.x, inst = 0;
     if (BATCH) {
         if ((int)blockIdx.x >= slots) return;
         const int2 sa = slot[blockIdx.x];
@@ -262,7 +262,7 @@ cudaError_t launch_update_batch(const CommitArgs* cargs, const int2* slot, int s
                                 int count, const RebuildArgs* rargs, const int4* blockmap, int rblocks, int m_cap,
                                 int k, cudaStream_t s) {
     CommitArgs c0{};
-    commit_kernel<true, 32><<<slots, 32, 0, s>>>(c0, cargs, slot, slots);
+    commit_kernel<true, 32><<<slots, 32, 0, s>>>(c0, cargs, slot, slots, 0);
     GbestArgs g0{};
     gbest_q_kernel<true><<<count, 256, 0, s>>>(g0, gargs);
     RebuildArgs r0{};
@@ -292,7 +292,17 @@ aco_status launch_update_lbest(aco_instance* inst) {
     const aco_params& p = inst->p;
     CommitArgs C;
     fill_commit_args(inst, C);
-    commit_kernel<false, 256><<<p.m, 256, 0, inst->stream>>>(C, nullptr, nullptr, 0);
+    if (!inst->initialized) {
+        // the first commit: every ant writes a whole tour's entries at random cities of the
+        // neighbour tables; 64 ants at a time touch 1 KB of ids and 128 B of ranks per city row
+        // (128 MB at 200,000 cities), so their partial sectors fill in L2 instead of going to DRAM
+        // half written
+        for (int a0 = 0; a0 < p.m; a0 += 64)
+            commit_kernel<false, 1024><<<p.m - a0 < 64 ? p.m - a0 : 64, 1024, 0, inst->stream>>>(C, nullptr, nullptr, 0,
+                                                                                               a0);
+    } else {
+        commit_kernel<false, 256><<<p.m, 256, 0, inst->stream>>>(C, nullptr, nullptr, 0, 0);
+    }
     aco_status st = check_launch(inst, "commit_kernel");
     if (st != ACO_OK) return st;
     GbestArgs G;
