@@ -197,6 +197,16 @@ def measure_l2_peak(stream, nbytes: int = 32 << 20, passes: int = 64):
             "how": "aco_probe_bandwidth, best of 3 launches of 64 passes, CUDA events"}
 
 
+def instance_desc(wl) -> str:
+    """The coordinates of a workload, as its generator draws them."""
+    kind, g = wl["gen"]
+    if kind == "clustered":
+        return f"clustered ({g['n_clusters']} Gaussian clusters, sigma={g['sigma']})"
+    if kind == "mixed":
+        return f"half uniform in [0,1)^2, half in {g['n_clusters']} Gaussian clusters (sigma={g['sigma']})"
+    return "uniform in [0,1)^2"
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
@@ -318,7 +328,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(t_max / args.steps * 1e3, 4), "higher_is_better": True,
         "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "iterations_per_s": round(its, 2),
-        "config": {"workload": f"{args.workload}: n={n} clustered (200 Gaussian clusters, sigma=0.005), k={k}, m={m}, "
+        "config": {"workload": f"{args.workload}: n={n} {instance_desc(wl)}, k={k}, m={m}, "
                                f"f={params['max_mod_frac']}, alpha={params['alpha']}, beta={params['beta']}, "
                                f"tau0={params['tau0']}, p_partial={params['p_partial']}",
                    "n": n, "m": m, "k": k, "parallelism": f"one colony split by ants over {world} GPUs" if world > 1 else "single colony",
