@@ -34,8 +34,10 @@ import aco_synth  # noqa: E402
 METRIC = "city decisions/s and ACO iterations/s at n=200K on 1 GB300; % of mem roofline"
 # DRAM bytes (read + write) per decision of construct_lbest_kernel from one ncu capture of the
 # 200,000-city workload at m = 256 (62.95 MB for 266,770 decisions), valid for the code it was
-# taken on: code_sha1 hashes construct.cu without its comments and blank lines, and the bench
-# reports null traffic once the code changes.
+# taken on: code_sha1 hashes the kernel's sources (the construction's device code and its
+# single-colony launch) without their comments and blank lines, and the bench reports null
+# traffic once the code changes.
+CONSTRUCT_SOURCES = ("construct_dev.cuh", "construct.cu")
 CONSTRUCT_TRAFFIC = {"code_sha1_12": "be12a2c5c526", "bytes_per_decision": 62916864.0 / 266769.67}
 L2_FLUSH_BYTES = 512 << 20  # > 126 MB L2
 
@@ -135,18 +137,20 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ algorithmic bytes
-def code_sha1(name: str) -> str:
-    """SHA-1 (12 hex digits) of a kernel source with its // comments, trailing blanks and blank
-    lines removed: comment edits keep an ncu capture of the code valid, code edits do not."""
+def code_sha1(*names: str) -> str:
+    """SHA-1 (12 hex digits) of kernel sources, in order, with their // comments, trailing blanks
+    and blank lines removed: comment edits keep an ncu capture of the code valid, code edits do
+    not."""
     import hashlib
     import re
 
     lines = []
-    with open(os.path.join(ROOT, "paper_1709_03187_gb300", "csrc", name), encoding="utf-8") as f:
-        for line in f:
-            line = re.sub(r"//.*$", "", line).rstrip()
-            if line:
-                lines.append(line)
+    for name in names:
+        with open(os.path.join(ROOT, "paper_1709_03187_gb300", "csrc", name), encoding="utf-8") as f:
+            for line in f:
+                line = re.sub(r"//.*$", "", line).rstrip()
+                if line:
+                    lines.append(line)
     return hashlib.sha1("\n".join(lines).encode()).hexdigest()[:12]
 
 
@@ -297,7 +301,7 @@ def run_ours(args):
     dom = "construct_lbest_kernel" if c_avg >= u_avg else "update (commit + gbest_q + rebuild)"
     ach = kernels[dom]["achieved_gbs"]
     traffic = None
-    if dom == "construct_lbest_kernel" and code_sha1("construct.cu") == CONSTRUCT_TRAFFIC["code_sha1_12"]:
+    if dom == "construct_lbest_kernel" and code_sha1(*CONSTRUCT_SOURCES) == CONSTRUCT_TRAFFIC["code_sha1_12"]:
         traffic = round(CONSTRUCT_TRAFFIC["bytes_per_decision"] * decisions / launches)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 2), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(ach / hbm_peak, 5), "peak_source": f"{peak_kind} hbm_gbs", "traffic": traffic,

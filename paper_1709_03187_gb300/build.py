@@ -22,6 +22,9 @@ UNITS = [
     ("api.cu", []),
     ("grid_knn.cu", []),
     ("construct.cu", []),
+    ("construct_batch.cu", []),
+    ("construct_batch_multi.cu", []),
+    ("construct_persist.cu", []),
     ("update.cu", []),
     ("noalloc.cu", []),
     ("batch.cu", []),

@@ -1,8 +1,8 @@
 """Host-side logic of bench.py that needs no GPU: the key of the stored construction traffic.
 
 The ncu traffic figure is valid for the kernel code it was captured on.  bench.py keys it to a
-hash of construct.cu without comments and blank lines: an edit of comments keeps the key, an
-edit of code changes it (and the bench then reports null traffic)."""
+hash of the construction kernel's sources without comments and blank lines: an edit of comments
+keeps the key, an edit of code changes it (and the bench then reports null traffic)."""
 import importlib.util
 import os
 import shutil
@@ -21,16 +21,24 @@ def test_code_hash_ignores_comments_and_blank_lines_only(tmp_path):
     b = _bench()
     csrc = tmp_path / "paper_1709_03187_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    src = os.path.join(ROOT, "paper_1709_03187_gb300", "csrc", "construct.cu")
-    shutil.copy(src, csrc / "construct.cu")
+    names = b.CONSTRUCT_SOURCES
+    for name in names:
+        shutil.copy(os.path.join(ROOT, "paper_1709_03187_gb300", "csrc", name), csrc / name)
     b.ROOT = str(tmp_path)
-    h0 = b.code_sha1("construct.cu")
-    text = (csrc / "construct.cu").read_text()
-    (csrc / "construct.cu").write_text("// a new header comment\n\n" + text.replace("\n", "  // note\n", 3))
-    assert b.code_sha1("construct.cu") == h0
-    (csrc / "construct.cu").write_text(text.replace("#define FULL 0xffffffffu", "#define FULL 0xfffffffeu"))
-    assert b.code_sha1("construct.cu") != h0
-
+    h0 = b.code_sha1(*names)
+    for name in names:
+        text = (csrc / name).read_text()
+        (csrc / name).write_text("// a new header comment\n\n" + text.replace("\n", "  // note\n", 3))
+        assert b.code_sha1(*names) == h0, name
+        (csrc / name).write_text(text)
+    # a code edit in either file changes the key
+    dev = (csrc / names[0]).read_text()
+    (csrc / names[0]).write_text(dev.replace("#define FULL 0xffffffffu", "#define FULL 0xfffffffeu"))
+    assert b.code_sha1(*names) != h0
+    (csrc / names[0]).write_text(dev)
+    host = (csrc / names[1]).read_text()
+    (csrc / names[1]).write_text(host.replace("A.n = p.n;", "A.n = p.n + 0;"))
+    assert b.code_sha1(*names) != h0
 
 
 def test_construct_byte_model():

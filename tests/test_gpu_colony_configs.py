@@ -1,9 +1,9 @@
 """Whole colonies against the oracle at the sizes of the benchmark configurations (needs a GB300).
 
   * The 10,000-city configuration (half uniform, half in 20 Gaussian clusters; k = 20, m = 256,
-    f = 0.1): k = 20 takes the construction kernel's unstaged row path, with 32-lane scans and the
-    FP32-screened exhausted step over the remaining list.  Every tour, length, l_best and counter
-    bit for bit over several iterations.
+    f = 0.1): k = 20 takes the construction kernel's wide stage (rows of 24 entries) with 32-lane
+    scans and the hashed exhausted step.  Every tour, length, l_best and counter bit for bit over
+    several iterations.
   * A 2,400-city colony with k = 16 (the staged rows and the hashed exhausted step).
   * In both, the oracle counts exhausted-list picks whose pheromone lies above tau0 (an l_best
     neighbour outside the candidate list, Section 3 pheromone under the Section 6 fallback), and

@@ -130,6 +130,9 @@ def test_dense_probabilities_within_1e5():
     (300, 1030, 6, 0.5, 3, 1.0, 0),  # m > 1024 and not a multiple of 8: the scalar rank-row paths
     (12000, 8, 16, 0.05, 3, 1.0, 0),  # above 8,192 cities: initial tours read the 128-nearest lists
     (10000, 6, 20, 0.05, 2, 1.0, 0),
+    (700, 24, 24, 0.3, 8, 1.0, 0),   # the widest stage (k = 24 rows of 24 entries)
+    (500, 16, 18, 0.4, 8, 0.8, 0),   # k = 18 on the wide stage, full tours mid-run
+    (400, 12, 21, 0.3, 6, 1.0, 0),   # odd k above 16: rows read from global memory
 ])
 def test_partialaco_iterations_bit_exact(n, m, k, f, iters, p_partial, fallback):
     xy = aco_synth.clustered(n, max(1, n // 50), 0.02, n + m)
