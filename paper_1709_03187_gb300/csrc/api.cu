@@ -1,6 +1,6 @@
 // api.cu -- the C ABI entry points of include/aco.h: argument checks, allocation (all in
 // aco_create_instance), call ordering and error reporting.  Kernels live in grid_knn.cu,
-// construct.cu and update.cu.
+// construct_dev.cuh (launched from construct.cu and the batched units) and update.cu.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>

@@ -6,7 +6,7 @@
 //   commit (one block per ant slot), C_gbest and weights (one block per colony),
 //   pheromone rebuild (block map over every colony's cities),
 // plus a one-thread increment of the device iteration counter, captured once as a CUDA graph and
-// replayed -- or all iterations of a call in one persistent cooperative launch (construct.cu:
+// replayed -- or all iterations of a call in one persistent cooperative launch (construct_persist.cu:
 // work queues of ant slots and city chunks, grid-wide barriers with bounded waits).  The schedule
 // does not change any result (each ant's work is deterministic), so the autotuner times live
 // iterations with each schedule -- for the four launches, ants per block and a register cap
@@ -23,7 +23,7 @@
 
 #include "common.cuh"
 
-struct LbestArgs;  // defined in construct.cu
+struct LbestArgs;  // defined in construct_dev.cuh
 void fill_lbest_args(const aco_instance* inst, int32_t iteration, LbestArgs& A);
 size_t construct_smem_per_ant(int n, int k);
 cudaError_t launch_construct_batch(const LbestArgs* args, const int2* slot, const int* iteration, int slots,

@@ -279,7 +279,7 @@ struct RebuildArgs {
 };
 
 // ------------------------------------------------------------------ persistent batched launch
-struct LbestArgs;  // construct.cu
+struct LbestArgs;  // construct_dev.cuh
 struct PersistArgs {
     const LbestArgs* largs;
     const CommitArgs* cargs;
