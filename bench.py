@@ -301,7 +301,9 @@ def run_ours(args):
     dom = "construct_lbest_kernel" if c_avg >= u_avg else "update (commit + gbest_q + rebuild)"
     ach = kernels[dom]["achieved_gbs"]
     traffic = None
-    if dom == "construct_lbest_kernel" and code_sha1(*CONSTRUCT_SOURCES) == CONSTRUCT_TRAFFIC["code_sha1_12"]:
+    # the stored figure is per decision of the 200,000-city workload (k = 16) at this code
+    if (dom == "construct_lbest_kernel" and args.workload == "lbest200k"
+            and code_sha1(*CONSTRUCT_SOURCES) == CONSTRUCT_TRAFFIC["code_sha1_12"]):
         traffic = round(CONSTRUCT_TRAFFIC["bytes_per_decision"] * decisions / launches)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 2), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(ach / hbm_peak, 5), "peak_source": f"{peak_kind} hbm_gbs", "traffic": traffic,
