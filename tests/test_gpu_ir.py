@@ -10,7 +10,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("n,m,k,f,seed", [(300, 16, 8, 0.5, 3), (2000, 24, 16, 0.2, 5), (777, 8, 10, 1.0, 9)])
+@pytest.mark.parametrize("n,m,k,f,seed", [(300, 16, 8, 0.5, 3), (2000, 24, 16, 0.2, 5), (777, 8, 10, 1.0, 9),
+                                          (1500, 16, 20, 0.3, 11)])  # k = 20: the 24-entry stage
 def test_ir_colony_matches_oracle(n, m, k, f, seed):
     require_gpu()
     from paper_1709_03187_gb300 import Colony

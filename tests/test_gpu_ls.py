@@ -14,6 +14,7 @@ pytestmark = pytest.mark.gpu
     (1500, 16, 12, 0.3, 0.3, 40, 1),   # about 19 blocks per pass and a ragged last block
     (200, 12, 8, 1.0, 1.0, 300, 2),    # one block covering the tour; the 8-ant cap binds
     (2600, 8, 16, 0.05, 0.5, 500, 3),  # the paper's window, partial rebuilds of 130 cities
+    (1200, 8, 20, 0.2, 0.5, 100, 4),   # k = 20: construction on the 24-entry stage
 ])
 def test_local_search_matches_oracle(n, m, k, f, p, W, seed):
     require_gpu()
