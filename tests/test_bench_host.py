@@ -76,3 +76,23 @@ def test_every_name_read_is_bound_somewhere():
                 bound.add(node.name)
         used = {n.id for n in ast.walk(tree) if isinstance(n, ast.Name) and isinstance(n.ctx, ast.Load)}
         assert not used - bound, (rel, sorted(used - bound))
+
+
+def test_every_cuda_unit_is_built():
+    """Every .cu file under csrc is a unit of the library build (a unit left out would leave its
+    launches undefined at link time only on the machine that builds it)."""
+    import importlib
+    import pathlib
+
+    build = importlib.import_module("paper_1709_03187_gb300.build")
+    csrc = pathlib.Path(ROOT) / "paper_1709_03187_gb300" / "csrc"
+    assert {p.name for p in csrc.glob("*.cu")} == {u for u, _ in build.UNITS}
+
+
+def test_workload_descriptions_follow_the_generators():
+    import aco_synth
+
+    b = _bench()
+    assert b.instance_desc(aco_synth.WORKLOADS["lbest200k"]) == "clustered (200 Gaussian clusters, sigma=0.005)"
+    assert b.instance_desc(aco_synth.WORKLOADS["lbest10k"]).startswith("half uniform in [0,1)^2, half in 20")
+    assert b.instance_desc(aco_synth.WORKLOADS["dense100"]) == "uniform in [0,1)^2"
