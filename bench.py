@@ -33,12 +33,12 @@ import aco_synth  # noqa: E402
 
 METRIC = "city decisions/s and ACO iterations/s at n=200K on 1 GB300; % of mem roofline"
 # DRAM bytes (read + write) per decision of construct_lbest_kernel from one ncu capture of the
-# 200,000-city workload at m = 256 (62.90 MB for 266,770 decisions), valid for the code it was
+# 200,000-city workload at m = 256 (62.83 MB for 266,770 decisions), valid for the code it was
 # taken on: code_sha1 hashes the kernel's sources (the construction's device code and its
 # single-colony launch) without their comments and blank lines, and the bench reports null
 # traffic once the code changes.
 CONSTRUCT_SOURCES = ("construct_dev.cuh", "construct.cu")
-CONSTRUCT_TRAFFIC = {"code_sha1_12": "8c5f991a57bc", "bytes_per_decision": 62898944.0 / 266769.67}
+CONSTRUCT_TRAFFIC = {"code_sha1_12": "c8c114747692", "bytes_per_decision": 62828032.0 / 266769.67}
 L2_FLUSH_BYTES = 512 << 20  # > 126 MB L2
 
 

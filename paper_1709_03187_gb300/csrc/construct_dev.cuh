@@ -1493,7 +1493,8 @@ __device__ __forceinline__ void construct_ant(const LbestArgs& A, int a, int ite
         }
         // the previous step's city is marked now: it is not a candidate of itself, and the
         // warp synchronises before the next candidate test and before any exhausted step
-        if (lane == 0 && pend >= 0) atomicOr(&bits[pend >> 5], 1u << (pend & 31));
+        // (a plain read-modify-write: during the walk lane 0 is the set's only writer)
+        if (lane == 0 && pend >= 0) bits[pend >> 5] |= 1u << (pend & 31);
         int c = -1;
         float w = 0.f;
         bool feas = false;
