@@ -88,3 +88,61 @@ print(st, lib.aco_last_error(None).decode())
     assert r.returncode == 0, r.stderr
     status, msg = r.stdout.split(" ", 1)
     assert int(status) == 2 and "ACO_DEVICE_BYTES_LIMIT" in msg  # ACO_ERR_OOM
+
+
+def test_invalid_parameters_are_refused_before_any_device_call():
+    """aco_create_instance checks its arguments before it touches the device, so each refusal
+    (ACO_ERR_INVALID_ARG with the reason in aco_last_error) shows without a GPU."""
+    import sys
+
+    code = r'''
+import ctypes, json, sys
+sys.path.insert(0, sys.argv[1])
+from paper_1709_03187_gb300 import build
+from paper_1709_03187_gb300._ffi import Params
+lib = ctypes.CDLL(build.build())
+lib.aco_last_error.restype = ctypes.c_char_p
+# (mode, n, m, k, alpha, beta, rho, tau0, max_mod_frac, p_partial, seed, fallback, selection)
+ok = (1, 1000, 64, 16, 1.0, 2.0, 0.1, 1.0, 0.1, 1.0, 3, 0, 0)
+cases = {
+    "mode": dict(mode=7),
+    "n < 3": dict(n=2),
+    "m must be in [1, 16384]": dict(m=0),
+    "k must be in [1, min(32, n-1)]": dict(k=33),
+    "alpha, beta must be finite and >= 0": dict(alpha=float("nan")),
+    "tau0 must be > 0": dict(tau0=0.0),
+    "max_mod_frac in (0,1]": dict(max_mod_frac=0.0),
+    "p_partial in [0,1]": dict(p_partial=1.5),
+    "fallback must be 0 or 1": dict(fallback=2),
+    "selection must be 0 or 1": dict(selection=3),
+    "beta must be > 0 with candidate lists": dict(beta=0.0),
+    "Independent Roulette needs candidate lists (LBEST mode)": dict(mode=0, k=0, selection=1),
+    "DENSE mode supports n <= 8192": dict(mode=0, k=0, n=9000),
+    "n too large for the visited bitset": dict(n=2000000, m=8),
+    "n*m must be < 2^31": dict(n=1000000, m=4096),
+}
+names = ["mode", "n", "m", "k", "alpha", "beta", "rho", "tau0", "max_mod_frac", "p_partial", "seed",
+         "fallback", "selection"]
+out = {}
+for why, change in cases.items():
+    v = dict(zip(names, ok))
+    v.update(change)
+    p = Params(*[v[k] for k in names])
+    h = ctypes.c_void_p()
+    st = lib.aco_create_instance(ctypes.c_void_p(0x1000), ctypes.byref(p), None, ctypes.byref(h))
+    out[why] = [st, lib.aco_last_error(None).decode(), h.value]
+p = Params(*ok)
+h = ctypes.c_void_p()
+st = lib.aco_create_instance(ctypes.c_void_p(0x1004), ctypes.byref(p), None, ctypes.byref(h))
+out["xy_dev not 8-byte aligned"] = [st, lib.aco_last_error(None).decode(), h.value]
+print(json.dumps(out))
+'''
+    r = subprocess.run([sys.executable, "-c", code, ROOT], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    import json
+
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    for why, (status, msg, handle) in out.items():
+        assert status == 1, (why, status, msg)  # ACO_ERR_INVALID_ARG
+        assert msg == why, (why, msg)
+        assert handle is None, why
