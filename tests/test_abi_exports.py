@@ -146,3 +146,19 @@ print(json.dumps(out))
         assert status == 1, (why, status, msg)  # ACO_ERR_INVALID_ARG
         assert msg == why, (why, msg)
         assert handle is None, why
+
+
+def test_noalloc_refusals_before_any_device_call():
+    """aco_build_candidates_noalloc checks its pointers and sizes before any CUDA call: null or
+    misaligned buffers, n outside [2, 65,536] and k outside [1, min(32, n - 1)] give
+    ACO_ERR_INVALID_ARG without a GPU."""
+    from paper_1709_03187_gb300 import build
+
+    lib = ctypes.CDLL(build.build())
+    f = lib.aco_build_candidates_noalloc
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    xy, out = 0x1000, 0x2000  # never dereferenced: every case below is refused first
+    cases = [(None, 100, 8, out), (xy, 100, 8, None), (0x1004, 100, 8, out), (xy, 100, 8, 0x2002),
+             (xy, 1, 1, out), (xy, 65_537, 8, out), (xy, 100, 0, out), (xy, 100, 33, out), (xy, 10, 10, out)]
+    for c in cases:
+        assert f(c[0], c[1], c[2], c[3], None) == 1, c  # ACO_ERR_INVALID_ARG
