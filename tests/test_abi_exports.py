@@ -162,3 +162,50 @@ def test_noalloc_refusals_before_any_device_call():
              (xy, 1, 1, out), (xy, 65_537, 8, out), (xy, 100, 0, out), (xy, 100, 33, out), (xy, 10, 10, out)]
     for c in cases:
         assert f(c[0], c[1], c[2], c[3], None) == 1, c  # ACO_ERR_INVALID_ARG
+
+
+def test_every_entry_point_refuses_a_null_handle_without_a_gpu():
+    """Every call on an instance, a batch or a network checks its handle first: a null handle gives
+    ACO_ERR_INVALID_ARG (and the destroy calls do nothing), so a caller's mistake there never
+    reaches the device."""
+    import sys
+
+    code = r'''
+import ctypes as C, sys
+sys.path.insert(0, sys.argv[1])
+from paper_1709_03187_gb300 import build
+lib = C.CDLL(build.build())
+P, I32, I64, D, F = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_float
+sig = {
+    "aco_build_candidates": [P, P], "aco_construct_tours": [P, I32, P, P], "aco_update_pheromone": [P],
+    "aco_tour_lengths": [P, P, I32, P], "aco_get_state": [P, P, P, P], "aco_set_state": [P, P, P],
+    "aco_get_stats": [P, P], "aco_step_probs": [P, I32, P, P, P], "aco_set_max_mod_frac": [P, D],
+    "aco_set_p_partial": [P, D], "aco_set_local_search": [P, D, I32], "aco_set_async_share": [P, I32],
+    "aco_set_ant_range": [P, I32, I32], "aco_export_commits": [P, P, I64, P],
+    "aco_import_commits": [P, P, I32, I64], "aco_batch_build_candidates": [P],
+    "aco_batch_run": [P, I32, I32, I32], "aco_batch_get_state": [P, P, P], "aco_batch_get_best": [P, P],
+    "aco_batch_schedule": [P, P, P, P, P, P], "aco_batch_set_schedule": [P, I32],
+    "aco_batch_set_wait_limit": [P, D], "aco_batch_instance": [P, I32, P], "aco_mlp_get_weights": [P, P],
+    "aco_mlp_forward": [P, P, I64, P, P, F], "aco_mlp_backward": [P, P, P, I32, I32, F, P, P],
+    "aco_mlp_adam": [P, P, F], "aco_mlp_train": [P, P, P, I32, I32, I32, I32, F, P],
+    "aco_edge_features": [P, I32, P], "aco_tour_labels": [P, P], "aco_set_edge_scores": [P, P],
+}
+bad = []
+for name, args in sig.items():
+    f = getattr(lib, name)
+    f.argtypes = args
+    f.restype = C.c_int
+    vals = [None if a is P else a(0) for a in args]
+    st = f(*vals)
+    if st != 1:
+        bad.append((name, st))
+for name in ("aco_destroy_instance", "aco_batch_destroy", "aco_mlp_destroy"):
+    f = getattr(lib, name)
+    f.argtypes = [P]
+    f.restype = None
+    f(None)
+print("bad", bad)
+'''
+    r = subprocess.run([sys.executable, "-c", code, ROOT], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip().splitlines()[-1] == "bad []", r.stdout
