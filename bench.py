@@ -501,6 +501,7 @@ def run_reference(args):
         return
     import oracle
 
+    t_run = time.perf_counter()
     wl = aco_synth.WORKLOADS[args.workload]
     params = dict(wl["params"])
     n, m, k = params["n"], params["m"], params["k"]
@@ -516,10 +517,12 @@ def run_reference(args):
     sample = max(1, min(m, cores))  # one sampled ant per host thread and step
     rng = np.random.default_rng(1)
     per = []
+    sampled = []  # measured seconds of each step's sampled ants
     for step in range(args.warmup + args.steps):
         if params["mode"] == 1:
             ants = rng.choice(m, size=sample, replace=False).astype(np.int32)
             t_cs, dec = time_oracle_sample(ref, step + 2, ants, cores)
+            sampled.append(t_cs)
             # the rebuild (measured once in set-up) plus the sampled ants projected to the colony
             t_full = t_rb + t_cs * m / sample
             per.append((dec * m / sample, t_full))
@@ -543,6 +546,9 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tt / max(1, len(timed)) * 1e3, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "projected": params["mode"] == 1,
+           # what ran: the whole run's wall time, and per timed step the sampled ants' seconds
+           "wall_s": round(time.perf_counter() - t_run, 3),
+           "sampled_ms_per_step": round(sum(sampled[args.warmup:]) / max(1, len(timed)) * 1e3, 3) if sampled else None,
            "config": {"workload": args.workload, "n": n, "m": m, "k": k},
            "cpu_baseline": {"value": round(value, 1), "unit": "decisions/s",
                             "cores": cores if params["mode"] == 1 else 1, "kind": "oracle", "sample": how},
